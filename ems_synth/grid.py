@@ -1,0 +1,245 @@
+"""Seeded synthetic power-grid netlists, thermal rasters and Monte Carlo factors.
+
+These stand in for the paper's SAED32 power-grid netlists, YAML files and
+measured thermal maps (Sec. V), which are not available.  The generator only
+draws inputs; it holds none of the EM/TM method's arithmetic.  Both the CPU
+oracle and the CUDA library consume the same arrays.
+
+A grid is a dict of NumPy arrays (the content of an extracted netlist):
+
+  node_x, node_y        float64 [n_nodes]   IR node coordinates (m)
+  seg_a, seg_b          int32   [n_seg]     segment end nodes (a -> b is +x)
+  seg_layer             int32   [n_seg]     metal layer; trees never cross layers
+  seg_R0                float64 [n_seg]     resistance (Ohm), rho_Cu L/(W H)
+  seg_W, seg_H, seg_L   float64 [n_seg]     width, thickness, length (m)
+  seg_cells             int32   [n_seg]     finite-difference cells per segment
+  pad_node, pad_V       int32/float64       supply pads (Dirichlet)
+  sink_node, sink_I     int32/float64       current sinks (A drawn from node)
+  thermal               None or dict(T=[ny,nx] K, x0, y0, x1, y1)
+  kappa_factor          None or float64 [S, n_seg]  MC multiplier on kappa
+  sigc_factor           None or float64 [S, n_seg]  MC multiplier on sigma_crit
+
+Seeds follow NumPy Generator(PCG64(seed)).
+"""
+import math
+
+import numpy as np
+
+from .params import default_params
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def stripe_mesh(N, pitch, W=0.5e-6, H=0.2e-6, dx=0.5e-6, rho_Cu=None,
+                tree_cells=None):
+    """Two-layer mesh of N horizontal (layer 0) x N vertical (layer 1) stripes.
+
+    Crossing (row i, column j) is IR node i*N + j at (j*pitch, i*pitch); the
+    two layers are merged at each crossing (no via resistors).  Each stripe
+    ends at its outermost crossings and carries N-1 segments of length pitch.
+    Horizontal segments come first (row-major), then vertical ones.
+    tree_cells: optional int array [2N] of FD cells per segment for each
+    stripe (uneven trees); default is round(pitch / dx).
+    """
+    if rho_Cu is None:
+        rho_Cu = default_params()["rho_Cu"]
+    n = N * N
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N))
+    node_x = (jj.ravel() * pitch).astype(np.float64)
+    node_y = (ii.ravel() * pitch).astype(np.float64)
+    a, b, layer, stripe = [], [], [], []
+    for i in range(N):
+        for j in range(N - 1):
+            a.append(i * N + j); b.append(i * N + j + 1); layer.append(0); stripe.append(i)
+    for j in range(N):
+        for i in range(N - 1):
+            a.append(i * N + j); b.append((i + 1) * N + j); layer.append(1); stripe.append(N + j)
+    a = np.array(a, np.int32); b = np.array(b, np.int32)
+    ns = a.size
+    L = np.full(ns, pitch, np.float64)
+    Wa = np.full(ns, W, np.float64)
+    Ha = np.full(ns, H, np.float64)
+    if tree_cells is None:
+        cells = np.full(ns, int(round(pitch / dx)), np.int32)
+    else:
+        cells = np.asarray(tree_cells, np.int32)[np.array(stripe)]
+    return dict(
+        N=N, pitch=pitch,
+        node_x=node_x, node_y=node_y,
+        seg_a=a, seg_b=b, seg_layer=np.array(layer, np.int32),
+        seg_R0=rho_Cu * L / (Wa * Ha), seg_W=Wa, seg_H=Ha, seg_L=L,
+        seg_cells=cells,
+        pad_node=np.zeros(0, np.int32), pad_V=np.zeros(0),
+        sink_node=np.zeros(0, np.int32), sink_I=np.zeros(0),
+        thermal=None, kappa_factor=None, sigc_factor=None,
+    )
+
+
+def hotspot_raster(rng, die, n_spots, base, amp_lo, amp_hi, s_frac, nx=512, ny=512):
+    """Raster T(x, y) = base + sum_k A_k exp(-r_k^2 / (2 s^2)) over [0, die]^2.
+
+    Vertex-centred: sample (ix, iy) sits at (ix*die/(nx-1), iy*die/(ny-1)).
+    A_k ~ U(amp_lo, amp_hi); centres ~ U(die); s = s_frac * die (scalar or
+    (lo, hi) range drawn per spot).
+    """
+    xs = np.linspace(0.0, die, nx)
+    ys = np.linspace(0.0, die, ny)
+    X, Y = np.meshgrid(xs, ys)
+    T = np.full((ny, nx), float(base))
+    for _ in range(n_spots):
+        cx, cy = rng.uniform(0.0, die, size=2)
+        A = rng.uniform(amp_lo, amp_hi) if amp_hi > amp_lo else amp_lo
+        if isinstance(s_frac, tuple):
+            s = rng.uniform(*s_frac) * die
+        else:
+            s = s_frac * die
+        T += A * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2.0 * s * s))
+    return dict(T=T, x0=0.0, y0=0.0, x1=die, y1=die)
+
+
+def mc_factors(rng, n_samples, n_seg, cov=0.2):
+    """Lognormal multipliers with mean 1 and the given CoV, independent per
+    (sample, segment, parameter): returns (kappa_factor, sigc_factor)."""
+    s_ln = math.sqrt(math.log(1.0 + cov * cov))
+    mu = -0.5 * s_ln * s_ln
+    kf = np.exp(rng.normal(mu, s_ln, size=(n_samples, n_seg)))
+    sf = np.exp(rng.normal(mu, s_ln, size=(n_samples, n_seg)))
+    return kf, sf
+
+
+def _lognormal_currents(rng, k, median=0.707e-3, s_ln=0.98, lo=0.1e-3, hi=5e-3):
+    return np.clip(rng.lognormal(math.log(median), s_ln, size=k), lo, hi)
+
+
+def _pad_array(N, every):
+    idx = np.arange(every // 2, N, every)
+    return np.array([i * N + j for i in idx for j in idx], np.int32)
+
+
+def tiny_grid(seed=1, N=8, pitch=20e-6):
+    """8x8 stripes of 7 x 20 um segments, 4 corner pads at 1 V, a sink on
+    every crossing drawing U(0.5, 2) mA; uniform temperature (no map)."""
+    rng = _rng(seed)
+    g = stripe_mesh(N, pitch)
+    g["pad_node"] = np.array([0, N - 1, N * (N - 1), N * N - 1], np.int32)
+    g["pad_V"] = np.ones(4)
+    g["sink_node"] = np.arange(N * N, dtype=np.int32)
+    g["sink_I"] = rng.uniform(0.5e-3, 2e-3, size=N * N)
+    return g
+
+
+def mid_grid(seed=2, N=256, pitch=10e-6, n_spots=3, with_map=True, raster=512):
+    """N x N stripes at 10 um, a pad every 32 crossings, 2 % of crossings as
+    lognormal sinks (median 0.707 mA, s_ln 0.98, clipped to 0.1-5 mA), and a
+    340 K map with 3 Gaussian +40 K hotspots of s = 15 % of the die width."""
+    rng = _rng(seed)
+    g = stripe_mesh(N, pitch)
+    pads = _pad_array(N, 32 if N >= 64 else max(2, N // 2))
+    g["pad_node"] = pads
+    g["pad_V"] = np.ones(pads.size)
+    free = np.setdiff1d(np.arange(N * N, dtype=np.int32), pads)
+    k = max(1, int(round(0.02 * N * N)))
+    g["sink_node"] = np.sort(rng.choice(free, size=k, replace=False)).astype(np.int32)
+    g["sink_I"] = _lognormal_currents(rng, k)
+    if with_map:
+        die = (N - 1) * pitch
+        g["thermal"] = hotspot_raster(rng, die, n_spots, 340.0, 40.0, 40.0, 0.15,
+                                      nx=raster, ny=raster)
+    return g
+
+
+def mc_grid(seed=3, n_samples=1024, N=8, pitch=20e-6, cells_lo=32, cells_hi=1024):
+    """The tiny grid with uneven trees: each stripe's total FD cell count is
+    drawn log-uniform in [cells_lo, cells_hi] and split evenly over its N-1
+    segments; n_samples sets of lognormal (CoV 20 %) kappa and sigma_crit
+    factors per segment."""
+    rng = _rng(seed)
+    g = tiny_grid(seed=seed, N=N, pitch=pitch)
+    tot = np.exp(rng.uniform(math.log(cells_lo), math.log(cells_hi), size=2 * N))
+    per_seg = np.maximum(1, np.round(tot / (N - 1))).astype(np.int32)
+    stripe = np.concatenate([np.repeat(np.arange(N), N - 1),
+                             np.repeat(np.arange(N, 2 * N), N - 1)])
+    g["seg_cells"] = per_seg[stripe].astype(np.int32)
+    if n_samples > 0:
+        g["kappa_factor"], g["sigc_factor"] = mc_factors(rng, n_samples, g["seg_a"].size)
+    return g
+
+
+def large_grid(seed=5, N=2048, pitch=5e-6, n_samples=256, raster=512):
+    """2048 x 2048 stripes at 5 um (10 cells per segment), a pad every 32
+    crossings, 5 % lognormal sinks, 8 hotspots on 330 K with amplitudes
+    U(0, 90) K, and n_samples MC factor sets."""
+    rng = _rng(seed)
+    g = stripe_mesh(N, pitch)
+    pads = _pad_array(N, 32)
+    g["pad_node"] = pads
+    g["pad_V"] = np.ones(pads.size)
+    free = np.setdiff1d(np.arange(N * N, dtype=np.int32), pads)
+    k = int(round(0.05 * N * N))
+    g["sink_node"] = np.sort(rng.choice(free, size=k, replace=False)).astype(np.int32)
+    g["sink_I"] = _lognormal_currents(rng, k)
+    die = (N - 1) * pitch
+    g["thermal"] = hotspot_raster(rng, die, 8, 330.0, 0.0, 90.0, 0.15, nx=raster, ny=raster)
+    if n_samples > 0:
+        g["kappa_factor"], g["sigc_factor"] = mc_factors(rng, n_samples, g["seg_a"].size)
+    return g
+
+
+def tree_grid(kind, seed=0, seg_len=10e-6, cells=8, W=0.5e-6, H=0.2e-6, I_sink=2e-3,
+              rho_Cu=None):
+    """Single-layer branched test trees (one tree each) with one pad and sinks:
+    'T' (3 arms from a junction), 'comb' (spine with 3 teeth), 'star'
+    (5 arms), 'chain' (4 segments).  The pad sits at node 0; every other IR
+    node draws a seeded U(0.5, 1.5) x I_sink."""
+    if rho_Cu is None:
+        rho_Cu = default_params()["rho_Cu"]
+    rng = _rng(seed)
+    if kind == "chain":
+        xy = [(0, 0), (1, 0), (2, 0), (3, 0), (4, 0)]
+        edges = [(0, 1), (1, 2), (2, 3), (3, 4)]
+    elif kind == "T":
+        xy = [(0, 0), (1, 0), (2, 0), (1, 1)]
+        edges = [(0, 1), (1, 2), (1, 3)]
+    elif kind == "comb":
+        xy = [(0, 0), (1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)]
+        edges = [(0, 1), (1, 2), (2, 3), (1, 4), (2, 5), (3, 6)]
+    elif kind == "star":
+        xy = [(0, 0), (1, 0), (2, 0), (1, 1), (1, -1), (0, 1)]
+        edges = [(0, 1), (1, 2), (1, 3), (1, 4), (1, 5)]
+    else:
+        raise ValueError(kind)
+    xy = np.array(xy, np.float64) * seg_len
+    a = np.array([e[0] for e in edges], np.int32)
+    b = np.array([e[1] for e in edges], np.int32)
+    L = np.hypot(*(xy[b] - xy[a]).T)
+    ns = a.size
+    Wa = np.full(ns, W); Ha = np.full(ns, H)
+    nn = xy.shape[0]
+    return dict(
+        N=0, pitch=seg_len,
+        node_x=xy[:, 0].copy(), node_y=xy[:, 1].copy(),
+        seg_a=a, seg_b=b, seg_layer=np.zeros(ns, np.int32),
+        seg_R0=rho_Cu * L / (Wa * Ha), seg_W=Wa, seg_H=Ha, seg_L=L,
+        seg_cells=np.full(ns, cells, np.int32),
+        pad_node=np.array([0], np.int32), pad_V=np.ones(1),
+        sink_node=np.arange(1, nn, dtype=np.int32),
+        sink_I=I_sink * rng.uniform(0.5, 1.5, size=nn - 1),
+        thermal=None, kappa_factor=None, sigc_factor=None,
+    )
+
+
+def config(name, **kw):
+    """The five workloads by name: 'tiny' (8x8, 4,496 stress nodes), 'mid'
+    (256x256 with map, 2,611,712 nodes), 'mc' (uneven 8x8 trees, 1,024
+    samples), 'large' (2048x2048, 256 samples)."""
+    if name == "tiny":
+        return tiny_grid(**kw)
+    if name == "mid":
+        return mid_grid(**kw)
+    if name == "mc":
+        return mc_grid(**kw)
+    if name == "large":
+        return large_grid(**kw)
+    raise ValueError(name)
