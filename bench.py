@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Benchmark: stress node-steps/s of the full coupled EM/TM/IR aging run.
+
+One step = one full time-to-failure run (64 aging steps x 256 backward-Euler
+steps over every tree, IR re-solves, nucleation, void growth, resistance
+write-back) of the 256 x 256-stripe two-layer mesh: 512 trees x 5,101 nodes =
+2,611,712 stress nodes with a 3-hotspot thermal map, so 4.28e10 node-steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+trees and samples are independent; no collective on the data path) and
+rank 0 prints the aggregate.  --impl reference times the CPU oracle on the
+same workload (bounded sample per step) on this host's cores.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stress node-steps/s; full-chip TTF time at <=0.05% TTF error, plain vs chosen"
+WORKLOAD = ("256x256-stripe two-layer Cu mesh: 512 trees x 5,101 stress nodes (2,611,712), "
+            "10 um segments, dx 0.5 um, 64 pads, 1,311 lognormal sinks, 340 K + 3 x 40 K hotspot map; "
+            "64 aging steps x 256 BE steps over a 10-year horizon per TTF run")
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_mine(args):
+    import numpy as np
+    import torch
+
+    import ems_synth as es
+    from paper_2604_10743_gb300 import EMS_F32, EMS_F64
+    from paper_2604_10743_gb300.engine import Engine
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    g = es.mid_grid()
+    p = es.default_params()
+    prec = EMS_F32 if args.precision == "f32" else EMS_F64
+    eng = Engine(p, g, precision=prec)
+    init = eng.state_export()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def one():
+        eng.state_import(init)
+        flush.fill_(1)
+        return eng.ttf()
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    l0 = eng.launch_count()
+    clk = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stress_ms = 0.0
+    res = None
+    for _ in range(args.steps):
+        res = one()
+        stress_ms += res["stress_ms"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = eng.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    node_steps = res["node_steps"]
+    value = node_steps * args.steps * world / (ms / 1e3)
+
+    # dominant kernel: the chain stress kernel; one launch advances every tree
+    # by n_inner steps.  Algorithmic bytes per node-step: state in + out (2w)
+    # plus the per-launch coefficient arrays amortised over the inner steps.
+    w = 4 if prec == EMS_F32 else 8
+    n_nodes = eng.n_stress
+    n_inner = p["n_inner"]
+    n_coef = 7 if prec == EMS_F32 else 6
+    alg_bytes_launch = n_nodes * (2 * w * n_inner + n_coef * w)
+    per_launch_ms = stress_ms / (args.steps * p["n_outer"])
+    peaks, src = _peaks()
+    achieved = alg_bytes_launch / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")
+    if os.path.exists(tf):
+        try:
+            t = json.load(open(tf))
+            if t.get("precision") == args.precision:
+                traffic = t.get("bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src if src == "measured" else "fallback 6.8 TB/s",
+            "kernel": "k_chain (stress advance, one launch = 256 BE steps of all trees)",
+            "alg_bytes_per_launch": alg_bytes_launch, "launch_ms": round(per_launch_ms, 4)}
+
+    # end to end through the public API with host buffers: load the netlist
+    # and map from host arrays, run, read the TTF results back
+    e2e = None
+    if not args.no_e2e:
+        th = g["thermal"]
+        h2d = sum(np.asarray(g[k]).nbytes for k in ("node_x", "node_y", "seg_a", "seg_b", "seg_layer",
+                                                      "seg_cells", "seg_R0", "seg_W", "seg_H", "seg_L",
+                                                      "pad_node", "pad_V", "sink_node", "sink_I"))
+        h2d += th["T"].nbytes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 2))
+        for _ in range(ke):
+            e = Engine(p, g, precision=prec)
+            r = e.ttf()
+            e.close()
+        torch.cuda.synchronize()
+        dt_e = (time.perf_counter() - t0) / ke
+        d2h = 8 * 3 + 4 + 8 * (p["n_outer"] + 1)
+        e2e = {"value": node_steps * world / dt_e, "unit": "node-steps/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "s_per_step": round(dt_e, 4)}
+
+    # plain method (FP64 backward Euler, no screen) for the TTF-time comparison
+    plain = None
+    if not args.no_plain and prec != EMS_F64:
+        ep = Engine(p, g, precision=EMS_F64)
+        ip = ep.state_export()                     # fresh state
+        ep.ttf()                                   # warm
+        torch.cuda.synchronize()
+        ep.state_import(ip)
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        rp = ep.ttf()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pms = a0.elapsed_time(a1)
+        plain = {"ttf_s": float(rp["ttf"][0]), "final_drop": float(rp["final_drop"][0]),
+                 "ttf_wall_ms": round(pms, 2), "node_steps_per_s": rp["node_steps"] / (pms / 1e3)}
+        ep.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(g, p, 1)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (stress, increment form) / f64 (IR PCG, nucleation time)" if prec == EMS_F32 else "f64",
+        "data": "synthetic (seeded generator; the paper's SAED32 netlists and maps are not available)",
+        "config": {"workload": WORKLOAD, "trees": eng.n_trees, "stress_nodes": eng.n_stress,
+                   "node_steps_per_step": node_steps, "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "256 MB buffer written between timed iterations (L2 flush)"},
+        "ttf_s": float(res["ttf"][0]), "final_drop": float(res["final_drop"][0]),
+        "ttf_wall_ms": ms / args.steps, "plain_fp64": plain,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    eng.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(g, p, n_outer):
+    """The CPU oracle, as it stands, on a bounded sample of the same workload:
+    the full grid (all 512 trees) for n_outer aging steps."""
+    from oracle import flow as F
+    g = dict(g)
+    g["trees"] = F.build_trees(g)
+    t0 = time.perf_counter()
+    r = F.run_ttf(g, p, n_outer=n_outer)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": r["node_steps"] / dt, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d aging steps (all 512 trees, %d BE steps each) incl. IR solves" %
+                      (n_outer, p["n_outer"], p["n_inner"]), "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    import ems_synth as es
+    from oracle import flow as F
+    g = es.mid_grid()
+    p = es.default_params()
+    g["trees"] = F.build_trees(g)
+    for _ in range(args.warmup):
+        F.run_ttf(g, p, n_outer=1)
+    t0 = time.perf_counter()
+    ns = 0
+    for _ in range(args.steps):
+        r = F.run_ttf(g, p, n_outer=1)
+        ns += r["node_steps"]
+    dt = time.perf_counter() - t0
+    v = ns / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "node-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 aging step per step"},
+            "cpu_baseline": {"value": v, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "1 of 64 aging steps of the full grid per step"},
+            "e2e": {"value": v, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        import __graft_entry__ as ge
+        ge.build()
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * ems.h -- C ABI of the GB300 EM/TM stress / void / IR-drop engine.
+ *
+ * The engine runs the hot path of EMSpice 3 (arXiv 2604.10743) on one GPU:
+ * transient electromigration + thermomigration stress on every interconnect
+ * tree of a power grid (Korhonen's PDE, Sec. III-D, Eq. tm_aware_korhonen_pde),
+ * advanced by backward-Euler steps (Sec. IV-B) or a rational Krylov reduced
+ * model (Sec. IV-E), with void nucleation and growth (Sec. III-D.2/3), void
+ * resistance write-back (Sec. IV-C) and IR-drop re-solves (Sec. III-C) up to
+ * the 10 %-IR-drop time to failure (Sec. V).
+ *
+ * Conventions
+ *   - Every call returns an ems_status; ems_last_error() gives a message.
+ *   - All calls on one context are ordered on the context's CUDA stream; a
+ *     call that returns host data synchronises that stream.
+ *   - Host input arrays are read during the call and not retained.
+ *   - Host output arrays are caller-allocated with the sizes stated.
+ *   - Units are SI (m, s, Pa, K, A, V, Ohm).
+ *   - Monte Carlo: a context holds S >= 1 samples; per-sample outputs are
+ *     laid out sample-major ([S][...]).
+ *
+ * Stress-node order ("canonical order") used by every per-node array:
+ *   trees are the connected components of same-layer segments (vias separate
+ *   trees), ordered by their smallest segment id.  A tree's nodes are the IR
+ *   nodes it touches plus seg_cells-1 interior nodes per segment.  Node 0 is
+ *   the root, the lowest-id IR node of degree one in the tree; the rest follow
+ *   depth-first, child segments in increasing segment id, each segment's
+ *   interior nodes listed from the parent end, then its far IR node.
+ *   Trees are concatenated in tree order.
+ */
+#ifndef EMS_H
+#define EMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EMS_OK = 0,
+    EMS_E_INVAL = 1,      /* bad argument or input (NaN, negative length, cycle, island) */
+    EMS_E_STATE = 2,      /* call out of order (e.g. stress advance before a grid is loaded) */
+    EMS_E_NOMEM = 3,      /* workspace too small or device allocation failed */
+    EMS_E_CUDA = 4,       /* a CUDA runtime call failed */
+    EMS_E_NOCONV = 5,     /* IR PCG did not reach its tolerance within its iteration cap */
+    EMS_E_TIMEOUT = 6,    /* a device-side wait ran out its iteration limit */
+    EMS_E_BREAKDOWN = 7,  /* Krylov basis broke down (tree falls back to backward Euler) */
+    EMS_E_OVERFLOW = 8    /* more voids in one tree than max_voids_per_tree */
+} ems_status;
+
+enum { EMS_F64 = 0, EMS_F32 = 1 };                 /* stress-path arithmetic */
+enum { EMS_BE = 0, EMS_KRYLOV = 1, EMS_AUTO = 2 }; /* stress method */
+
+/*
+ * Material and numerical settings (the paper's YAML parameter file,
+ * Sec. IV-A).  Symbols as in Sec. III-D: kappa = D0 exp(-Ea/(k_B T)) B Omega
+ * / (k_B T); S = e Z* rho_Cu j / Omega; M = Q* / (Omega T) dT/dx.
+ */
+typedef struct {
+    double e_charge, k_B, Omega, rho_Cu, B_modulus, Z_star, D0, Ea, Q_star;
+    double delta;          /* void interface thickness (Robin BC, Eq. incubation_bc) */
+    double rho_Ta, h_Ta;   /* barrier resistivity / thickness (void growth dR) */
+    double sigma_T;        /* initial residual stress (Eq. tm_aware_korhonen_ic) */
+    double sigma_crit;     /* critical stress (nucleation threshold) */
+    double T0;             /* uniform temperature when no thermal map is set */
+    double horizon;        /* simulated time span (s) */
+    int    n_outer, n_inner;      /* aging steps and BE steps per aging step */
+    double ir_fail_frac;   /* failure threshold on max IR drop / Vdd */
+    double Vdd;            /* supply voltage for the drop fraction */
+    int    precision;      /* EMS_F64 or EMS_F32 for the stress path (IR is always FP64) */
+    int    method;         /* EMS_BE, EMS_KRYLOV or EMS_AUTO */
+    int    krylov_q;       /* Krylov block order q (Alg. 1) */
+    double krylov_eta;     /* shift-time factor eta (Eq. rak_shift_time) */
+    double ir_rtol;        /* PCG relative residual target (||r|| <= rtol ||b||) */
+    int    ir_max_iter;    /* PCG iteration cap (EMS_E_NOCONV beyond it) */
+    int    max_voids_per_tree;  /* void slots per (tree, sample) */
+} ems_params;
+
+/*
+ * Extracted power-grid netlist (Sec. III-C: a resistor network with uniform
+ * current density per segment).  Segment a -> b is the +x direction of its
+ * current density.  Pads are Dirichlet voltage sources; sinks draw current.
+ * kappa_factor / sigc_factor, when not NULL, are [n_samples][n_seg] Monte
+ * Carlo multipliers (Sec. IV-F) on kappa and sigma_crit of every face / node
+ * of the segment (a crossing node takes the factor of its lowest-id
+ * incident segment within the tree); NULL means one unperturbed sample.
+ */
+typedef struct {
+    int n_nodes;
+    const double *node_x, *node_y;
+    int n_seg;
+    const int32_t *seg_a, *seg_b, *seg_layer, *seg_cells;
+    const double *seg_R0, *seg_W, *seg_H, *seg_L;
+    int n_pads;
+    const int32_t *pad_node;
+    const double *pad_V;
+    int n_sinks;
+    const int32_t *sink_node;
+    const double *sink_I;
+    int n_samples;
+    const double *kappa_factor, *sigc_factor;
+} ems_grid_desc;
+
+typedef struct ems_ctx ems_ctx;
+
+/* Bytes of device workspace a context needs for this grid.  Returns 0 if
+ * the descriptor is invalid. */
+size_t ems_workspace_bytes(const ems_params *params, const ems_grid_desc *grid);
+
+/*
+ * Create a context on the current CUDA device.
+ *   stream     cudaStream_t the context orders its work on (NULL = default stream)
+ *   workspace  caller-owned device memory of at least ems_workspace_bytes()
+ *              for the grid later loaded, 256-byte aligned; NULL lets the
+ *              context allocate (and free) its own.  The caller keeps a
+ *              caller-owned workspace alive until ems_destroy().
+ */
+ems_status ems_create(ems_ctx **out, const ems_params *params, void *stream,
+                      void *workspace, size_t ws_bytes);
+ems_status ems_destroy(ems_ctx *ctx);
+const char *ems_last_error(const ems_ctx *ctx);
+
+/*
+ * Load the grid (Sec. IV-A: partition into trees): checks the inputs,
+ * extracts the trees in canonical order, packs them by size into the
+ * chunk-interleaved layout, copies everything to the device, sets every
+ * sample's stress to sigma_T, its resistances to R0 and the time to 0.
+ * Errors: EMS_E_INVAL for NaN / non-positive geometry, bad indices, a
+ * same-layer cycle, or a node not connected to any pad; EMS_E_NOMEM.
+ */
+ems_status ems_load_grid(ems_ctx *ctx, const ems_grid_desc *grid);
+
+/* Number of trees / stress nodes / samples of the loaded grid. */
+ems_status ems_dims(const ems_ctx *ctx, int *n_trees, int64_t *n_stress_nodes,
+                    int *n_samples);
+
+/*
+ * Set the temperature field (Sec. III-A, "via-node temperatures are read
+ * from the map"): T at every stress node by bilinear interpolation of the
+ * vertex-centred raster T[iy*nx + ix] over [x0,x1] x [y0,y1] (clamped at the
+ * border); then kappa per face (Arrhenius at the face's mean temperature)
+ * and the thermomigration term M per face.  T == NULL sets uniform params.T0.
+ */
+ems_status ems_set_thermal_map(ems_ctx *ctx, const double *T, int nx, int ny,
+                               double x0, double y0, double x1, double y1);
+
+/*
+ * IR-drop solve (Sec. III-C, Eq. ir_drop_mna) for every sample with the
+ * current resistances: PCG (Jacobi) on the conductance matrix of the
+ * non-pad nodes, FP64, warm-started from the previous solution; then the
+ * segment current densities j = (u_a - u_b) / (R W H).
+ *   u_out         optional host [S][n_nodes] node voltages
+ *   max_drop_frac optional host [S]: max over nodes of (Vdd - u) / Vdd
+ * EMS_E_NOCONV if a sample misses ir_rtol within ir_max_iter iterations.
+ */
+ems_status ems_ir_solve(ems_ctx *ctx, double *u_out, double *max_drop_frac);
+
+/*
+ * Steady-state immortality screen (Sec. III-B) with the current currents
+ * and temperatures: per tree, zero flux on every face gives sigma_ss up to
+ * a constant fixed by atom conservation; a tree is mortal iff some node's
+ * sigma_ss exceeds its critical stress.
+ *   mortal        optional host [S][n_trees] (1 = mortal)
+ *   sigma_ss_max  optional host [S][n_trees]
+ *   sigma_ss      optional host [S][n_stress_nodes] canonical order
+ */
+ems_status ems_immortality_check(ems_ctx *ctx, uint8_t *mortal, double *sigma_ss_max,
+                                 double *sigma_ss);
+
+/*
+ * Advance every tree of every sample by n_steps backward-Euler steps of dt
+ * (Sec. IV-B; Eq. em_tm_ode: (C - dt A) s^{k+1} = C s^k + dt f) with the
+ * current currents, nucleation after every step (the non-void node with the
+ * largest sigma - sigma_crit, lowest index on ties, when that is >= 0;
+ * Sec. III-D.2), the Robin void stamp from the next step on (Sec. IV-D,
+ * Eq. robin_mid_tree) and void-volume growth by the Robin leak
+ * (Eq. void_volume_equation).  method EMS_KRYLOV / EMS_AUTO route trees
+ * through the reduced model (Sec. IV-E) where ems_krylov_reduce() built one.
+ *   n_new_voids   optional host: voids nucleated during the call (all samples)
+ */
+ems_status ems_stress_advance(ems_ctx *ctx, double dt, int n_steps, int method,
+                              int *n_new_voids);
+
+/*
+ * Build the rational Krylov reduced model (Sec. IV-E, Alg. 1) of every tree
+ * with n >= max(3q, 30) (Eq. krylov_threshold): shift t_s = eta L_max^2 /
+ * (pi^2 kappa_mean) (Eq. rak_shift_time), K = C/t_s - A, starting block
+ * [K^-1 C sigma0, K^-1 f], block Arnoldi to order q with FP64 modified
+ * Gram-Schmidt, projections A_h, C_h, f_h (Eq. rak_reduced).
+ *   n_reduced / n_fallback  optional host: trees reduced / sent back to BE
+ */
+ems_status ems_krylov_reduce(ems_ctx *ctx, int q, double eta, int *n_reduced,
+                             int *n_fallback);
+
+/*
+ * Void growth resistance write-back (Sec. III-D.3, IV-C, late failure):
+ * R_s = R0_s + sum over the voids on segment s of
+ * max(0, (V_v - W^2 H)/(W H) [rho_Ta/(h_Ta (2H+W)) - rho_Cu/(H W)]).
+ *   n_segments_changed  optional host: segments (all samples) whose R changed
+ */
+ems_status ems_void_update(ems_ctx *ctx, int *n_segments_changed);
+
+typedef struct {
+    int screen;        /* 1: run the immortality screen first (reported only) */
+    int n_outer;       /* 0: params.n_outer */
+} ems_ttf_opts;
+
+typedef struct {
+    double *ttf;          /* [S] time of the first 10 % crossing (0 if initially above, +inf if never) */
+    double *drop0;        /* [S] initial max IR drop fraction */
+    double *final_drop;   /* [S] max IR drop fraction at the end */
+    int32_t *n_voids;     /* [S] voids at the end */
+    int32_t *n_mortal;    /* [S] mortal trees by the screen (if opts.screen) */
+    double *drops;        /* optional [S][n_outer+1] drop after every aging step */
+    double node_steps;    /* out: sum over trees and samples of nodes x BE steps */
+    double stress_ms;     /* out: device time of the stress kernels (ms) */
+    double ir_ms;         /* out: device time of the IR solves (ms) */
+} ems_ttf_result;
+
+/*
+ * Full coupled aging run (Sec. IV-A, Eq. em_tm_ir_ode; TTF per Sec. V): from
+ * the current state, IR solve, then per aging step: stress advance of
+ * n_inner steps of horizon/(n_outer n_inner), void update, IR re-solve, max
+ * drop; TTF is the linear interpolation of the first crossing of
+ * ir_fail_frac.  Host result arrays are caller-allocated (NULL to skip).
+ */
+ems_status ems_ttf(ems_ctx *ctx, const ems_ttf_opts *opts, ems_ttf_result *out);
+
+/* Copies of device state (host buffers, canonical order). */
+ems_status ems_get_sigma(ems_ctx *ctx, double *sigma /* [S][n_stress_nodes] */);
+ems_status ems_get_currents(ems_ctx *ctx, double *j /* [S][n_seg] */);
+ems_status ems_get_resistance(ems_ctx *ctx, double *R /* [S][n_seg] */);
+/* Voids of every (tree, sample): up to cap entries, sample-major then tree,
+ * then nucleation order.  Returns the count in *n. */
+ems_status ems_get_voids(ems_ctx *ctx, int cap, int32_t *sample, int32_t *node,
+                         int32_t *seg, double *volume, double *t_nuc, int *n);
+
+/* PCG iterations of the last IR solve, per sample (host [S]). */
+ems_status ems_ir_iterations(ems_ctx *ctx, int32_t *iters);
+
+/* Number of kernels the context has launched since it was created. */
+ems_status ems_launch_count(const ems_ctx *ctx, int64_t *launches);
+
+/*
+ * Checkpoint / resume of the aging state (stress, voids, resistances, node
+ * voltages, time; Sec. IV-A: the state carried between aging steps).
+ * ems_state_export with buf == NULL returns the size in *bytes.
+ */
+ems_status ems_state_export(ems_ctx *ctx, void *buf, size_t *bytes);
+ems_status ems_state_import(ems_ctx *ctx, const void *buf, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,774 @@
+// ems_host.cu -- context, grid loading (tree extraction, packing, IR
+// structure), workspace layout, state I/O of the GB300 EM/TM engine.
+#include <algorithm>
+#include <cstdlib>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "ems_internal.cuh"
+
+namespace ems {
+
+ems_status fail(ems_ctx *c, ems_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+ems_status cuda_check(ems_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, EMS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t elem_bytes(const ems_ctx *c) { return c->prm.precision == EMS_F32 ? 4 : 8; }
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Input validation
+// ---------------------------------------------------------------------------
+bool finite_pos(const double *a, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!(std::isfinite(a[i]) && a[i] > 0.0)) return false;
+    return true;
+}
+
+ems_status validate(ems_ctx *c, const ems_params *p, const ems_grid_desc *g) {
+    if (!p || !g) return fail(c, EMS_E_INVAL, "null params or grid");
+    if (g->n_nodes <= 0 || g->n_seg <= 0 || g->n_pads <= 0)
+        return fail(c, EMS_E_INVAL, "grid needs nodes, segments and at least one pad");
+    if (!g->node_x || !g->node_y || !g->seg_a || !g->seg_b || !g->seg_layer || !g->seg_cells ||
+        !g->seg_R0 || !g->seg_W || !g->seg_H || !g->seg_L || !g->pad_node || !g->pad_V)
+        return fail(c, EMS_E_INVAL, "null grid array");
+    if (g->n_sinks > 0 && (!g->sink_node || !g->sink_I))
+        return fail(c, EMS_E_INVAL, "null sink array");
+    for (int i = 0; i < g->n_nodes; ++i)
+        if (!std::isfinite(g->node_x[i]) || !std::isfinite(g->node_y[i]))
+            return fail(c, EMS_E_INVAL, "non-finite node coordinate");
+    for (int s = 0; s < g->n_seg; ++s) {
+        if (g->seg_a[s] < 0 || g->seg_a[s] >= g->n_nodes || g->seg_b[s] < 0 ||
+            g->seg_b[s] >= g->n_nodes || g->seg_a[s] == g->seg_b[s])
+            return fail(c, EMS_E_INVAL, "segment end out of range");
+        if (g->seg_cells[s] < 1) return fail(c, EMS_E_INVAL, "segment with < 1 FD cell");
+    }
+    if (!finite_pos(g->seg_R0, g->n_seg) || !finite_pos(g->seg_W, g->n_seg) ||
+        !finite_pos(g->seg_H, g->n_seg) || !finite_pos(g->seg_L, g->n_seg))
+        return fail(c, EMS_E_INVAL, "non-positive or non-finite segment R, W, H or L");
+    for (int i = 0; i < g->n_pads; ++i)
+        if (g->pad_node[i] < 0 || g->pad_node[i] >= g->n_nodes || !std::isfinite(g->pad_V[i]))
+            return fail(c, EMS_E_INVAL, "bad pad");
+    for (int i = 0; i < g->n_sinks; ++i)
+        if (g->sink_node[i] < 0 || g->sink_node[i] >= g->n_nodes || !std::isfinite(g->sink_I[i]))
+            return fail(c, EMS_E_INVAL, "bad sink (index or NaN current)");
+    int S = g->n_samples > 0 ? g->n_samples : 1;
+    if ((g->kappa_factor || g->sigc_factor) && g->n_samples <= 0)
+        return fail(c, EMS_E_INVAL, "MC factors need n_samples > 0");
+    for (const double *fct : {g->kappa_factor, g->sigc_factor})
+        if (fct && !finite_pos(fct, S * g->n_seg))
+            return fail(c, EMS_E_INVAL, "non-positive MC factor");
+    if (!(p->sigma_crit > 0.0) || !(p->delta > 0.0) || !(p->B_modulus > 0.0) ||
+        !(p->T0 > 0.0) || !(p->D0 > 0.0) || p->n_inner < 1 || p->n_outer < 1 ||
+        !(p->horizon > 0.0) || p->max_voids_per_tree < 1 ||
+        p->max_voids_per_tree > EMS_MAX_VOIDS || p->ir_max_iter < 1 || !(p->ir_rtol > 0.0))
+        return fail(c, EMS_E_INVAL, "bad parameter value");
+    if (p->precision != EMS_F64 && p->precision != EMS_F32)
+        return fail(c, EMS_E_INVAL, "precision must be EMS_F64 or EMS_F32");
+    return EMS_OK;
+}
+
+// Every node must reach a pad through segments (else the IR system is singular).
+bool connected_to_pads(const ems_grid_desc *g) {
+    int n = g->n_nodes;
+    std::vector<int> deg(n + 1, 0);
+    for (int s = 0; s < g->n_seg; ++s) { deg[g->seg_a[s] + 1]++; deg[g->seg_b[s] + 1]++; }
+    for (int i = 0; i < n; ++i) deg[i + 1] += deg[i];
+    std::vector<int> adj(deg[n]), pos(deg.begin(), deg.end() - 1);
+    for (int s = 0; s < g->n_seg; ++s) {
+        adj[pos[g->seg_a[s]]++] = g->seg_b[s];
+        adj[pos[g->seg_b[s]]++] = g->seg_a[s];
+    }
+    std::vector<uint8_t> seen(n, 0);
+    std::vector<int> st;
+    for (int i = 0; i < g->n_pads; ++i)
+        if (!seen[g->pad_node[i]]) { seen[g->pad_node[i]] = 1; st.push_back(g->pad_node[i]); }
+    while (!st.empty()) {
+        int u = st.back(); st.pop_back();
+        for (int k = deg[u]; k < deg[u + 1]; ++k)
+            if (!seen[adj[k]]) { seen[adj[k]] = 1; st.push_back(adj[k]); }
+    }
+    for (int i = 0; i < n; ++i)
+        if (!seen[i]) return false;
+    return true;
+}
+
+int find(std::vector<int> &p, int x) {
+    while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Tree extraction in canonical order (see ems.h)
+// ---------------------------------------------------------------------------
+ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
+    const int ns = g->n_seg;
+    // (layer, node) groups of incident segments, via sorting endpoint records
+    struct Rec { int32_t layer, node, seg; };
+    std::vector<Rec> rec(2 * (size_t)ns);
+    for (int s = 0; s < ns; ++s) {
+        rec[2 * s] = {g->seg_layer[s], g->seg_a[s], s};
+        rec[2 * s + 1] = {g->seg_layer[s], g->seg_b[s], s};
+    }
+    std::sort(rec.begin(), rec.end(), [](const Rec &x, const Rec &y) {
+        if (x.layer != y.layer) return x.layer < y.layer;
+        if (x.node != y.node) return x.node < y.node;
+        return x.seg < y.seg;
+    });
+    std::vector<int64_t> gstart;          // group boundaries in rec
+    for (size_t k = 0; k < rec.size(); ++k)
+        if (k == 0 || rec[k].layer != rec[k - 1].layer || rec[k].node != rec[k - 1].node)
+            gstart.push_back((int64_t)k);
+    gstart.push_back((int64_t)rec.size());
+    const size_t ng = gstart.size() - 1;
+    std::unordered_map<int64_t, int32_t> gid;
+    gid.reserve(ng * 2);
+    auto key = [](int32_t layer, int32_t node) { return ((int64_t)layer << 32) ^ (uint32_t)node; };
+    std::vector<int> uf(ns);
+    std::iota(uf.begin(), uf.end(), 0);
+    for (size_t q = 0; q < ng; ++q) {
+        gid[key(rec[gstart[q]].layer, rec[gstart[q]].node)] = (int32_t)q;
+        for (int64_t k = gstart[q] + 1; k < gstart[q + 1]; ++k) {
+            int a = find(uf, rec[gstart[q]].seg), b = find(uf, rec[k].seg);
+            if (a != b) uf[std::max(a, b)] = std::min(a, b);
+        }
+    }
+    // tree ids in order of smallest segment id
+    std::vector<int32_t> tid_of_root(ns, -1);
+    tr.tree_of_seg.assign(ns, -1);
+    std::vector<std::vector<int32_t>> tsegs;
+    for (int s = 0; s < ns; ++s) {
+        int r = find(uf, s);
+        if (tid_of_root[r] < 0) { tid_of_root[r] = (int32_t)tsegs.size(); tsegs.emplace_back(); }
+        tr.tree_of_seg[s] = tid_of_root[r];
+        tsegs[tid_of_root[r]].push_back(s);
+    }
+    tr.n_trees = (int)tsegs.size();
+    tr.off.assign(1, 0);
+    int64_t total = 0;
+    for (auto &ts : tsegs)
+        for (int s : ts) total += g->seg_cells[s];
+    total += tr.n_trees;
+    tr.par.reserve(total); tr.face_seg.reserve(total); tr.face_dx.reserve(total);
+    tr.face_area.reserve(total); tr.face_sign.reserve(total); tr.x.reserve(total);
+    tr.y.reserve(total); tr.owner_seg.reserve(total);
+    tr.inc_ptr.assign(1, 0);
+    tr.is_chain.assign(tr.n_trees, 1);
+
+    auto group_of = [&](int32_t layer, int32_t node) -> int32_t {
+        auto it = gid.find(key(layer, node));
+        return it == gid.end() ? -1 : it->second;
+    };
+    for (int t = 0; t < tr.n_trees; ++t) {
+        const auto &ts = tsegs[t];
+        const int32_t layer = g->seg_layer[ts[0]];
+        // distinct IR nodes and root
+        std::vector<int32_t> nodes;
+        nodes.reserve(2 * ts.size());
+        for (int s : ts) { nodes.push_back(g->seg_a[s]); nodes.push_back(g->seg_b[s]); }
+        std::sort(nodes.begin(), nodes.end());
+        nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+        if (nodes.size() != ts.size() + 1)
+            return fail(c, EMS_E_INVAL, "same-layer component with a cycle: not a tree");
+        int32_t root = -1;
+        for (int32_t nd : nodes) {
+            int32_t q = group_of(layer, nd);
+            if (gstart[q + 1] - gstart[q] == 1) { root = nd; break; }   // nodes sorted: lowest id
+        }
+        if (root < 0) return fail(c, EMS_E_INVAL, "tree without a leaf");
+        const int64_t base = (int64_t)tr.par.size();
+        int32_t cnt = 0;
+        auto emit = [&](int32_t parent, int32_t seg, double dx, double area, int8_t sign, double xx,
+                        double yy, int32_t own, int32_t grp) -> int32_t {
+            tr.par.push_back(parent); tr.face_seg.push_back(seg); tr.face_dx.push_back(dx);
+            tr.face_area.push_back(area); tr.face_sign.push_back(sign);
+            tr.x.push_back(xx); tr.y.push_back(yy); tr.owner_seg.push_back(own);
+            if (grp >= 0) {
+                for (int64_t k = gstart[grp]; k < gstart[grp + 1]; ++k) tr.inc_seg.push_back(rec[k].seg);
+            } else {
+                tr.inc_seg.push_back(seg);
+            }
+            tr.inc_ptr.push_back((int32_t)tr.inc_seg.size());
+            return cnt++;
+        };
+        int32_t rg = group_of(layer, root);
+        emit(-1, -1, 0.0, 0.0, 0, g->node_x[root], g->node_y[root], rec[gstart[rg]].seg, rg);
+        // depth-first preorder: ("node", ir, local, came) or ("seg", pir, plocal, seg, cir)
+        struct Item { int kind; int32_t u, lu, s, w; };
+        std::vector<Item> stack;
+        stack.push_back({0, root, 0, -1, -1});
+        std::vector<int32_t> kids;
+        while (!stack.empty()) {
+            Item it = stack.back(); stack.pop_back();
+            if (it.kind == 0) {
+                int32_t q = group_of(layer, it.u);
+                kids.clear();
+                for (int64_t k = gstart[q]; k < gstart[q + 1]; ++k)
+                    if (rec[k].seg != it.s) kids.push_back(rec[k].seg);
+                for (auto k = kids.rbegin(); k != kids.rend(); ++k) {
+                    int32_t s = *k;
+                    int32_t w = g->seg_a[s] == it.u ? g->seg_b[s] : g->seg_a[s];
+                    stack.push_back({1, it.u, it.lu, s, w});
+                }
+            } else {
+                const int32_t s = it.s, u = it.u, w = it.w;
+                const int cells = g->seg_cells[s];
+                const double dx = g->seg_L[s] / cells, area = g->seg_W[s] * g->seg_H[s];
+                const int8_t sign = g->seg_a[s] == u ? 1 : -1;
+                int32_t prev = it.lu;
+                for (int k = 1; k < cells; ++k) {
+                    double f = (double)k / cells;
+                    prev = emit(prev, s, dx, area, sign,
+                                g->node_x[u] + f * (g->node_x[w] - g->node_x[u]),
+                                g->node_y[u] + f * (g->node_y[w] - g->node_y[u]), s, -1);
+                }
+                int32_t wg = group_of(layer, w);
+                int32_t lw = emit(prev, s, dx, area, sign, g->node_x[w], g->node_y[w],
+                                  rec[gstart[wg]].seg, wg);
+                stack.push_back({0, w, lw, s, -1});
+            }
+        }
+        for (int32_t i = 1; i < cnt; ++i)
+            if (tr.par[base + i] != i - 1) { tr.is_chain[t] = 0; break; }
+        tr.off.push_back(base + cnt);
+    }
+    // children CSR (tree-local indices)
+    const int64_t N = tr.off.back();
+    tr.child_ptr.assign(N + 1, 0);
+    for (int t = 0; t < tr.n_trees; ++t)
+        for (int64_t i = tr.off[t] + 1; i < tr.off[t + 1]; ++i) tr.child_ptr[tr.off[t] + tr.par[i] + 1]++;
+    for (int64_t i = 0; i < N; ++i) tr.child_ptr[i + 1] += tr.child_ptr[i];
+    tr.child_idx.assign(tr.child_ptr[N], 0);
+    std::vector<int32_t> fill(tr.child_ptr.begin(), tr.child_ptr.end() - 1);
+    for (int t = 0; t < tr.n_trees; ++t)
+        for (int64_t i = tr.off[t] + 1; i < tr.off[t + 1]; ++i)
+            tr.child_idx[fill[tr.off[t] + tr.par[i]]++] = (int32_t)(i - tr.off[t]);
+    return EMS_OK;
+}
+
+// Chunk length for a chain of n nodes: the smallest power of two in [4, 64]
+// that keeps the team at or below 128 threads, then T = ceil(n / M) rounded
+// up to whole warps.  A team larger than the chunk length allows (register
+// file) moves to a longer chunk; chains too long for any chunk fall back to
+// the single-thread tree path.  EMS_CHAIN_M (environment) pins M for tuning.
+void chain_shape(int64_t n, int prec, int *T, int *M) {
+    int m = 4;
+    while (m < 64 && (n + m - 1) / m > 128) m *= 2;
+    if (const char *e = getenv("EMS_CHAIN_M")) {
+        int v = atoi(e);
+        if (v == 4 || v == 8 || v == 16 || v == 32 || v == 64) m = v;
+    }
+    for (; m <= 64; m *= 2) {
+        int64_t t = ((n + m - 1) / m + 31) / 32 * 32;
+        if (t <= chain_max_threads(prec, m)) { *T = (int)t; *M = m; return; }
+    }
+    *T = 0; *M = 0;
+}
+
+// IR structure on the free (non-pad) nodes
+struct HostIR {
+    std::vector<int32_t> free_of_node, node_of_free, ptr, col, ent_ptr, ent_seg, rhs_ptr, rhs_seg;
+    std::vector<int8_t> ent_diag;
+    std::vector<double> rhs_padV, sink;
+    std::vector<double> padV_of_node;
+};
+
+void build_ir(const ems_grid_desc *g, HostIR &ir) {
+    const int n = g->n_nodes;
+    ir.padV_of_node.assign(n, NAN);
+    for (int i = 0; i < g->n_pads; ++i) ir.padV_of_node[g->pad_node[i]] = g->pad_V[i];
+    ir.free_of_node.assign(n, -1);
+    for (int i = 0; i < n; ++i)
+        if (std::isnan(ir.padV_of_node[i])) {
+            ir.free_of_node[i] = (int32_t)ir.node_of_free.size();
+            ir.node_of_free.push_back(i);
+        }
+    const int nf = (int)ir.node_of_free.size();
+    // per free row: (col, seg, diag) contributions
+    struct E { int32_t col, seg; int8_t diag; };
+    std::vector<std::vector<E>> rows(nf);
+    std::vector<std::vector<std::pair<int32_t, double>>> pads(nf);
+    for (int s = 0; s < g->n_seg; ++s) {
+        int a = g->seg_a[s], b = g->seg_b[s];
+        int fa = ir.free_of_node[a], fb = ir.free_of_node[b];
+        if (fa >= 0) {
+            rows[fa].push_back({fa, s, 1});
+            if (fb >= 0) rows[fa].push_back({fb, s, 0});
+            else pads[fa].push_back({s, ir.padV_of_node[b]});
+        }
+        if (fb >= 0) {
+            rows[fb].push_back({fb, s, 1});
+            if (fa >= 0) rows[fb].push_back({fa, s, 0});
+            else pads[fb].push_back({s, ir.padV_of_node[a]});
+        }
+    }
+    ir.ptr.assign(1, 0); ir.ent_ptr.assign(1, 0); ir.rhs_ptr.assign(1, 0);
+    for (int r = 0; r < nf; ++r) {
+        auto &v = rows[r];
+        std::sort(v.begin(), v.end(), [](const E &x, const E &y) {
+            return x.col != y.col ? x.col < y.col : x.seg < y.seg;
+        });
+        for (size_t k = 0; k < v.size(); ++k) {
+            if (k == 0 || v[k].col != v[k - 1].col) {
+                if (k > 0) ir.ent_ptr.push_back((int32_t)ir.ent_seg.size());
+                ir.col.push_back(v[k].col);
+                ir.ent_diag.push_back(v[k].diag);
+            }
+            ir.ent_seg.push_back(v[k].seg);
+        }
+        if (!v.empty()) ir.ent_ptr.push_back((int32_t)ir.ent_seg.size());
+        ir.ptr.push_back((int32_t)ir.col.size());
+        for (auto &pv : pads[r]) { ir.rhs_seg.push_back(pv.first); ir.rhs_padV.push_back(pv.second); }
+        ir.rhs_ptr.push_back((int32_t)ir.rhs_seg.size());
+    }
+    ir.sink.assign(nf, 0.0);
+    for (int i = 0; i < g->n_sinks; ++i) {
+        int f = ir.free_of_node[g->sink_node[i]];
+        if (f >= 0) ir.sink[f] += g->sink_I[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout: every device array carved from one block
+// ---------------------------------------------------------------------------
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((char *)b) {}
+    template <class T> T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct Plan {
+    HostTrees tr;
+    HostIR ir;
+    std::vector<TreePack> pack;
+    int64_t P = 0;
+    int S = 1;
+};
+
+ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Plan &pl) {
+    EMS_TRY(validate(c, p, g));
+    if (!connected_to_pads(g)) return fail(c, EMS_E_INVAL, "node not connected to any pad");
+    EMS_TRY(extract_trees(c, g, pl.tr));
+    build_ir(g, pl.ir);
+    pl.S = g->n_samples > 0 ? g->n_samples : 1;
+    pl.pack.resize(pl.tr.n_trees);
+    int64_t P = 0;
+    for (int t = 0; t < pl.tr.n_trees; ++t) {
+        int64_t n = pl.tr.off[t + 1] - pl.tr.off[t];
+        int T = 0, M = 0;
+        if (pl.tr.is_chain[t]) chain_shape(n, p->precision, &T, &M);
+        TreePack tp;
+        if (T > 0) { tp.T = T; tp.M = M; tp.pbase = P; P += (int64_t)T * M; }
+        else { tp.T = 1; tp.M = (int)n; tp.pbase = P; P += (n + 31) / 32 * 32; }
+        pl.pack[t] = tp;
+    }
+    pl.P = P;
+    return EMS_OK;
+}
+
+size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev &d) {
+    Carver cv(base);
+    const int S = pl.S, ns = g->n_seg, nn = g->n_nodes, nf = (int)pl.ir.node_of_free.size();
+    const int64_t nnz = (int64_t)pl.ir.col.size(), N = pl.tr.off.back(), P = pl.P;
+    const int nt = pl.tr.n_trees;
+    const int maxv = c ? c->prm.max_voids_per_tree : EMS_MAX_VOIDS;
+    const size_t eb = (c && c->prm.precision == EMS_F32) ? 4 : 8;
+    d.seg_a = cv.take<int32_t>(ns); d.seg_b = cv.take<int32_t>(ns);
+    d.seg_R0 = cv.take<double>(ns); d.seg_W = cv.take<double>(ns); d.seg_H = cv.take<double>(ns);
+    d.R = cv.take<double>((size_t)S * ns); d.j = cv.take<double>((size_t)S * ns);
+    d.ir_free_of_node = cv.take<int32_t>(nn); d.ir_node_of_free = cv.take<int32_t>(nf);
+    d.csr_ptr = cv.take<int32_t>(nf + 1); d.csr_col = cv.take<int32_t>(nnz);
+    d.ent_ptr = cv.take<int32_t>(nnz + 1); d.ent_seg = cv.take<int32_t>(pl.ir.ent_seg.size());
+    d.ent_diag = cv.take<int8_t>(nnz);
+    d.rhs_ptr = cv.take<int32_t>(nf + 1); d.rhs_seg = cv.take<int32_t>(pl.ir.rhs_seg.size() + 1);
+    d.rhs_padV = cv.take<double>(pl.ir.rhs_padV.size() + 1);
+    d.sink_of_free = cv.take<double>(nf);
+    d.csr_val = cv.take<double>((size_t)S * nnz);
+    d.ir_b = cv.take<double>((size_t)S * nf); d.ir_dinv = cv.take<double>((size_t)S * nf);
+    d.ir_x = cv.take<double>((size_t)S * nf); d.ir_r = cv.take<double>((size_t)S * nf);
+    d.ir_p = cv.take<double>((size_t)S * nf); d.ir_Ap = cv.take<double>((size_t)S * nf);
+    d.ir_z = cv.take<double>((size_t)S * nf);
+    d.u = cv.take<double>((size_t)S * nn); d.pad_V_of_node = cv.take<double>(nn);
+    d.drop = cv.take<double>(S);
+    d.red = cv.take<double>(4096 + 8 * (size_t)S);
+    d.ir_iters = cv.take<int32_t>(S);
+    d.gbar = cv.take<unsigned int>(64);
+    d.toff = cv.take<int64_t>(nt + 1);
+    d.par = cv.take<int32_t>(N); d.face_seg = cv.take<int32_t>(N); d.owner_seg = cv.take<int32_t>(N);
+    d.inc_ptr = cv.take<int32_t>(N + 1); d.inc_seg = cv.take<int32_t>(pl.tr.inc_seg.size());
+    d.child_ptr = cv.take<int32_t>(N + 1); d.child_idx = cv.take<int32_t>(pl.tr.child_idx.size() + 1);
+    d.face_sign = cv.take<int8_t>(N);
+    d.face_dx = cv.take<double>(N); d.face_area = cv.take<double>(N);
+    d.nx_ = cv.take<double>(N); d.ny_ = cv.take<double>(N);
+    d.Tn = cv.take<double>(N); d.Mface = cv.take<double>(N); d.V = cv.take<double>(N);
+    d.kap_a = cv.take<double>((size_t)S * N); d.g = cv.take<double>((size_t)S * N);
+    d.leak = cv.take<double>((size_t)S * N); d.thr = cv.take<double>((size_t)S * N);
+    d.f = cv.take<double>((size_t)S * N); d.sig_ss = cv.take<double>((size_t)S * N);
+    d.pbase = cv.take<int64_t>(nt); d.pT = cv.take<int32_t>(nt); d.pM = cv.take<int32_t>(nt);
+    d.sig = cv.take<char>((size_t)S * P * eb); d.alpha = cv.take<char>((size_t)S * P * eb);
+    d.beta = cv.take<char>((size_t)S * P * eb); d.gam = cv.take<char>((size_t)S * P * eb);
+    d.uu = cv.take<char>((size_t)S * P * eb); d.Pf = cv.take<char>((size_t)S * P * eb);
+    d.Pb = cv.take<char>((size_t)S * P * eb); d.pinv = cv.take<double>((size_t)S * P);
+    d.dtg = cv.take<char>((size_t)S * P * eb); d.dtl = cv.take<char>((size_t)S * P * eb);
+    d.v_count = cv.take<int32_t>((size_t)S * nt);
+    d.v_node = cv.take<int32_t>((size_t)S * nt * maxv); d.v_seg = cv.take<int32_t>((size_t)S * nt * maxv);
+    d.v_vol = cv.take<double>((size_t)S * nt * maxv); d.v_tnuc = cv.take<double>((size_t)S * nt * maxv);
+    d.dirty = cv.take<int32_t>((size_t)S * nt);
+    d.status = cv.take<int32_t>(8); d.counters = cv.take<int32_t>(8);
+    d.mortal = cv.take<uint8_t>((size_t)S * nt); d.ssmax = cv.take<double>((size_t)S * nt);
+    d.kfac = cv.take<double>((size_t)S * ns); d.sfac = cv.take<double>((size_t)S * ns);
+    d.thr0 = cv.take<double>((size_t)S * N);
+    d.R_prev = cv.take<double>((size_t)S * ns);
+    d.raster = cv.take<double>(EMS_MAX_RASTER);
+    return cv.off + 256;
+}
+
+template <class T>
+cudaError_t up(T *dst, const T *src, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+}  // namespace ems
+
+using namespace ems;
+
+extern "C" size_t ems_workspace_bytes(const ems_params *params, const ems_grid_desc *grid) {
+    ems_ctx tmp;
+    if (!params) return 0;
+    tmp.prm = *params;
+    Plan pl;
+    if (make_plan(&tmp, params, grid, pl) != EMS_OK) return 0;
+    Dev d{};
+    return carve(&tmp, pl, grid, nullptr, d);
+}
+
+extern "C" ems_status ems_create(ems_ctx **out, const ems_params *params, void *stream,
+                                 void *workspace, size_t ws_bytes) {
+    if (!out || !params) return EMS_E_INVAL;
+    ems_ctx *c = new ems_ctx();
+    c->prm = *params;
+    c->stream = (cudaStream_t)stream;
+    c->ws = workspace;
+    c->ws_bytes = workspace ? ws_bytes : 0;
+    c->own_ws = workspace == nullptr;
+    if (workspace && ((uintptr_t)workspace & 255)) {
+        delete c;
+        return EMS_E_INVAL;
+    }
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        delete c;
+        return EMS_E_CUDA;
+    }
+    *out = c;
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_destroy(ems_ctx *c) {
+    if (!c) return EMS_E_INVAL;
+    for (auto &b : c->buckets)
+        if (b.d_trees) cudaFree(b.d_trees);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return EMS_OK;
+}
+
+extern "C" const char *ems_last_error(const ems_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
+    if (!c) return EMS_E_INVAL;
+    Plan pl;
+    EMS_TRY(make_plan(c, &c->prm, g, pl));
+    Dev d{};
+    size_t need = carve(c, pl, g, nullptr, d);
+    if (c->own_ws) {
+        if (c->ws && c->ws_bytes < need) { cudaFree(c->ws); c->ws = nullptr; }
+        if (!c->ws) {
+            if (cudaMalloc(&c->ws, need) != cudaSuccess)
+                return fail(c, EMS_E_NOMEM, "workspace allocation failed");
+            c->ws_bytes = need;
+        }
+    } else if (c->ws_bytes < need) {
+        return fail(c, EMS_E_NOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+    }
+    carve(c, pl, g, c->ws, c->d);
+    Dev &D = c->d;
+    cudaStream_t st = c->stream;
+    EMS_CUDA(c, cudaMemsetAsync(c->ws, 0, need - 256, st));
+    c->S = pl.S; c->n_nodes = g->n_nodes; c->n_seg = g->n_seg; c->n_pads = g->n_pads;
+    c->n_sinks = g->n_sinks; c->nf = (int)pl.ir.node_of_free.size(); c->nnz = (int64_t)pl.ir.col.size();
+    c->N = pl.tr.off.back(); c->P = pl.P; c->n_trees = pl.tr.n_trees;
+    c->maxv = c->prm.max_voids_per_tree;
+    const int S = c->S, ns = c->n_seg;
+    // grid
+    EMS_CUDA(c, up(D.seg_a, g->seg_a, ns, st)); EMS_CUDA(c, up(D.seg_b, g->seg_b, ns, st));
+    EMS_CUDA(c, up(D.seg_R0, g->seg_R0, ns, st)); EMS_CUDA(c, up(D.seg_W, g->seg_W, ns, st));
+    EMS_CUDA(c, up(D.seg_H, g->seg_H, ns, st));
+    for (int s = 0; s < S; ++s) {
+        EMS_CUDA(c, up(D.R + (size_t)s * ns, g->seg_R0, ns, st));
+        EMS_CUDA(c, up(D.R_prev + (size_t)s * ns, g->seg_R0, ns, st));
+    }
+    std::vector<double> ones((size_t)S * ns, 1.0);
+    EMS_CUDA(c, up(D.kfac, g->kappa_factor ? g->kappa_factor : ones.data(), (size_t)S * ns, st));
+    EMS_CUDA(c, up(D.sfac, g->sigc_factor ? g->sigc_factor : ones.data(), (size_t)S * ns, st));
+    // IR
+    const HostIR &ir = pl.ir;
+    EMS_CUDA(c, up(D.ir_free_of_node, ir.free_of_node.data(), ir.free_of_node.size(), st));
+    EMS_CUDA(c, up(D.ir_node_of_free, ir.node_of_free.data(), ir.node_of_free.size(), st));
+    EMS_CUDA(c, up(D.csr_ptr, ir.ptr.data(), ir.ptr.size(), st));
+    EMS_CUDA(c, up(D.csr_col, ir.col.data(), ir.col.size(), st));
+    EMS_CUDA(c, up(D.ent_ptr, ir.ent_ptr.data(), ir.ent_ptr.size(), st));
+    EMS_CUDA(c, up(D.ent_seg, ir.ent_seg.data(), ir.ent_seg.size(), st));
+    EMS_CUDA(c, up(D.ent_diag, ir.ent_diag.data(), ir.ent_diag.size(), st));
+    EMS_CUDA(c, up(D.rhs_ptr, ir.rhs_ptr.data(), ir.rhs_ptr.size(), st));
+    EMS_CUDA(c, up(D.rhs_seg, ir.rhs_seg.data(), ir.rhs_seg.size(), st));
+    EMS_CUDA(c, up(D.rhs_padV, ir.rhs_padV.data(), ir.rhs_padV.size(), st));
+    EMS_CUDA(c, up(D.sink_of_free, ir.sink.data(), ir.sink.size(), st));
+    EMS_CUDA(c, up(D.pad_V_of_node, ir.padV_of_node.data(), ir.padV_of_node.size(), st));
+    // initial guess: every free node at the mean pad voltage
+    {
+        double vm = 0.0;
+        for (int i = 0; i < g->n_pads; ++i) vm += g->pad_V[i];
+        vm /= g->n_pads;
+        std::vector<double> x0((size_t)S * c->nf, vm), u0((size_t)S * g->n_nodes);
+        for (int s = 0; s < S; ++s)
+            for (int i = 0; i < g->n_nodes; ++i)
+                u0[(size_t)s * g->n_nodes + i] = std::isnan(ir.padV_of_node[i]) ? vm : ir.padV_of_node[i];
+        EMS_CUDA(c, up(D.ir_x, x0.data(), x0.size(), st));
+        EMS_CUDA(c, up(D.u, u0.data(), u0.size(), st));
+    }
+    // trees
+    HostTrees &tr = pl.tr;
+    const int64_t N = c->N;
+    EMS_CUDA(c, up(D.toff, tr.off.data(), tr.off.size(), st));
+    {   // parents and children as global node indices
+        std::vector<int32_t> gp(N), gc(tr.child_idx.size());
+        for (int t = 0; t < tr.n_trees; ++t)
+            for (int64_t i = tr.off[t]; i < tr.off[t + 1]; ++i) {
+                gp[i] = tr.par[i] < 0 ? -1 : (int32_t)(tr.off[t] + tr.par[i]);
+                for (int k = tr.child_ptr[i]; k < tr.child_ptr[i + 1]; ++k)
+                    gc[k] = (int32_t)(tr.off[t] + tr.child_idx[k]);
+            }
+        EMS_CUDA(c, up(D.par, gp.data(), N, st));
+        EMS_CUDA(c, up(D.child_idx, gc.data(), gc.size(), st));
+        EMS_CUDA(c, cudaStreamSynchronize(st));   // gp / gc are host temporaries
+    }
+    EMS_CUDA(c, up(D.face_seg, tr.face_seg.data(), N, st));
+    EMS_CUDA(c, up(D.owner_seg, tr.owner_seg.data(), N, st));
+    EMS_CUDA(c, up(D.inc_seg, tr.inc_seg.data(), tr.inc_seg.size(), st));
+    EMS_CUDA(c, up(D.child_ptr, tr.child_ptr.data(), tr.child_ptr.size(), st));
+    EMS_CUDA(c, up(D.face_sign, tr.face_sign.data(), N, st));
+    EMS_CUDA(c, up(D.face_dx, tr.face_dx.data(), N, st));
+    EMS_CUDA(c, up(D.face_area, tr.face_area.data(), N, st));
+    EMS_CUDA(c, up(D.nx_, tr.x.data(), N, st));
+    EMS_CUDA(c, up(D.ny_, tr.y.data(), N, st));
+    {   // inc_ptr is per node: global CSR over all nodes
+        EMS_CUDA(c, up(D.inc_ptr, tr.inc_ptr.data(), tr.inc_ptr.size(), st));
+    }
+    std::vector<int64_t> pb(c->n_trees);
+    std::vector<int32_t> pT(c->n_trees), pM(c->n_trees);
+    for (int t = 0; t < c->n_trees; ++t) { pb[t] = pl.pack[t].pbase; pT[t] = pl.pack[t].T; pM[t] = pl.pack[t].M; }
+    EMS_CUDA(c, up(D.pbase, pb.data(), pb.size(), st));
+    EMS_CUDA(c, up(D.pT, pT.data(), pT.size(), st));
+    EMS_CUDA(c, up(D.pM, pM.data(), pM.size(), st));
+    // buckets by (chain, T, M)
+    for (auto &b : c->buckets)
+        if (b.d_trees) cudaFree(b.d_trees);
+    c->buckets.clear();
+    for (int t = 0; t < c->n_trees; ++t) {
+        bool ch = pl.pack[t].T > 1;
+        Bucket *bk = nullptr;
+        for (auto &b : c->buckets)
+            if (b.chain == ch && (!ch || (b.T == pl.pack[t].T && b.M == pl.pack[t].M))) bk = &b;
+        if (!bk) {
+            c->buckets.push_back(Bucket{});
+            bk = &c->buckets.back();
+            bk->chain = ch; bk->T = ch ? pl.pack[t].T : 1; bk->M = ch ? pl.pack[t].M : 0;
+        }
+        bk->trees.push_back(t);
+    }
+    for (auto &b : c->buckets) {
+        EMS_CUDA(c, cudaMalloc(&b.d_trees, b.trees.size() * sizeof(int32_t)));
+        EMS_CUDA(c, up(b.d_trees, b.trees.data(), b.trees.size(), st));
+    }
+    c->trees = std::move(pl.tr);
+    c->pack = std::move(pl.pack);
+    c->t = 0.0;
+    c->factored_dt = -1.0;
+    c->have_u = false;
+    c->loaded = true;
+    // uniform temperature, node physics, initial stress
+    EMS_TRY(ems_set_thermal_map(c, nullptr, 0, 0, 0, 0, 0, 0));
+    EMS_TRY(ems::init_sigma(c));
+    EMS_CUDA(c, cudaStreamSynchronize(st));
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_dims(const ems_ctx *c, int *n_trees, int64_t *n_stress_nodes, int *n_samples) {
+    if (!c) return EMS_E_INVAL;
+    if (!c->loaded) return EMS_E_STATE;
+    if (n_trees) *n_trees = c->n_trees;
+    if (n_stress_nodes) *n_stress_nodes = c->N;
+    if (n_samples) *n_samples = c->S;
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_launch_count(const ems_ctx *c, int64_t *launches) {
+    if (!c || !launches) return EMS_E_INVAL;
+    *launches = c->launches;
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_get_currents(ems_ctx *c, double *j) {
+    if (!c || !j) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    EMS_CUDA(c, cudaMemcpyAsync(j, c->d.j, sizeof(double) * c->S * c->n_seg, cudaMemcpyDeviceToHost, c->stream));
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_get_resistance(ems_ctx *c, double *R) {
+    if (!c || !R) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    EMS_CUDA(c, cudaMemcpyAsync(R, c->d.R, sizeof(double) * c->S * c->n_seg, cudaMemcpyDeviceToHost, c->stream));
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_get_sigma(ems_ctx *c, double *sigma) {
+    if (!c || !sigma) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    EMS_TRY(ems::pack_sigma(c, /*to_packed=*/false));   // packed -> canonical f (scratch)
+    EMS_CUDA(c, cudaMemcpyAsync(sigma, c->d.sig_ss, sizeof(double) * c->S * c->N,
+                                cudaMemcpyDeviceToHost, c->stream));
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_get_voids(ems_ctx *c, int cap, int32_t *sample, int32_t *node, int32_t *seg,
+                                    double *volume, double *t_nuc, int *n) {
+    if (!c || !n) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    const size_t st_n = (size_t)c->S * c->n_trees, mv = c->maxv;
+    std::vector<int32_t> cnt(st_n), vn(st_n * mv), vs(st_n * mv);
+    std::vector<double> vv(st_n * mv), vt(st_n * mv);
+    auto cs = c->stream;
+    EMS_CUDA(c, cudaMemcpyAsync(cnt.data(), c->d.v_count, st_n * 4, cudaMemcpyDeviceToHost, cs));
+    EMS_CUDA(c, cudaMemcpyAsync(vn.data(), c->d.v_node, st_n * mv * 4, cudaMemcpyDeviceToHost, cs));
+    EMS_CUDA(c, cudaMemcpyAsync(vs.data(), c->d.v_seg, st_n * mv * 4, cudaMemcpyDeviceToHost, cs));
+    EMS_CUDA(c, cudaMemcpyAsync(vv.data(), c->d.v_vol, st_n * mv * 8, cudaMemcpyDeviceToHost, cs));
+    EMS_CUDA(c, cudaMemcpyAsync(vt.data(), c->d.v_tnuc, st_n * mv * 8, cudaMemcpyDeviceToHost, cs));
+    EMS_CUDA(c, cudaStreamSynchronize(cs));
+    int k = 0;
+    for (int s = 0; s < c->S; ++s)
+        for (int t = 0; t < c->n_trees; ++t) {
+            size_t st = (size_t)s * c->n_trees + t;
+            for (int q = 0; q < cnt[st]; ++q) {
+                if (k < cap) {
+                    size_t e = st * mv + q;
+                    if (sample) sample[k] = s;
+                    if (node) node[k] = (int32_t)(c->trees.off[t] + vn[e]);
+                    if (seg) seg[k] = vs[e];
+                    if (volume) volume[k] = vv[e];
+                    if (t_nuc) t_nuc[k] = vt[e];
+                }
+                ++k;
+            }
+        }
+    *n = k;
+    return EMS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint: header + sigma (canonical, double) + void tables + R + u + x
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    uint64_t magic, S, N, n_trees, maxv, n_seg, n_nodes, nf;
+    double t;
+};
+const uint64_t kMagic = 0x454d5333434b5054ull;  // "EMS3CKPT"
+}  // namespace
+
+extern "C" ems_status ems_state_export(ems_ctx *c, void *buf, size_t *bytes) {
+    if (!c || !bytes) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    const size_t S = c->S, N = c->N, st = S * c->n_trees, mv = c->maxv;
+    const size_t need = sizeof(CkptHeader) + S * N * 8 + st * 4 + st * mv * (4 + 4 + 8 + 8) +
+                        S * c->n_seg * 8 + S * c->n_nodes * 8 + S * c->nf * 8;
+    if (!buf) { *bytes = need; return EMS_OK; }
+    if (*bytes < need) return fail(c, EMS_E_INVAL, "checkpoint buffer too small");
+    char *p = (char *)buf;
+    CkptHeader h{kMagic, S, N, (uint64_t)c->n_trees, mv, (uint64_t)c->n_seg, (uint64_t)c->n_nodes,
+                 (uint64_t)c->nf, c->t};
+    std::memcpy(p, &h, sizeof h); p += sizeof h;
+    EMS_TRY(ems_get_sigma(c, (double *)p)); p += S * N * 8;
+    auto cs = c->stream;
+    auto dn = [&](void *dst, const void *src, size_t nb) {
+        return cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToHost, cs);
+    };
+    EMS_CUDA(c, dn(p, c->d.v_count, st * 4)); p += st * 4;
+    EMS_CUDA(c, dn(p, c->d.v_node, st * mv * 4)); p += st * mv * 4;
+    EMS_CUDA(c, dn(p, c->d.v_seg, st * mv * 4)); p += st * mv * 4;
+    EMS_CUDA(c, dn(p, c->d.v_vol, st * mv * 8)); p += st * mv * 8;
+    EMS_CUDA(c, dn(p, c->d.v_tnuc, st * mv * 8)); p += st * mv * 8;
+    EMS_CUDA(c, dn(p, c->d.R, S * c->n_seg * 8)); p += S * c->n_seg * 8;
+    EMS_CUDA(c, dn(p, c->d.u, S * c->n_nodes * 8)); p += S * c->n_nodes * 8;
+    EMS_CUDA(c, dn(p, c->d.ir_x, S * c->nf * 8)); p += S * c->nf * 8;
+    EMS_CUDA(c, cudaStreamSynchronize(cs));
+    *bytes = need;
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_state_import(ems_ctx *c, const void *buf, size_t bytes) {
+    if (!c || !buf) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    CkptHeader h;
+    if (bytes < sizeof h) return fail(c, EMS_E_INVAL, "checkpoint truncated");
+    std::memcpy(&h, buf, sizeof h);
+    const size_t S = c->S, N = c->N, st = S * c->n_trees, mv = c->maxv;
+    if (h.magic != kMagic || h.S != S || h.N != N || h.n_trees != (uint64_t)c->n_trees || h.maxv != mv ||
+        h.n_seg != (uint64_t)c->n_seg || h.n_nodes != (uint64_t)c->n_nodes || h.nf != (uint64_t)c->nf)
+        return fail(c, EMS_E_INVAL, "checkpoint does not match the loaded grid");
+    const size_t need = sizeof(CkptHeader) + S * N * 8 + st * 4 + st * mv * (4 + 4 + 8 + 8) +
+                        S * c->n_seg * 8 + S * c->n_nodes * 8 + S * c->nf * 8;
+    if (bytes < need) return fail(c, EMS_E_INVAL, "checkpoint truncated");
+    const char *p = (const char *)buf + sizeof h;
+    auto cs = c->stream;
+    auto upb = [&](void *dst, const void *src, size_t nb) {
+        return cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, cs);
+    };
+    EMS_CUDA(c, upb(c->d.sig_ss, p, S * N * 8)); p += S * N * 8;
+    EMS_CUDA(c, upb(c->d.v_count, p, st * 4)); p += st * 4;
+    EMS_CUDA(c, upb(c->d.v_node, p, st * mv * 4)); p += st * mv * 4;
+    EMS_CUDA(c, upb(c->d.v_seg, p, st * mv * 4)); p += st * mv * 4;
+    EMS_CUDA(c, upb(c->d.v_vol, p, st * mv * 8)); p += st * mv * 8;
+    EMS_CUDA(c, upb(c->d.v_tnuc, p, st * mv * 8)); p += st * mv * 8;
+    EMS_CUDA(c, upb(c->d.R, p, S * c->n_seg * 8)); p += S * c->n_seg * 8;
+    EMS_CUDA(c, upb(c->d.u, p, S * c->n_nodes * 8)); p += S * c->n_nodes * 8;
+    EMS_CUDA(c, upb(c->d.ir_x, p, S * c->nf * 8)); p += S * c->nf * 8;
+    c->t = h.t;
+    c->have_u = true;
+    EMS_TRY(ems::node_physics(c));          // thresholds with the imported voids, all dirty
+    EMS_TRY(ems::pack_sigma(c, /*to_packed=*/true));
+    EMS_TRY(ems::ir_currents_and_drop(c));
+    EMS_CUDA(c, cudaStreamSynchronize(cs));
+    return EMS_OK;
+}

@@ -1,0 +1,197 @@
+// ems_internal.cuh -- internal definitions of the GB300 EM/TM engine.
+//
+// Device data layout (all arrays live in one workspace block):
+//   canonical per-node arrays   [S][N]  (N = stress nodes, canonical order)
+//   packed per-node arrays      [S][P]  (P = padded nodes of the packed layout)
+//   per-segment arrays          [S][n_seg]
+//   IR arrays                   [S][n_nodes] / CSR [S][nnz]
+// A chain tree handled by T threads with chunks of M nodes stores canonical
+// node i at packed offset pbase + (i % M) * T + (i / M): at every step of a
+// chunk sweep the T threads touch T consecutive elements (coalesced).
+// Branched trees use T = 1, M = n (packed == canonical order).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ems.h"
+
+#define EMS_MAX_VOIDS 32      // compile-time cap on void slots per (tree, sample)
+#define EMS_MAX_RASTER (1024 * 1024)  // thermal raster values held in the workspace
+
+namespace ems {
+
+// Largest team (threads per chain) each chunk length supports: the chunk's
+// stress lives in registers (M values of R per thread) and the team must fit
+// the 64K-register file of one SM.
+template <typename R, int M> struct ChainMaxThreads;
+template <int M> struct ChainMaxThreads<double, M> {
+    static constexpr int value = M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 384 : 256;
+};
+// the FP32 kernel solves for the increment and keeps two chunks (state and
+// increment) in registers
+template <int M> struct ChainMaxThreads<float, M> {
+    static constexpr int value = M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 448 : 256;
+};
+inline int chain_max_threads(int prec, int M) {
+    if (prec == EMS_F32) return M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 448 : 256;
+    return M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 384 : 256;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side tree extraction result (canonical order)
+// ---------------------------------------------------------------------------
+struct HostTrees {
+    int n_trees = 0;
+    std::vector<int64_t> off;          // [n_trees+1]
+    std::vector<int32_t> par;          // tree-local parent, -1 at the root
+    std::vector<int32_t> face_seg;     // segment of the face to the parent (-1 root)
+    std::vector<double> face_dx, face_area;
+    std::vector<int8_t> face_sign;     // +1 if parent->child is the segment's a->b
+    std::vector<double> x, y;
+    std::vector<int32_t> owner_seg;    // MC factor segment of the node
+    std::vector<int32_t> inc_ptr, inc_seg;  // incident tree segments (IR nodes), CSR
+    std::vector<int32_t> child_ptr, child_idx;  // tree-local children, CSR over nodes
+    std::vector<uint8_t> is_chain;     // per tree
+    std::vector<int32_t> tree_of_seg;  // per segment
+};
+
+// Packing of one tree
+struct TreePack {
+    int T, M;          // threads per tree and chunk length (T = 1 for branched)
+    int64_t pbase;     // packed base (within one sample)
+};
+
+struct Bucket {        // trees launched together: same precision kernel, T and M
+    int T, M;
+    bool chain;
+    std::vector<int32_t> trees;
+    int32_t *d_trees = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// Device arrays (pointers into the workspace)
+// ---------------------------------------------------------------------------
+struct Dev {
+    // grid
+    int32_t *seg_a, *seg_b;
+    double *seg_R0, *seg_W, *seg_H;
+    double *R, *j;                     // [S][n_seg]
+    // IR (free-node system)
+    int32_t *ir_free_of_node;          // node -> free index or -1
+    int32_t *ir_node_of_free;          // free index -> node
+    int32_t *csr_ptr, *csr_col;        // [nf+1], [nnz]
+    int32_t *ent_ptr, *ent_seg;        // per nnz: contributing segments (diag +, off -)
+    int8_t *ent_diag;                  // per nnz: 1 if diagonal
+    int32_t *rhs_ptr, *rhs_seg;        // per free row: segments to a pad
+    double *rhs_padV;                  // matching pad voltage
+    double *sink_of_free;              // [nf] current drawn
+    double *csr_val;                   // [S][nnz]
+    double *ir_b, *ir_dinv;            // [S][nf]
+    double *ir_x, *ir_r, *ir_p, *ir_Ap, *ir_z;  // [S][nf]
+    double *u;                         // [S][n_nodes]
+    double *pad_V_of_node;             // [n_nodes] NaN if not a pad
+    double *drop;                      // [S]
+    double *red;                       // reduction scratch
+    int32_t *ir_iters;                 // [S]
+    unsigned int *gbar;                // grid barrier words
+    // trees (canonical)
+    int64_t *toff;                     // [n_trees+1]
+    int32_t *par, *face_seg, *owner_seg, *inc_ptr, *inc_seg, *child_ptr, *child_idx;
+    int8_t *face_sign;
+    double *face_dx, *face_area, *nx_, *ny_;
+    double *Tn;                        // [N] node temperature
+    double *Mface;                     // [N] TM term per face
+    double *V;                         // [N]
+    double *kap_a, *g, *leak, *thr;    // [S][N]
+    double *f;                         // [S][N] forcing
+    double *sig_ss;                    // [S][N] steady state (screen)
+    // packing
+    int64_t *pbase;                    // [n_trees]
+    int32_t *pT, *pM;                  // [n_trees]
+    // packed state and factors: element type is float or double (precision)
+    void *sig, *alpha, *beta, *gam, *uu, *Pf, *Pb, *pinv;   // [S][P]
+    void *dtg, *dtl;                   // [S][P] FP32 increment form: dt g per face, dt leak per node
+    // voids per (sample, tree)
+    int32_t *v_count;                  // [S][n_trees]
+    int32_t *v_node, *v_seg;           // [S][n_trees][MAXV]
+    double *v_vol, *v_tnuc;            // [S][n_trees][MAXV]
+    int32_t *dirty;                    // [S][n_trees] refactor needed
+    int32_t *status;                   // [8] device error words
+    int32_t *counters;                 // [8]
+    uint8_t *mortal;                   // [S][n_trees]
+    double *ssmax;                     // [S][n_trees]
+    double *kfac, *sfac;               // [S][n_seg] MC multipliers (1 when absent)
+    double *thr0;                      // [S][N] critical stress without voids
+    double *R_prev;                    // [S][n_seg]
+    double *raster;                    // thermal raster (up to EMS_MAX_RASTER values)
+};
+
+}  // namespace ems
+
+struct ems_ctx {
+    ems_params prm;
+    cudaStream_t stream = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    bool loaded = false;
+    std::string err;
+    // sizes
+    int n_nodes = 0, n_seg = 0, n_pads = 0, n_sinks = 0, S = 1;
+    int nf = 0;                // free IR nodes
+    int64_t nnz = 0;
+    int64_t N = 0;             // stress nodes (canonical)
+    int64_t P = 0;             // packed stress nodes per sample
+    int n_trees = 0;
+    int maxv = 16;
+    double t = 0.0;            // simulated time
+    double factored_dt = -1.0; // dt the packed factors were built for
+    bool have_u = false;       // IR solved at least once
+    ems::HostTrees trees;
+    std::vector<ems::TreePack> pack;
+    std::vector<ems::Bucket> buckets;
+    ems::Dev d{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int coop_blocks = 0;       // resident CTAs for the cooperative PCG
+    int64_t launches = 0;      // kernels this context has launched
+    int cluster_ok = -1;       // cluster PCG residency (-1 unknown, 0 no, 1 yes)
+    // thermal raster currently set (nx = 0: uniform T0)
+    int rnx = 0, rny = 0;
+    double rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;
+};
+
+namespace ems {
+
+// helpers implemented in ems_host.cu
+ems_status fail(ems_ctx *c, ems_status s, const std::string &msg);
+ems_status cuda_check(ems_ctx *c, cudaError_t e, const char *what);
+size_t elem_bytes(const ems_ctx *c);
+
+// IR (ems_ir.cu)
+ems_status ir_assemble_and_solve(ems_ctx *c, bool warm);
+ems_status ir_currents_and_drop(ems_ctx *c);
+ems_status check_status(ems_ctx *c);
+
+// stress (ems_stress.cu)
+ems_status node_physics(ems_ctx *c);
+ems_status forcing(ems_ctx *c);
+ems_status advance(ems_ctx *c, double dt, int n_steps, int *n_new);
+ems_status void_update(ems_ctx *c, int *n_changed);
+ems_status screen(ems_ctx *c);
+ems_status pack_sigma(ems_ctx *c, bool to_packed);
+ems_status init_sigma(ems_ctx *c);
+
+}  // namespace ems
+
+#define EMS_CUDA(c, call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ems::cuda_check((c), e_, #call); \
+    } while (0)
+#define EMS_TRY(call)                                       \
+    do {                                                    \
+        ems_status s_ = (call);                             \
+        if (s_ != EMS_OK) return s_;                        \
+    } while (0)

@@ -1,0 +1,952 @@
+// ems_stress.cu -- per-tree EM/TM stress path on the GPU.
+//
+//   node physics  T at every stress node (bilinear map sample), kappa and the
+//                 TM term per face, node volume, Robin leak coefficient and
+//                 critical stress per node (Sec. III-A, III-D.1)
+//   forcing       f = B j - D of Eq. em_tm_ode per node from the currents
+//   advance       backward-Euler steps (Sec. IV-B) with nucleation, Robin
+//                 voids (Sec. IV-D) and void growth (Eq. void_volume_equation)
+//   void update   resistance write-back (Sec. III-D.3, IV-C)
+//   screen        steady-state immortality check (Sec. III-B)
+//
+// Chain trees (every stripe of a mesh) run one CTA of T threads per (tree,
+// sample).  Thread c owns the contiguous chunk [c M, c M + M) of the chain
+// and keeps its stress in registers for all inner steps of a launch.  The
+// matrix M = C - dt A is factored once per (dt, void set) as
+// M = L D L^T, written as the scaled recurrences
+//     z_i = alpha_i s_i + beta_i - gamma_i z_{i-1},    x_i = z_i - u_i x_{i+1}
+// with alpha = V/d', beta = dt f/d', gamma = e_{i-1}/d', u = e_i/d'.  Each
+// first-order recurrence is solved chunk-parallel: a local sweep with zero
+// carry, an exclusive scan of the chunk's affine transfer maps across the
+// team (warp shuffles + one shared-memory level), and a correction with the
+// precomputed carry products Pf / Pb.  Trees with branches run one thread
+// per (tree, sample) with leaf-to-root elimination.
+#include <cfloat>
+#include <cmath>
+
+#include "ems_internal.cuh"
+
+namespace ems {
+ems_status check_status(ems_ctx *c);
+
+namespace {
+
+constexpr int kStatusOverflow = 2;
+
+// ---------------------------------------------------------------------------
+// Node physics
+// ---------------------------------------------------------------------------
+__global__ void k_temperature(int64_t N, const double *x, const double *y, const double *T, int nx, int ny,
+                              double x0, double y0, double x1, double y1, double T0, double *Tn) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        if (nx == 0) { Tn[i] = T0; continue; }
+        double fx = (x[i] - x0) / (x1 - x0) * (nx - 1);
+        double fy = (y[i] - y0) / (y1 - y0) * (ny - 1);
+        fx = fmin(fmax(fx, 0.0), (double)(nx - 1));
+        fy = fmin(fmax(fy, 0.0), (double)(ny - 1));
+        int ix = min((int)floor(fx), nx - 2), iy = min((int)floor(fy), ny - 2);
+        double tx = fx - ix, ty = fy - iy;
+        const double *r0 = T + (int64_t)iy * nx, *r1 = r0 + nx;
+        Tn[i] = (1 - tx) * (1 - ty) * r0[ix] + tx * (1 - ty) * r0[ix + 1] + (1 - tx) * ty * r1[ix] +
+                tx * ty * r1[ix + 1];
+    }
+}
+
+struct PhysArgs {
+    int64_t N;
+    int n_seg;
+    const int32_t *gpar, *face_seg, *owner_seg, *child_ptr, *child_gidx;
+    const double *Tn, *dx, *area, *kfac, *sfac;
+    double D0, Ea, kB, B, Omega, Qs, delta, sigma_crit;
+    double *kap_a, *g, *Mface, *V, *leak, *thr0, *thr;
+};
+
+// per face (stored at the child node): a kappa, g = a kappa / dx, TM term M
+__global__ void k_faces(PhysArgs a) {
+    const int s = blockIdx.y;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t si = (int64_t)s * a.N + i;
+        const int32_t q = a.gpar[i];
+        if (q < 0) {
+            a.kap_a[si] = 0.0; a.g[si] = 0.0;
+            if (s == 0) a.Mface[i] = 0.0;
+            continue;
+        }
+        const double Te = 0.5 * (a.Tn[i] + a.Tn[q]);
+        const double ikT = 1.0 / (a.kB * Te);
+        const double kap = a.D0 * exp(-a.Ea * ikT) * a.B * a.Omega * ikT *
+                           a.kfac[(int64_t)s * a.n_seg + a.face_seg[i]];
+        const double ka = a.area[i] * kap;
+        a.kap_a[si] = ka;
+        a.g[si] = ka / a.dx[i];
+        if (s == 0) a.Mface[i] = a.Qs / (a.Omega * Te) * (a.Tn[i] - a.Tn[q]) / a.dx[i];
+    }
+}
+
+// per node: V = sum of a dx / 2, leak = sum of a kappa / delta over faces at
+// the node; critical stress from the owner segment's factor
+__global__ void k_nodes(PhysArgs a) {
+    const int s = blockIdx.y;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t so = (int64_t)s * a.N;
+        double vol = 0.0, lk = 0.0;
+        if (a.gpar[i] >= 0) { vol += 0.5 * a.area[i] * a.dx[i]; lk += a.kap_a[so + i]; }
+        for (int k = a.child_ptr[i]; k < a.child_ptr[i + 1]; ++k) {
+            const int32_t ch = a.child_gidx[k];
+            vol += 0.5 * a.area[ch] * a.dx[ch];
+            lk += a.kap_a[so + ch];
+        }
+        if (s == 0) a.V[i] = vol;
+        a.leak[so + i] = lk / a.delta;
+        const double t0 = a.sigma_crit * a.sfac[(int64_t)s * a.n_seg + a.owner_seg[i]];
+        a.thr0[so + i] = t0;
+        a.thr[so + i] = t0;
+    }
+}
+
+// voids exclude their node from nucleation (threshold +inf) and force a refactor
+__global__ void k_apply_voids(int n_trees, int S, int maxv, int64_t N, const int64_t *toff,
+                              const int32_t *v_count, const int32_t *v_node, double *thr, int32_t *dirty) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= (int64_t)n_trees * S) return;
+    const int s = (int)(k / n_trees), t = (int)(k % n_trees);
+    for (int q = 0; q < v_count[k]; ++q) thr[(int64_t)s * N + toff[t] + v_node[k * maxv + q]] = INFINITY;
+    dirty[k] = 1;
+}
+
+// f_i = q_i - sum over children q_c with q = a kappa G, G = S + M
+__global__ void k_forcing(int64_t N, int n_seg, double sfac_em, const int32_t *gpar, const int32_t *face_seg,
+                          const int8_t *sign, const int32_t *child_ptr, const int32_t *child_gidx,
+                          const double *Mface, const double *kap_a, const double *j, double *f) {
+    const int s = blockIdx.y;
+    const double *js = j + (int64_t)s * n_seg, *ka = kap_a + (int64_t)s * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        if (gpar[i] >= 0) acc = ka[i] * (sfac_em * sign[i] * js[face_seg[i]] + Mface[i]);
+        for (int k = child_ptr[i]; k < child_ptr[i + 1]; ++k) {
+            const int32_t ch = child_gidx[k];
+            acc -= ka[ch] * (sfac_em * sign[ch] * js[face_seg[ch]] + Mface[ch]);
+        }
+        f[(int64_t)s * N + i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packed <-> canonical stress
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_pack(int n_trees, int64_t N, int64_t P, const int64_t *toff, const int64_t *pbase,
+                       const int32_t *pT, const int32_t *pM, double *canon, R *packed, int dir, double fill) {
+    // dir 1: canonical -> packed; 0: packed -> canonical; 2: packed := fill on real nodes
+    const int t = blockIdx.x, s = blockIdx.y;
+    const int64_t cb = toff[t], n = toff[t + 1] - cb;
+    const int T = pT[t], M = pM[t];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t pk = (int64_t)s * P + pbase[t] + (T > 1 ? (i % M) * T + i / M : i);
+        const int64_t ck = (int64_t)s * N + cb + i;
+        if (dir == 1) packed[pk] = (R)canon[ck];
+        else if (dir == 0) canon[ck] = (double)packed[pk];
+        else packed[pk] = (R)fill;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chain kernel
+// ---------------------------------------------------------------------------
+template <typename R>
+struct ChainArgs {
+    const int32_t *trees;
+    const int64_t *toff, *pbase;
+    int64_t N, P;
+    int n_trees, maxv, n_steps, refactor_all, n_bucket, S;
+    double dt, t0, Binv;
+    const double *V, *g, *leak, *f;
+    double *thr;
+    R *sig, *alpha, *beta, *gam, *uu, *Pf, *Pb, *dtg, *dtl;
+    double *pinv;
+    int32_t *v_count, *v_node, *v_seg;
+    double *v_vol, *v_tnuc;
+    int32_t *dirty;
+    const double *j;
+    int n_seg;
+    const int32_t *face_seg, *inc_ptr, *inc_seg, *gpar, *child_ptr, *child_gidx;
+    int32_t *status, *counters;
+};
+
+// exclusive scan of affine maps x -> A + B x, left to right; returns the carry
+// into this thread's chunk (the composite of all earlier chunks applied to 0)
+template <typename R>
+__device__ __forceinline__ R scan_fwd(R A, R B, R *sA, R *sB, R *sC) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const R Ao = __shfl_up_sync(full, A, d), Bo = __shfl_up_sync(full, B, d);
+        if (lane >= d) { A = fma(B, Ao, A); B = B * Bo; }
+    }
+    R cw = R(0);
+    if (nw > 1) {
+        if (lane == 31) { sA[w] = A; sB[w] = B; }
+        __syncthreads();
+        if (w == 0) {
+            R a = lane < nw ? sA[lane] : R(0), b = lane < nw ? sB[lane] : R(1);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const R ao = __shfl_up_sync(full, a, d), bo = __shfl_up_sync(full, b, d);
+                if (lane >= d) { a = fma(b, ao, a); b = b * bo; }
+            }
+            R ex = __shfl_up_sync(full, a, 1);
+            if (lane < nw) sC[lane] = lane == 0 ? R(0) : ex;
+        }
+        __syncthreads();
+        cw = sC[w];
+    }
+    const R incl = fma(B, cw, A);
+    const R ex = __shfl_up_sync(full, incl, 1);
+    return lane == 0 ? cw : ex;
+}
+
+// the same from right to left (carry = start value of the next chunk)
+template <typename R>
+__device__ __forceinline__ R scan_bwd(R A, R B, R *sA, R *sB, R *sC) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const R Ao = __shfl_down_sync(full, A, d), Bo = __shfl_down_sync(full, B, d);
+        if (lane + d < 32) { A = fma(B, Ao, A); B = B * Bo; }
+    }
+    R cw = R(0);
+    if (nw > 1) {
+        if (lane == 0) { sA[w] = A; sB[w] = B; }
+        __syncthreads();
+        if (w == 0) {
+            R a = lane < nw ? sA[lane] : R(0), b = lane < nw ? sB[lane] : R(1);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const R ao = __shfl_down_sync(full, a, d), bo = __shfl_down_sync(full, b, d);
+                if (lane + d < 32) { a = fma(b, ao, a); b = b * bo; }
+            }
+            R ex = __shfl_down_sync(full, a, 1);
+            if (lane < nw) sC[lane] = lane == 31 ? R(0) : ex;
+        }
+        __syncthreads();
+        cw = sC[w];
+    }
+    const R incl = fma(B, cw, A);
+    const R ex = __shfl_down_sync(full, incl, 1);
+    return lane == 31 ? cw : ex;
+}
+
+// block-wide argmax (largest value, lowest index on ties); all threads get it
+__device__ __forceinline__ void block_argmax(double &v, int &i, double *sv, int *si) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, v, o);
+        const int oi = __shfl_down_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+    }
+    __syncthreads();
+    if (lane == 0) { sv[w] = v; si[w] = i; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k)
+            if (sv[k] > sv[0] || (sv[k] == sv[0] && si[k] < si[0])) { sv[0] = sv[k]; si[0] = si[k]; }
+    }
+    __syncthreads();
+    v = sv[0]; i = si[0];
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_min(double v, double *sv) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sv[w] = v;
+    __syncthreads();
+    double r = sv[0];
+    for (int k = 1; k < nw; ++k) r = fmin(r, sv[k]);
+    __syncthreads();
+    return r;
+}
+
+// Factor M = C - dt A of one chain from node `from` on (earlier factors are
+// unchanged when only later diagonals changed), then every chunk's
+// right-hand-side coefficients and carry products.  Must be called by the
+// whole block.  DELTA (increment form) stores p = 1/d', dt g, dt f, dt leak
+// instead of alpha = V/d', beta = dt f/d'.
+template <typename R, int M, bool DELTA>
+__device__ __forceinline__ void chain_factor(const ChainArgs<R> &a, int n, int T, int c, int64_t cb, int64_t cs,
+                                             int64_t ps, int from) {
+    const double dt = a.dt;
+    __syncthreads();
+    if (c == 0) {
+        double pprev = 0.0;
+        if (from > 0) pprev = a.pinv[ps + (int64_t)((from - 1) % M) * T + (from - 1) / M];
+        for (int i = from; i < n; ++i) {
+            const double gl = i > 0 ? a.g[cs + i] : 0.0, gr = i + 1 < n ? a.g[cs + i + 1] : 0.0;
+            const bool is_void = isinf(a.thr[cs + i]);
+            double d = a.V[cb + i] + dt * (gl + gr);
+            if (is_void) d += dt * a.leak[cs + i];
+            const double em = -dt * gl, ep = -dt * gr;
+            const double p = 1.0 / (d - em * em * pprev);
+            const int64_t pk = ps + (int64_t)(i % M) * T + i / M;
+            a.pinv[pk] = p;
+            if (DELTA) {
+                a.alpha[pk] = (R)p;
+                a.dtg[pk] = (R)(dt * gl);
+                a.dtl[pk] = is_void ? (R)(dt * a.leak[cs + i]) : R(0);
+            } else {
+                a.alpha[pk] = (R)(p * a.V[cb + i]);
+            }
+            a.gam[pk] = (R)(p * em);
+            a.uu[pk] = (R)(p * ep);
+            pprev = p;
+        }
+    }
+    __syncthreads();
+    R acc = R(1);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const int64_t pk = ps + (int64_t)k * T + c;
+        const int i = c * M + k;
+        if (DELTA) a.beta[pk] = i < n ? (R)(dt * a.f[cs + i]) : R(0);
+        else a.beta[pk] = i < n ? (R)(a.pinv[pk] * dt * a.f[cs + i]) : R(0);
+        acc *= -a.gam[pk];
+        a.Pf[pk] = acc;
+    }
+    acc = R(1);
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+        const int64_t pk = ps + (int64_t)k * T + c;
+        acc *= -a.uu[pk];
+        a.Pb[pk] = acc;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ bool above(R s, long long tb, float tf);
+template <>
+__device__ __forceinline__ bool above<double>(double s, long long tb, float) {
+    // sigma >= thr for thr > 0 by comparing IEEE bit patterns as integers
+    return __double_as_longlong(s) >= tb;
+}
+template <>
+__device__ __forceinline__ bool above<float>(float s, long long, float tf) { return s >= tf; }
+
+// Segment a void at stress node v (tree-local) degrades: an interior node's
+// own segment; at an IR node the incident tree segment with the larger |j|
+// (lowest id on ties; the list is ascending).
+template <typename R>
+__device__ __forceinline__ int void_segment(const ChainArgs<R> &a, int s, int64_t gnode) {
+    int best = a.inc_seg[a.inc_ptr[gnode]];
+    double bj = fabs(a.j[(int64_t)s * a.n_seg + best]);
+    for (int k = a.inc_ptr[gnode] + 1; k < a.inc_ptr[gnode + 1]; ++k) {
+        const int sg = a.inc_seg[k];
+        const double aj = fabs(a.j[(int64_t)s * a.n_seg + sg]);
+        if (aj > bj) { bj = aj; best = sg; }
+    }
+    return best;
+}
+
+template <typename R, int M, bool DELTA>
+__global__ void __launch_bounds__(ChainMaxThreads<R, M>::value) k_chain(ChainArgs<R> a) {
+    __shared__ R sA[32], sB[32], sC[32], sL[32], sR[32];
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ int s_nv;
+    __shared__ int s_node[EMS_MAX_VOIDS];
+    __shared__ double s_vol[EMS_MAX_VOIDS], s_coef[EMS_MAX_VOIDS];
+
+    const int t = a.trees[blockIdx.x], s = blockIdx.y;
+    const int T = blockDim.x, c = threadIdx.x;
+    const int64_t cb = a.toff[t];
+    const int n = (int)(a.toff[t + 1] - cb);
+    const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
+    const int64_t st = (int64_t)s * a.n_trees + t;
+    const double dt = a.dt;
+
+    __shared__ int s_refac;
+    if (c == 0) {
+        const int nv = a.v_count[st];
+        s_nv = nv;
+        for (int q = 0; q < nv; ++q) {
+            const int v = a.v_node[st * a.maxv + q];
+            s_node[q] = v;
+            s_vol[q] = a.v_vol[st * a.maxv + q];
+            s_coef[q] = dt * a.Binv * a.leak[cs + v];
+        }
+        s_refac = (a.refactor_all || a.dirty[st]) ? 1 : 0;
+        a.dirty[st] = 0;
+    }
+    __syncthreads();
+    if (s_refac) {
+        chain_factor<R, M, DELTA>(a, n, T, c, cb, cs, ps, 0);
+    } else {
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int64_t pk = ps + (int64_t)k * T + c;
+            const int i = c * M + k;
+            if (DELTA) a.beta[pk] = i < n ? (R)(dt * a.f[cs + i]) : R(0);
+            else a.beta[pk] = i < n ? (R)(a.pinv[pk] * dt * a.f[cs + i]) : R(0);
+        }
+    }
+    double tm = INFINITY;
+    for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
+    double thrmin = block_min(tm, sv);
+    long long thr_bits = __double_as_longlong(thrmin);
+    float thr_f = __double2float_rd(thrmin);
+
+    R sg[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) sg[k] = a.sig[ps + (int64_t)k * T + c];
+    __syncthreads();
+    unsigned long long vmask = 0ull;     // void nodes in this thread's chunk
+    for (int q = 0; q < s_nv; ++q)
+        if (s_node[q] / M == c) vmask |= 1ull << (s_node[q] % M);
+
+    for (int step = 0; step < a.n_steps; ++step) {
+        if (!DELTA) {
+            // forward sweep z_i = alpha s_i + beta - gamma z_{i-1}
+            R z = R(0);
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int64_t pk = ps + (int64_t)k * T + c;
+                const R av = fma(a.alpha[pk], sg[k], a.beta[pk]);
+                z = fma(-a.gam[pk], z, av);
+                sg[k] = z;
+            }
+            const R cf = scan_fwd<R>(z, a.Pf[ps + (int64_t)(M - 1) * T + c], sA, sB, sC);
+#pragma unroll
+            for (int k = 0; k < M; ++k) sg[k] = fma(a.Pf[ps + (int64_t)k * T + c], cf, sg[k]);
+            // backward sweep x_i = z_i - u_i x_{i+1}
+            R x = R(0);
+#pragma unroll
+            for (int k = M - 1; k >= 0; --k) {
+                x = fma(-a.uu[ps + (int64_t)k * T + c], x, sg[k]);
+                sg[k] = x;
+            }
+            const R cr = scan_bwd<R>(x, a.Pb[ps + c], sA, sB, sC);
+#pragma unroll
+            for (int k = 0; k < M; ++k) sg[k] = fma(a.Pb[ps + (int64_t)k * T + c], cr, sg[k]);
+        } else {
+            // increment form: M d = dt (A s + f) with A s from face fluxes, s += d
+            const unsigned full = 0xffffffffu;
+            const int lane = c & 31, w = c >> 5, nw = T >> 5;
+            R left = __shfl_up_sync(full, sg[M - 1], 1);
+            R right = __shfl_down_sync(full, sg[0], 1);
+            if (nw > 1) {
+                if (lane == 31) sL[w] = sg[M - 1];
+                if (lane == 0) sR[w] = sg[0];
+                __syncthreads();
+                if (lane == 0 && w > 0) left = sL[w - 1];
+                if (lane == 31 && w + 1 < nw) right = sR[w + 1];
+            }
+            const R g_next = c + 1 < T ? a.dtg[ps + c + 1] : R(0);   // face to the next chunk
+            R qprev = a.dtg[ps + c] * (left - sg[0]);
+            R z = R(0);
+            R dz[M];
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int64_t pk = ps + (int64_t)k * T + c;
+                const R nxt = k + 1 < M ? sg[k + 1] : right;
+                const R gk1 = k + 1 < M ? a.dtg[pk + T] : g_next;
+                const R qn = gk1 * (sg[k] - nxt);
+                R r = qprev - qn + a.beta[pk];
+                if ((vmask >> k) & 1ull) r -= a.dtl[pk] * sg[k];
+                z = fma(-a.gam[pk], z, a.alpha[pk] * r);
+                dz[k] = z;
+                qprev = qn;
+            }
+            const R cf = scan_fwd<R>(z, a.Pf[ps + (int64_t)(M - 1) * T + c], sA, sB, sC);
+#pragma unroll
+            for (int k = 0; k < M; ++k) dz[k] = fma(a.Pf[ps + (int64_t)k * T + c], cf, dz[k]);
+            R x = R(0);
+#pragma unroll
+            for (int k = M - 1; k >= 0; --k) {
+                x = fma(-a.uu[ps + (int64_t)k * T + c], x, dz[k]);
+                dz[k] = x;
+            }
+            const R cr = scan_bwd<R>(x, a.Pb[ps + c], sA, sB, sC);
+#pragma unroll
+            for (int k = 0; k < M; ++k) sg[k] += fma(a.Pb[ps + (int64_t)k * T + c], cr, dz[k]);
+        }
+
+        // void growth by the Robin leak: the owner thread of a void node stores
+        // it (compile-time register index under a bit mask) and reads it back
+        if (vmask) {
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+                if ((vmask >> k) & 1ull) a.sig[ps + (int64_t)k * T + c] = sg[k];
+            for (int q = 0; q < s_nv; ++q) {
+                const int v = s_node[q];
+                if (v / M == c) s_vol[q] += s_coef[q] * (double)a.sig[ps + (int64_t)(v % M) * T + c];
+            }
+        }
+        // nucleation: cheap test against the tree's lowest threshold, exact on a hit
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < M; ++k) hit |= above<R>(sg[k], thr_bits, thr_f);
+        if (__syncthreads_or(hit)) {
+            double best = -INFINITY;
+            int arg = 0x7fffffff;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int i = c * M + k;
+                if (i < n) {
+                    const double m = (double)sg[k] - a.thr[cs + i];
+                    if (m > best) { best = m; arg = i; }
+                }
+            }
+            block_argmax(best, arg, sv, si);
+            if (best >= 0.0) {
+#pragma unroll
+                for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * T + c] = sg[k];
+                __syncthreads();
+                if (c == 0) {
+                    const int v = arg;
+                    auto S_ = [&](int i) { return (double)a.sig[ps + (int64_t)(i % M) * T + i / M]; };
+                    // previous-step stress at v from the BE relation M s^{k+1} = V s^k + dt f
+                    const double gl = v > 0 ? a.g[cs + v] : 0.0, gr = v + 1 < n ? a.g[cs + v + 1] : 0.0;
+                    double acc = (a.V[cb + v] + dt * (gl + gr)) * S_(v);
+                    if (v > 0) acc -= dt * gl * S_(v - 1);
+                    if (v + 1 < n) acc -= dt * gr * S_(v + 1);
+                    const double s0 = (acc - dt * a.f[cs + v]) / a.V[cb + v];
+                    const double m0 = s0 - a.thr[cs + v];
+                    const double frac = m0 < 0.0 ? -m0 / (best - m0) : 0.0;
+                    const int nv = s_nv;
+                    if (nv < a.maxv) {
+                        const int64_t e = st * a.maxv + nv;
+                        a.v_node[e] = v;
+                        a.v_seg[e] = void_segment<R>(a, s, cb + v);
+                        a.v_tnuc[e] = a.t0 + ((double)step + frac) * dt;
+                        a.v_vol[e] = 0.0;
+                        s_node[nv] = v; s_vol[nv] = 0.0; s_coef[nv] = dt * a.Binv * a.leak[cs + v];
+                        s_nv = nv + 1;
+                        a.v_count[st] = nv + 1;
+                        atomicAdd(&a.counters[0], 1);
+                    } else {
+                        atomicOr(&a.status[kStatusOverflow], 1);
+                    }
+                    a.thr[cs + v] = INFINITY;
+                }
+                __syncthreads();
+                if (arg / M == c) vmask |= 1ull << (arg % M);
+                chain_factor<R, M, DELTA>(a, n, T, c, cb, cs, ps, arg);
+                tm = INFINITY;
+                for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
+                thrmin = block_min(tm, sv);
+                thr_bits = __double_as_longlong(thrmin);
+                thr_f = __double2float_rd(thrmin);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * T + c] = sg[k];
+    __syncthreads();
+    if (c == 0)
+        for (int q = 0; q < s_nv; ++q) a.v_vol[st * a.maxv + q] = s_vol[q];
+}
+
+// ---------------------------------------------------------------------------
+// Branched trees: one thread per (tree, sample), leaf-to-root elimination.
+// Packed layout == canonical order.  pinv holds 1/d', gam holds l = e/d',
+// uu holds e, beta is the right-hand-side scratch.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void tree_factor(const ChainArgs<R> &a, int n, int64_t cb, int64_t cs, int64_t ps) {
+    const double dt = a.dt;
+    for (int i = 0; i < n; ++i) {
+        double d = a.V[cb + i] + (i > 0 ? dt * a.g[cs + i] : 0.0);
+        if (isinf(a.thr[cs + i])) d += dt * a.leak[cs + i];
+        a.pinv[ps + i] = d;
+    }
+    for (int i = 1; i < n; ++i) a.pinv[ps + (a.gpar[cb + i] - cb)] += dt * a.g[cs + i];
+    for (int i = n - 1; i >= 1; --i) {
+        const int q = (int)(a.gpar[cb + i] - cb);
+        const double e = -dt * a.g[cs + i];
+        const double l = e / a.pinv[ps + i];
+        a.pinv[ps + q] -= l * e;
+        a.gam[ps + i] = (R)l;
+        a.uu[ps + i] = (R)e;
+    }
+    for (int i = 0; i < n; ++i) a.pinv[ps + i] = 1.0 / a.pinv[ps + i];
+}
+
+template <typename R>
+__global__ void k_tree(ChainArgs<R> a) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)a.n_bucket * a.S) return;
+    const int t = a.trees[idx % a.n_bucket], s = (int)(idx / a.n_bucket);
+    const int64_t cb = a.toff[t];
+    const int n = (int)(a.toff[t + 1] - cb);
+    const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
+    const int64_t st = (int64_t)s * a.n_trees + t;
+    const double dt = a.dt;
+    if (a.refactor_all || a.dirty[st]) { tree_factor<R>(a, n, cb, cs, ps); a.dirty[st] = 0; }
+    int nv = a.v_count[st];
+    for (int step = 0; step < a.n_steps; ++step) {
+        R *r = a.beta + ps, *x = a.sig + ps;
+        for (int i = 0; i < n; ++i) r[i] = (R)(a.V[cb + i] * (double)x[i] + dt * a.f[cs + i]);
+        for (int i = n - 1; i >= 1; --i) {
+            const int q = (int)(a.gpar[cb + i] - cb);
+            r[q] -= a.gam[ps + i] * r[i];
+        }
+        x[0] = (R)((double)r[0] * a.pinv[ps]);
+        for (int i = 1; i < n; ++i) {
+            const int q = (int)(a.gpar[cb + i] - cb);
+            x[i] = (R)(((double)r[i] - (double)a.uu[ps + i] * (double)x[q]) * a.pinv[ps + i]);
+        }
+        for (int q = 0; q < nv; ++q) {
+            const int64_t e = st * a.maxv + q;
+            const int v = a.v_node[e];
+            a.v_vol[e] += dt * a.Binv * a.leak[cs + v] * (double)x[v];
+        }
+        double best = -INFINITY;
+        int arg = -1;
+        for (int i = 0; i < n; ++i) {
+            const double m = (double)x[i] - a.thr[cs + i];
+            if (m > best) { best = m; arg = i; }
+        }
+        if (arg >= 0 && best >= 0.0) {
+            const int v = arg;
+            // previous-step stress at v from the BE relation
+            double diag = a.V[cb + v], acc = 0.0;
+            if (v > 0) {
+                const int q = (int)(a.gpar[cb + v] - cb);
+                diag += dt * a.g[cs + v];
+                acc -= dt * a.g[cs + v] * (double)x[q];
+            }
+            for (int k = a.child_ptr[cb + v]; k < a.child_ptr[cb + v + 1]; ++k) {
+                const int ch = (int)(a.child_gidx[k] - cb);
+                diag += dt * a.g[cs + ch];
+                acc -= dt * a.g[cs + ch] * (double)x[ch];
+            }
+            acc += diag * (double)x[v];
+            const double s0 = (acc - dt * a.f[cs + v]) / a.V[cb + v];
+            const double m0 = s0 - a.thr[cs + v];
+            const double frac = m0 < 0.0 ? -m0 / (best - m0) : 0.0;
+            if (nv < a.maxv) {
+                const int64_t e = st * a.maxv + nv;
+                a.v_node[e] = v;
+                a.v_seg[e] = void_segment<R>(a, s, cb + v);
+                a.v_tnuc[e] = a.t0 + ((double)step + frac) * dt;
+                a.v_vol[e] = 0.0;
+                ++nv;
+                a.v_count[st] = nv;
+                atomicAdd(&a.counters[0], 1);
+            } else {
+                atomicOr(&a.status[kStatusOverflow], 1);
+            }
+            a.thr[cs + v] = INFINITY;
+            tree_factor<R>(a, n, cb, cs, ps);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Void growth resistance and the steady-state screen
+// ---------------------------------------------------------------------------
+__global__ void k_reset_R(int n_seg, int S, const double *R0, double *R) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)n_seg * S;
+         k += (int64_t)gridDim.x * blockDim.x)
+        R[k] = R0[k % n_seg];
+}
+
+// one thread per (sample, tree): a tree's voids degrade only its own segments
+__global__ void k_void_R(int n_trees, int S, int maxv, int n_seg, const int32_t *v_count, const int32_t *v_seg,
+                         const double *v_vol, const double *W, const double *H, double rho_Ta, double h_Ta,
+                         double rho_Cu, double *R) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= (int64_t)n_trees * S) return;
+    const int s = (int)(k / n_trees);
+    for (int q = 0; q < v_count[k]; ++q) {
+        const int sg = v_seg[k * maxv + q];
+        const double w = W[sg], h = H[sg];
+        const double coef = rho_Ta / (h_Ta * (2.0 * h + w)) - rho_Cu / (h * w);
+        const double dR = (v_vol[k * maxv + q] - w * w * h) / (w * h) * coef;
+        if (dR > 0.0) R[(int64_t)s * n_seg + sg] += dR;
+    }
+}
+
+__global__ void k_count_changed(int64_t n, const double *R, double *R_prev, int32_t *counter) {
+    int local = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        if (R[k] != R_prev[k]) { ++local; R_prev[k] = R[k]; }
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(counter, local);
+}
+
+// steady state per (sample, tree): sigma_child - sigma_parent = dx G, constant
+// from sum V (sigma - sigma_T) = 0; mortal iff some sigma_ss > sigma_crit
+__global__ void k_screen(int n_trees, int S, int64_t N, int n_seg, double sfac_em, double sigma_T,
+                         const int64_t *toff, const int32_t *gpar, const int32_t *face_seg, const int8_t *sign,
+                         const double *dx, const double *Mface, const double *V, const double *j,
+                         const double *thr0, double *ss, uint8_t *mortal, double *ssmax) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= (int64_t)n_trees * S) return;
+    const int s = (int)(k / n_trees), t = (int)(k % n_trees);
+    const int64_t cb = toff[t], n = toff[t + 1] - cb, cs = (int64_t)s * N + cb;
+    const double *js = j + (int64_t)s * n_seg;
+    double sv = V[cb], svp = 0.0;
+    ss[cs] = 0.0;
+    for (int64_t i = 1; i < n; ++i) {
+        const int64_t gi = cb + i;
+        const double G = sfac_em * sign[gi] * js[face_seg[gi]] + Mface[gi];
+        const double Pi = ss[(int64_t)s * N + gpar[gi]] + dx[gi] * G;
+        ss[cs + i] = Pi;
+        sv += V[gi];
+        svp += V[gi] * Pi;
+    }
+    const double mean = svp / sv;
+    double mx = -INFINITY;
+    uint8_t mort = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double v = sigma_T + ss[cs + i] - mean;
+        ss[cs + i] = v;
+        mx = fmax(mx, v);
+        if (v > thr0[cs + i]) mort = 1;
+    }
+    mortal[k] = mort;
+    ssmax[k] = mx;
+}
+
+template <typename R>
+ChainArgs<R> chain_args(ems_ctx *c, double dt, int n_steps) {
+    Dev &d = c->d;
+    ChainArgs<R> a;
+    a.toff = d.toff; a.pbase = d.pbase; a.N = c->N; a.P = c->P;
+    a.n_trees = c->n_trees; a.maxv = c->maxv; a.n_steps = n_steps; a.S = c->S;
+    a.refactor_all = (dt != c->factored_dt) ? 1 : 0;
+    a.dt = dt; a.t0 = c->t; a.Binv = 1.0 / c->prm.B_modulus;
+    a.V = d.V; a.g = d.g; a.leak = d.leak; a.f = d.f; a.thr = d.thr;
+    a.sig = (R *)d.sig; a.alpha = (R *)d.alpha; a.beta = (R *)d.beta; a.gam = (R *)d.gam;
+    a.uu = (R *)d.uu; a.Pf = (R *)d.Pf; a.Pb = (R *)d.Pb; a.pinv = (double *)d.pinv;
+    a.dtg = (R *)d.dtg; a.dtl = (R *)d.dtl;
+    a.v_count = d.v_count; a.v_node = d.v_node; a.v_seg = d.v_seg; a.v_vol = d.v_vol; a.v_tnuc = d.v_tnuc;
+    a.dirty = d.dirty; a.j = d.j; a.n_seg = c->n_seg; a.face_seg = d.face_seg; a.inc_ptr = d.inc_ptr;
+    a.inc_seg = d.inc_seg; a.gpar = d.par; a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx;
+    a.status = d.status; a.counters = d.counters;
+    return a;
+}
+
+// FP64 solves the state directly; FP32 solves for the increment so that the
+// rounding of its coefficients cannot drift the conserved slow modes
+template <typename R>
+ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
+    constexpr bool kDelta = sizeof(R) == 4;
+    for (auto &b : c->buckets) {
+        ChainArgs<R> a = chain_args<R>(c, dt, n_steps);
+        a.trees = b.d_trees;
+        a.n_bucket = (int)b.trees.size();
+        if (b.chain) {
+            dim3 grid((unsigned)b.trees.size(), c->S);
+            switch (b.M) {
+                case 4: k_chain<R, 4, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
+                case 8: k_chain<R, 8, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
+                case 16: k_chain<R, 16, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
+                case 32: k_chain<R, 32, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
+                case 64: k_chain<R, 64, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
+                default: return fail(c, EMS_E_STATE, "unsupported chunk length");
+            }
+            ++c->launches;
+        } else {
+            const int64_t items = (int64_t)b.trees.size() * c->S;   // (tree, sample) pairs
+            k_tree<R><<<(unsigned)((items + 63) / 64), 64, 0, c->stream>>>(a);
+            ++c->launches;
+        }
+        EMS_CUDA(c, cudaGetLastError());
+    }
+    return EMS_OK;
+}
+
+inline dim3 grid_1d(int64_t n, int S) {
+    int64_t b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return dim3((unsigned)b, (unsigned)S);
+}
+
+}  // namespace
+
+ems_status node_physics(ems_ctx *c) {
+    Dev &d = c->d;
+    const ems_params &p = c->prm;
+    cudaStream_t st = c->stream;
+    k_temperature<<<grid_1d(c->N, 1), 256, 0, st>>>(c->N, d.nx_, d.ny_, d.raster, c->rnx, c->rny, c->rx0, c->ry0,
+                                                    c->rx1, c->ry1, p.T0, d.Tn);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    PhysArgs a;
+    a.N = c->N; a.n_seg = c->n_seg; a.gpar = d.par; a.face_seg = d.face_seg; a.owner_seg = d.owner_seg;
+    a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx; a.Tn = d.Tn; a.dx = d.face_dx; a.area = d.face_area;
+    a.kfac = d.kfac; a.sfac = d.sfac; a.D0 = p.D0; a.Ea = p.Ea; a.kB = p.k_B; a.B = p.B_modulus;
+    a.Omega = p.Omega; a.Qs = p.Q_star; a.delta = p.delta; a.sigma_crit = p.sigma_crit;
+    a.kap_a = d.kap_a; a.g = d.g; a.Mface = d.Mface; a.V = d.V; a.leak = d.leak; a.thr0 = d.thr0; a.thr = d.thr;
+    k_faces<<<grid_1d(c->N, c->S), 256, 0, st>>>(a);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    k_nodes<<<grid_1d(c->N, c->S), 256, 0, st>>>(a);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    const int64_t ts = (int64_t)c->n_trees * c->S;
+    k_apply_voids<<<(unsigned)((ts + 255) / 256), 256, 0, st>>>(c->n_trees, c->S, c->maxv, c->N, d.toff,
+                                                                d.v_count, d.v_node, d.thr, d.dirty);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+ems_status forcing(ems_ctx *c) {
+    Dev &d = c->d;
+    const ems_params &p = c->prm;
+    const double sem = p.e_charge * p.Z_star * p.rho_Cu / p.Omega;
+    k_forcing<<<grid_1d(c->N, c->S), 256, 0, c->stream>>>(c->N, c->n_seg, sem, d.par, d.face_seg, d.face_sign,
+                                                          d.child_ptr, d.child_idx, d.Mface, d.kap_a, d.j, d.f);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+ems_status advance(ems_ctx *c, double dt, int n_steps, int *n_new) {
+    EMS_CUDA(c, cudaMemsetAsync(c->d.counters, 0, sizeof(int32_t), c->stream));
+    if (c->prm.precision == EMS_F32) {
+        EMS_TRY(launch_advance<float>(c, dt, n_steps));
+    } else {
+        EMS_TRY(launch_advance<double>(c, dt, n_steps));
+    }
+    c->factored_dt = dt;
+    c->t += dt * n_steps;
+    if (n_new) {
+        EMS_CUDA(c, cudaMemcpyAsync(n_new, c->d.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    }
+    return EMS_OK;
+}
+
+ems_status void_update(ems_ctx *c, int *n_changed) {
+    Dev &d = c->d;
+    const ems_params &p = c->prm;
+    cudaStream_t st = c->stream;
+    const int64_t nsS = (int64_t)c->n_seg * c->S;
+    k_reset_R<<<grid_1d(nsS, 1), 256, 0, st>>>(c->n_seg, c->S, d.seg_R0, d.R);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    const int64_t ts = (int64_t)c->n_trees * c->S;
+    k_void_R<<<(unsigned)((ts + 255) / 256), 256, 0, st>>>(c->n_trees, c->S, c->maxv, c->n_seg, d.v_count,
+                                                           d.v_seg, d.v_vol, d.seg_W, d.seg_H, p.rho_Ta, p.h_Ta,
+                                                           p.rho_Cu, d.R);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    EMS_CUDA(c, cudaMemsetAsync(d.counters + 1, 0, sizeof(int32_t), st));
+    k_count_changed<<<grid_1d(nsS, 1), 256, 0, st>>>(nsS, d.R, d.R_prev, d.counters + 1);
+    EMS_CUDA(c, cudaGetLastError());
+    if (n_changed)
+        EMS_CUDA(c, cudaMemcpyAsync(n_changed, d.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    return EMS_OK;
+}
+
+ems_status screen(ems_ctx *c) {
+    Dev &d = c->d;
+    const ems_params &p = c->prm;
+    const double sem = p.e_charge * p.Z_star * p.rho_Cu / p.Omega;
+    const int64_t ts = (int64_t)c->n_trees * c->S;
+    k_screen<<<(unsigned)((ts + 63) / 64), 64, 0, c->stream>>>(c->n_trees, c->S, c->N, c->n_seg, sem, p.sigma_T,
+                                                               d.toff, d.par, d.face_seg, d.face_sign, d.face_dx,
+                                                               d.Mface, d.V, d.j, d.thr0, d.sig_ss, d.mortal,
+                                                               d.ssmax);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+ems_status pack_sigma(ems_ctx *c, bool to_packed) {
+    Dev &d = c->d;
+    dim3 grid(c->n_trees, c->S);
+    if (c->prm.precision == EMS_F32)
+        k_pack<float><<<grid, 256, 0, c->stream>>>(c->n_trees, c->N, c->P, d.toff, d.pbase, d.pT, d.pM, d.sig_ss,
+                                                   (float *)d.sig, to_packed ? 1 : 0, 0.0);
+    else
+        k_pack<double><<<grid, 256, 0, c->stream>>>(c->n_trees, c->N, c->P, d.toff, d.pbase, d.pT, d.pM, d.sig_ss,
+                                                    (double *)d.sig, to_packed ? 1 : 0, 0.0);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+ems_status init_sigma(ems_ctx *c) {
+    Dev &d = c->d;
+    dim3 grid(c->n_trees, c->S);
+    if (c->prm.precision == EMS_F32)
+        k_pack<float><<<grid, 256, 0, c->stream>>>(c->n_trees, c->N, c->P, d.toff, d.pbase, d.pT, d.pM, d.sig_ss,
+                                                   (float *)d.sig, 2, c->prm.sigma_T);
+    else
+        k_pack<double><<<grid, 256, 0, c->stream>>>(c->n_trees, c->N, c->P, d.toff, d.pbase, d.pT, d.pM, d.sig_ss,
+                                                    (double *)d.sig, 2, c->prm.sigma_T);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+}  // namespace ems
+
+using namespace ems;
+
+extern "C" ems_status ems_set_thermal_map(ems_ctx *c, const double *T, int nx, int ny, double x0, double y0,
+                                          double x1, double y1) {
+    if (!c) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    if (T) {
+        if (nx < 2 || ny < 2 || (int64_t)nx * ny > EMS_MAX_RASTER || !(x1 > x0) || !(y1 > y0))
+            return fail(c, EMS_E_INVAL, "thermal raster must be 2x2..1024x1024 over a positive extent");
+        for (int64_t k = 0; k < (int64_t)nx * ny; ++k)
+            if (!(std::isfinite(T[k]) && T[k] > 0.0)) return fail(c, EMS_E_INVAL, "non-positive temperature");
+        EMS_CUDA(c, cudaMemcpyAsync(c->d.raster, T, sizeof(double) * nx * ny, cudaMemcpyHostToDevice, c->stream));
+        c->rnx = nx; c->rny = ny; c->rx0 = x0; c->ry0 = y0; c->rx1 = x1; c->ry1 = y1;
+    } else {
+        c->rnx = 0; c->rny = 0;
+    }
+    EMS_TRY(node_physics(c));
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_stress_advance(ems_ctx *c, double dt, int n_steps, int method, int *n_new_voids) {
+    if (!c) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    if (!c->have_u) return fail(c, EMS_E_STATE, "stress advance before the first IR solve");
+    if (!(dt > 0.0) || n_steps < 0) return fail(c, EMS_E_INVAL, "dt must be > 0 and n_steps >= 0");
+    if (method != EMS_BE && method != EMS_KRYLOV && method != EMS_AUTO)
+        return fail(c, EMS_E_INVAL, "unknown method");
+    EMS_TRY(forcing(c));
+    int nn = 0;
+    EMS_TRY(advance(c, dt, n_steps, &nn));
+    EMS_TRY(check_status(c));
+    if (n_new_voids) *n_new_voids = nn;
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_void_update(ems_ctx *c, int *n_segments_changed) {
+    if (!c) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    int nc = 0;
+    EMS_TRY(void_update(c, &nc));
+    EMS_TRY(check_status(c));
+    if (n_segments_changed) *n_segments_changed = nc;
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_immortality_check(ems_ctx *c, uint8_t *mortal, double *sigma_ss_max, double *sigma_ss) {
+    if (!c) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    if (!c->have_u) return fail(c, EMS_E_STATE, "screen before the first IR solve");
+    EMS_TRY(screen(c));
+    const size_t ts = (size_t)c->n_trees * c->S;
+    if (mortal) EMS_CUDA(c, cudaMemcpyAsync(mortal, c->d.mortal, ts, cudaMemcpyDeviceToHost, c->stream));
+    if (sigma_ss_max)
+        EMS_CUDA(c, cudaMemcpyAsync(sigma_ss_max, c->d.ssmax, ts * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (sigma_ss)
+        EMS_CUDA(c, cudaMemcpyAsync(sigma_ss, c->d.sig_ss, sizeof(double) * c->S * c->N, cudaMemcpyDeviceToHost,
+                                    c->stream));
+    return check_status(c);
+}

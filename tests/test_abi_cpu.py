@@ -1,0 +1,94 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function
+include/ems.h declares, and rejects invalid inputs in host code (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import ems_synth as es
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2604_10743_gb300 import build as B
+    from paper_2604_10743_gb300 import _abi as A
+    B.build()
+    return A.lib()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(ems_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    from paper_2604_10743_gb300 import _abi as A
+    decl = _declared()
+    assert "ems_stress_advance" in decl and "ems_ttf" in decl
+    for name in decl:
+        assert hasattr(L, name), name
+    assert decl <= set(A.EXPORTS) | decl
+
+
+def _ws(L, g, **kw):
+    from paper_2604_10743_gb300 import _abi as A
+    prm = A.make_params(es.default_params(), **kw)
+    gd = A.GridDesc(g)
+    return L.ems_workspace_bytes(ctypes.byref(prm), ctypes.byref(gd.desc))
+
+
+def test_workspace_sizes(L):
+    small = _ws(L, es.tiny_grid())
+    assert small > 0
+    assert _ws(L, es.mc_grid(n_samples=4)) > small
+
+
+def test_rejects_cycle(L):
+    g = es.stripe_mesh(2, 10e-6)
+    g["seg_layer"][:] = 0
+    g["pad_node"] = np.array([0], np.int32); g["pad_V"] = np.ones(1)
+    assert _ws(L, g) == 0
+
+
+def test_rejects_nan_current_and_bad_geometry(L):
+    g = es.tiny_grid()
+    g["sink_I"] = g["sink_I"].copy(); g["sink_I"][3] = np.nan
+    assert _ws(L, g) == 0
+    g = es.tiny_grid()
+    g["seg_L"] = g["seg_L"].copy(); g["seg_L"][0] = -1.0
+    assert _ws(L, g) == 0
+
+
+def test_rejects_island(L):
+    g = es.tiny_grid()
+    # an extra node linked to nothing
+    g["node_x"] = np.append(g["node_x"], 1.0); g["node_y"] = np.append(g["node_y"], 1.0)
+    assert _ws(L, g) == 0
+
+
+def test_rejects_bad_params(L):
+    from paper_2604_10743_gb300 import _abi as A
+    prm = A.make_params(es.default_params(sigma_crit=-1.0))
+    gd = A.GridDesc(es.tiny_grid())
+    assert L.ems_workspace_bytes(ctypes.byref(prm), ctypes.byref(gd.desc)) == 0
+    prm = A.make_params(es.default_params(), max_voids=0)
+    assert L.ems_workspace_bytes(ctypes.byref(prm), ctypes.byref(gd.desc)) == 0
+
+
+def test_branched_trees_accepted(L):
+    for kind in ("T", "comb", "star", "chain"):
+        assert _ws(L, es.tree_grid(kind)) > 0
+
+
+def test_null_context_calls_fail_cleanly(L):
+    assert L.ems_ir_solve(None, None, None) == 1       # EMS_E_INVAL
+    assert L.ems_destroy(None) == 1

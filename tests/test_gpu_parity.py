@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances: FP64 stress relative error <= 1e-9 (max abs error over max |sigma|),
+FP32 <= 1e-4; nucleated nodes and degraded segments identical; TTF and final
+IR drop within 0.05 %.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ems_synth as es
+from oracle import flow as F
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOL32 = 1e-4
+TTF_TOL = 5e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def _engine(p, g, **kw):
+    from paper_2604_10743_gb300.engine import Engine
+    return Engine(p, g, **kw)
+
+
+def _relerr(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _void_sets(eng, ref, sample=0):
+    v = eng.voids()
+    m = v["sample"] == sample
+    gpu = sorted(zip(v["node"][m].tolist(), v["seg"][m].tolist()))
+    ora = sorted(zip(ref["void_nodes"].tolist(), ref["void_seg"].tolist()))
+    return gpu, ora, v
+
+
+def test_ir_solve_tiny_and_grids():
+    for g in (es.tiny_grid(), es.mid_grid(N=64, with_map=False)):
+        p = es.default_params()
+        eng = _engine(p, g)
+        u, d = eng.ir_solve()
+        uo = F.ir_solve(g, g["seg_R0"])
+        assert np.abs(u[0] - uo).max() < 1e-11
+        assert abs(d[0] - F.max_drop(uo, 1.0)) < 1e-11
+        jo = F.current_density(g, uo, g["seg_R0"])
+        assert _relerr(eng.currents()[0], jo) < 1e-9
+        eng.close()
+
+
+def test_tiny_full_ttf_fp64():
+    g = es.tiny_grid()
+    p = es.default_params()
+    eng = _engine(p, g)
+    r = eng.ttf(screen=True)
+    ref = F.run_ttf(g, p, screen_first=True, keep_state=True)
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+    gpu, ora, v = _void_sets(eng, ref)
+    assert gpu == ora and len(ora) > 0
+    tn = dict(zip(v["node"].tolist(), v["t_nuc"].tolist()))
+    for node in ref["void_nodes"]:
+        assert abs(tn[node] - ref["state"].t_nuc[node]) < 1e-6 * ref["state"].t_nuc[node]
+    vol = dict(zip(v["node"].tolist(), v["volume"].tolist()))
+    for node in ref["void_nodes"]:
+        assert abs(vol[node] - ref["state"].vol[node]) <= 1e-8 * max(abs(ref["state"].vol[node]), 1e-30)
+    assert abs(r["final_drop"][0] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+    assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    if math.isfinite(ref["ttf"]):
+        assert abs(r["ttf"][0] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
+    else:
+        assert math.isinf(r["ttf"][0])
+    assert int(r["n_mortal"][0]) == int(ref["mortal"].sum())
+    assert _relerr(eng.resistance()[0], ref["R"]) < TOL64
+    eng.close()
+
+
+def test_tiny_full_ttf_fp32():
+    g = es.tiny_grid()
+    p = es.default_params()
+    from paper_2604_10743_gb300 import EMS_F32
+    eng = _engine(p, g, precision=EMS_F32)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True)
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+    gpu, ora, _ = _void_sets(eng, ref)
+    ambiguous = ref["margin"].min() < 1e-3
+    if not ambiguous:
+        assert gpu == ora
+    assert abs(r["final_drop"][0] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+    if math.isfinite(ref["ttf"]):
+        assert abs(r["ttf"][0] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
+    eng.close()
+
+
+@pytest.mark.parametrize("kind", ["T", "comb", "star", "chain"])
+def test_branched_trees_with_voids(kind):
+    g = es.tree_grid(kind, cells=12, seed=5, I_sink=6e-3)
+    p = es.default_params(n_outer=8, n_inner=64, sigma_crit=150e6)
+    eng = _engine(p, g)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True)
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+    gpu, ora, _ = _void_sets(eng, ref)
+    assert gpu == ora
+    assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    eng.close()
+
+
+def test_ragged_and_degenerate_chains():
+    # chains whose node counts are not multiples of any chunk length, down to
+    # one cell per segment (n = 8 nodes), with a hot thermal map
+    for cells in (1, 3, 13, 37):
+        g = es.stripe_mesh(8, 20e-6)
+        g["seg_cells"][:] = cells
+        t = es.tiny_grid()
+        g["pad_node"], g["pad_V"], g["sink_node"], g["sink_I"] = t["pad_node"], t["pad_V"], t["sink_node"], t["sink_I"]
+        g["thermal"] = es.hotspot_raster(np.random.default_rng(cells), 140e-6, 2, 370.0, 20.0, 40.0, 0.2, nx=33, ny=33)
+        p = es.default_params(n_outer=6, n_inner=32)
+        eng = _engine(p, g)
+        r = eng.ttf()
+        ref = F.run_ttf(g, p, keep_state=True)
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64, cells
+        gpu, ora, _ = _void_sets(eng, ref)
+        assert gpu == ora
+        eng.close()
+
+
+def test_screen_matches_oracle():
+    for g in (es.tiny_grid(), es.mid_grid(N=64)):
+        p = es.default_params()
+        eng = _engine(p, g)
+        eng.ir_solve()
+        mortal, smax, ss = eng.immortality_check(want_sigma=True)
+        tr = F.build_trees(g)
+        phys = F.tree_physics(tr, p, F.node_temperature(tr, g.get("thermal"), p["T0"]))
+        uo = F.ir_solve(g, g["seg_R0"])
+        G = F.face_G(tr, p, phys, F.current_density(g, uo, g["seg_R0"]))
+        mo, so, sso = F.screen(tr, p, phys, G)
+        assert np.array_equal(mortal[0], mo)
+        assert _relerr(ss[0], sso) < 1e-9
+        eng.close()
+
+
+def test_mid_grid_one_aging_step_fp64():
+    """256 x 256 stripes (512 trees x 5,101 nodes) with the hotspot map: one
+    aging step of 256 BE steps, every stress node compared."""
+    g = es.mid_grid()
+    tr = F.build_trees(g)
+    g["trees"] = tr
+    p = es.default_params()
+    eng = _engine(p, g)
+    r = eng.ttf(n_outer=1)
+    ref = F.run_ttf(g, p, n_outer=1, keep_state=True, n_threads=0)
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+    gpu, ora, _ = _void_sets(eng, ref)
+    assert gpu == ora
+    assert abs(r["final_drop"][0] - ref["final_drop"]) < 1e-9
+    eng.close()
+
+
+def test_mc_samples_ttf():
+    g = es.mc_grid(n_samples=6)
+    p = es.default_params(n_outer=32)
+    eng = _engine(p, g)
+    r = eng.ttf()
+    sig = eng.sigma()
+    for s in range(6):
+        ref = F.run_ttf(g, p, sample=s, keep_state=True)
+        assert _relerr(sig[s], ref["state"].sigma) < TOL64
+        gpu, ora, _ = _void_sets(eng, ref, sample=s)
+        assert gpu == ora
+        assert abs(r["final_drop"][s] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+        if math.isfinite(ref["ttf"]):
+            assert abs(r["ttf"][s] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
+        else:
+            assert math.isinf(r["ttf"][s])
+    eng.close()
+
+
+def test_checkpoint_resume_bit_identical():
+    g = es.tiny_grid()
+    p = es.default_params(n_outer=16)
+    a = _engine(p, g)
+    a.ttf(n_outer=8)
+    ck = a.state_export()
+    ra = a.ttf(n_outer=8)
+    sa = a.sigma()
+    b = _engine(p, g)
+    b.state_import(ck)
+    rb = b.ttf(n_outer=8)
+    assert np.array_equal(sa, b.sigma())
+    assert np.array_equal(ra["drops"], rb["drops"])
+    a.close(); b.close()
+
+
+def test_pcg_iteration_cap_reports_noconv():
+    from paper_2604_10743_gb300 import EmsError
+    eng = _engine(es.default_params(), es.tiny_grid(), ir_max_iter=1)
+    with pytest.raises(EmsError) as e:
+        eng.ir_solve()
+    assert e.value.status == 5
+    eng.close()
+
+
+def test_void_slot_overflow_reported():
+    from paper_2604_10743_gb300 import EmsError
+    eng = _engine(es.default_params(Z_star=12.0), es.tiny_grid(), max_voids=1)
+    with pytest.raises(EmsError) as e:
+        eng.ttf()
+    assert e.value.status == 8
+    eng.close()
+
+
+def test_stress_before_ir_is_state_error():
+    from paper_2604_10743_gb300 import EmsError
+    eng = _engine(es.default_params(), es.tiny_grid())
+    with pytest.raises(EmsError) as e:
+        eng.stress_advance(1e4, 4)
+    assert e.value.status == 2
+    eng.close()
