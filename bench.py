@@ -223,6 +223,8 @@ def run_mine(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MB buffer written between timed iterations (L2 flush)"},
         "ttf_s": float(res["ttf"][0]), "final_drop": float(res["final_drop"][0]),
+        "stress_node_steps_per_s": node_steps * args.steps / (stress_ms / 1e3),
+        "ir_ms_per_step": res["ir_ms"], "ir_iterations_per_step": res["ir_iterations"],
         "ttf_wall_ms": ms / args.steps, "plain_fp64": plain,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }

@@ -217,6 +217,7 @@ typedef struct {
     double node_steps;    /* out: sum over trees and samples of nodes x BE steps */
     double stress_ms;     /* out: device time of the stress kernels (ms) */
     double ir_ms;         /* out: device time of the IR solves (ms) */
+    double ir_iterations; /* out: PCG iterations summed over the IR solves and samples */
 } ems_ttf_result;
 
 /*

@@ -52,7 +52,8 @@ class EmsTtfOpts(ctypes.Structure):
 class EmsTtfResult(ctypes.Structure):
     _fields_ = [("ttf", c_double_p), ("drop0", c_double_p), ("final_drop", c_double_p),
                 ("n_voids", c_int32_p), ("n_mortal", c_int32_p), ("drops", c_double_p),
-                ("node_steps", ctypes.c_double), ("stress_ms", ctypes.c_double), ("ir_ms", ctypes.c_double)]
+                ("node_steps", ctypes.c_double), ("stress_ms", ctypes.c_double), ("ir_ms", ctypes.c_double),
+                ("ir_iterations", ctypes.c_double)]
 
 
 _LIB = None

@@ -255,13 +255,16 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
 }
 
 // Chunk length for a chain of n nodes: the smallest power of two in [4, 64]
-// that keeps the team at or below 128 threads, then T = ceil(n / M) rounded
-// up to whole warps.  A team larger than the chunk length allows (register
-// file) moves to a longer chunk; chains too long for any chunk fall back to
-// the single-thread tree path.  EMS_CHAIN_M (environment) pins M for tuning.
+// that keeps the team at or below a target size (FP32: 448 threads, the
+// state chunk is the only per-node register array; FP64: 192, the state form
+// keeps more per thread), then T = ceil(n / M) rounded up to whole warps.  A
+// team larger than the chunk length allows moves to a longer chunk; chains
+// too long for any chunk fall back to the single-thread tree path.
+// EMS_CHAIN_M (environment) pins M for tuning.
 void chain_shape(int64_t n, int prec, int *T, int *M) {
+    const int64_t target = prec == EMS_F32 ? 448 : 192;
     int m = 4;
-    while (m < 64 && (n + m - 1) / m > 128) m *= 2;
+    while (m < 64 && (n + m - 1) / m > target) m *= 2;
     if (const char *e = getenv("EMS_CHAIN_M")) {
         int v = atoi(e);
         if (v == 4 || v == 8 || v == 16 || v == 32 || v == 64) m = v;
@@ -402,6 +405,10 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.ir_x = cv.take<double>((size_t)S * nf); d.ir_r = cv.take<double>((size_t)S * nf);
     d.ir_p = cv.take<double>((size_t)S * nf); d.ir_Ap = cv.take<double>((size_t)S * nf);
     d.ir_z = cv.take<double>((size_t)S * nf);
+    d.val32 = cv.take<float>((size_t)S * nnz); d.dinv32 = cv.take<float>((size_t)S * nf);
+    d.r32 = cv.take<float>((size_t)S * nf); d.p32 = cv.take<float>((size_t)S * nf);
+    d.Ap32 = cv.take<float>((size_t)S * nf); d.z32 = cv.take<float>((size_t)S * nf);
+    d.d32 = cv.take<float>((size_t)S * nf);
     d.u = cv.take<double>((size_t)S * nn); d.pad_V_of_node = cv.take<double>(nn);
     d.drop = cv.take<double>(S);
     d.red = cv.take<double>(4096 + 8 * (size_t)S);

@@ -29,13 +29,19 @@ template <typename R, int M> struct ChainMaxThreads;
 template <int M> struct ChainMaxThreads<double, M> {
     static constexpr int value = M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 384 : 256;
 };
-// the FP32 kernel solves for the increment and keeps two chunks (state and
-// increment) in registers
+// the FP32 kernel solves for the increment; it keeps one chunk in registers
+// and stages the forward sweep in shared memory (8 bytes per node, at most
+// 160 KB per CTA)
 template <int M> struct ChainMaxThreads<float, M> {
-    static constexpr int value = M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 448 : 256;
+    static constexpr int value = M <= 8 ? 1024 : M == 16 ? 640 : M == 32 ? 640 : 320;
 };
+// minimum resident CTAs the register budget is sized for (launch bounds):
+// FP32 chunks of <= 16 nodes get 51 registers so that four 320-thread trees
+// share an SM (512 trees of 5,101 nodes then run in one wave on 152 SMs)
+template <typename R, int M> struct ChainMinBlocks { static constexpr int value = 1; };
+template <> struct ChainMinBlocks<float, 16> { static constexpr int value = 2; };
 inline int chain_max_threads(int prec, int M) {
-    if (prec == EMS_F32) return M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 448 : 256;
+    if (prec == EMS_F32) return M <= 8 ? 1024 : M == 16 ? 640 : M == 32 ? 640 : 320;
     return M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 384 : 256;
 }
 
@@ -90,6 +96,8 @@ struct Dev {
     double *csr_val;                   // [S][nnz]
     double *ir_b, *ir_dinv;            // [S][nf]
     double *ir_x, *ir_r, *ir_p, *ir_Ap, *ir_z;  // [S][nf]
+    float *val32, *dinv32;             // FP32 copies for the inner solve ([S][nnz], [S][nf])
+    float *r32, *p32, *Ap32, *z32, *d32;      // [S][nf] inner FP32 CG vectors
     double *u;                         // [S][n_nodes]
     double *pad_V_of_node;             // [n_nodes] NaN if not a pad
     double *drop;                      // [S]
@@ -157,6 +165,7 @@ struct ems_ctx {
     int coop_blocks = 0;       // resident CTAs for the cooperative PCG
     int64_t launches = 0;      // kernels this context has launched
     int cluster_ok = -1;       // cluster PCG residency (-1 unknown, 0 no, 1 yes)
+    int64_t ir_iter_total = 0; // PCG iterations accumulated by ems_ttf (inner iterations)
     // thermal raster currently set (nx = 0: uniform T0)
     int rnx = 0, rny = 0;
     double rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;

@@ -29,6 +29,7 @@ struct IRArgs {
     const double *rhs_padV, *sink, *R;
     int n_seg;
     double *val, *b, *dinv, *x, *r, *p, *Ap, *z;
+    float *val32, *dinv32, *r32, *p32, *Ap32, *z32, *d32;
     double rtol;
     int max_iter;
     int32_t *iters, *status;
@@ -52,6 +53,8 @@ __global__ void k_ir_assemble(IRArgs a) {
         for (int e = a.rhs_ptr[i]; e < a.rhs_ptr[i + 1]; ++e) bb += a.rhs_padV[e] / R[a.rhs_seg[e]];
         a.b[(size_t)s * a.nf + i] = bb;
         a.dinv[(size_t)s * a.nf + i] = 1.0 / diag;
+        a.dinv32[(size_t)s * a.nf + i] = (float)(1.0 / diag);
+        for (int k = a.ptr[i]; k < a.ptr[i + 1]; ++k) a.val32[(size_t)s * a.nnz + k] = (float)a.val[(size_t)s * a.nnz + k];
     }
 }
 
@@ -129,82 +132,6 @@ __global__ void __launch_bounds__(1024) k_pcg_block(IRArgs a) {
     }
 }
 
-// Mode C: one thread-block cluster (up to 16 CTAs) per sample.  Vectors stay
-// in global memory (L2-resident at these sizes); the cluster barrier orders
-// them, and reductions read every CTA's partial through distributed shared
-// memory in rank order (deterministic).  Partials are double-buffered so a
-// CTA can start the next reduction while slower CTAs still read the last one.
-template <int K>
-__device__ __forceinline__ void cluster_sum(cg::cluster_group &cl, double (&v)[K], double *sh,
-                                            double (*part)[4], int &buf) {
-    block_sum<K>(v, sh);
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int q = 0; q < K; ++q) part[buf][q] = v[q];
-    cl.sync();
-    const unsigned nb = cl.num_blocks();
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-        double t = 0.0;
-        for (unsigned r = 0; r < nb; ++r) t += cl.map_shared_rank(&part[buf][0], r)[q];
-        v[q] = t;
-    }
-    buf ^= 1;
-}
-
-__global__ void __launch_bounds__(1024) k_pcg_cluster(IRArgs a) {
-    __shared__ double sh[96];
-    __shared__ double part[2][4];
-    cg::cluster_group cl = cg::this_cluster();
-    const int CL = (int)cl.num_blocks();
-    const int s = blockIdx.x / CL, nf = a.nf;
-    const int tid = (int)cl.block_rank() * blockDim.x + threadIdx.x, stride = CL * blockDim.x;
-    const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf, *dinv = a.dinv + (size_t)s * nf;
-    double *x = a.x + (size_t)s * nf, *r = a.r + (size_t)s * nf, *p = a.p + (size_t)s * nf;
-    double *Ap = a.Ap + (size_t)s * nf, *z = a.z + (size_t)s * nf;
-    int buf = 0;
-    double v3[3] = {0.0, 0.0, 0.0};
-    for (int i = tid; i < nf; i += stride) {
-        double ri = b[i] - row_dot(a, val, x, i);
-        double zi = dinv[i] * ri;
-        r[i] = ri; z[i] = zi; p[i] = zi;
-        v3[0] += ri * zi; v3[1] += ri * ri; v3[2] += b[i] * b[i];
-    }
-    cluster_sum<3>(cl, v3, sh, part, buf);
-    double rz = v3[0], rr = v3[1];
-    const double tol2 = a.rtol * a.rtol * v3[2];
-    int it = 0;
-    while (rr > tol2 && it < a.max_iter) {
-        cl.sync();                                  // p complete
-        double v1[1] = {0.0};
-        for (int i = tid; i < nf; i += stride) {
-            double q = row_dot(a, val, p, i);
-            Ap[i] = q;
-            v1[0] += p[i] * q;
-        }
-        cluster_sum<1>(cl, v1, sh, part, buf);
-        const double alpha = rz / v1[0];
-        double v2[2] = {0.0, 0.0};
-        for (int i = tid; i < nf; i += stride) {
-            x[i] += alpha * p[i];
-            double ri = r[i] - alpha * Ap[i];
-            double zi = dinv[i] * ri;
-            r[i] = ri; z[i] = zi;
-            v2[0] += ri * zi; v2[1] += ri * ri;
-        }
-        cluster_sum<2>(cl, v2, sh, part, buf);
-        const double beta = v2[0] / rz;
-        rz = v2[0]; rr = v2[1];
-        for (int i = tid; i < nf; i += stride) p[i] = z[i] + beta * p[i];
-        ++it;
-    }
-    if (cl.block_rank() == 0 && threadIdx.x == 0) {
-        a.iters[s] = it;
-        if (rr > tol2) atomicOr(&a.status[kStatusNoConv], 1);
-    }
-    cl.sync();                                      // keep shared memory alive for readers
-}
-
 // Grid barrier for a cooperative launch: sense by generation counter, bounded
 // spin.  Returns false (and sets the timeout status) if the wait expired.
 __device__ bool grid_sync(unsigned int *bar, int32_t *status) {
@@ -263,6 +190,119 @@ __device__ bool grid_sum(double (&v)[K], double *sh, double *red, unsigned int *
 #pragma unroll
     for (int q = 0; q < K; ++q) v[q] = bc[q];
     return true;
+}
+
+__device__ __forceinline__ float row_dot32(const IRArgs &a, const float *val, const float *v, int i) {
+    float acc = 0.0f;
+    for (int k = a.ptr[i]; k < a.ptr[i + 1]; ++k) acc = fmaf(val[k], v[a.col[k]], acc);
+    return acc;
+}
+
+// Mode P: pipelined Jacobi-PCG (the Ghysels-Vanroose recurrences) on a
+// cooperative grid, one barrier per iteration: each iteration's dot
+// products and the preconditioned vector m = D^-1 w are published before a
+// single grid barrier, after which every block sums the partials (fixed
+// order) and forms A m from its neighbours' m.  Each thread owns up to ROWS
+// rows and keeps their CG vectors in registers; m is double-buffered in
+// global memory.  The recurrences run in FP64 (in FP32 they stagnate on
+// these systems); the true residual b - A x is recomputed after each pass
+// and a new pass is started on the correction (iterative refinement) while
+// it misses rtol, which also closes the residual gap of the pipelined form.
+template <int ROWS>
+__global__ void __launch_bounds__(512, 1) k_pcg_pipe(IRArgs a) {
+    __shared__ double sh[96];
+    const int nf = a.nf, G = gridDim.x;
+    const int nt = G * blockDim.x, gid = blockIdx.x * blockDim.x + threadIdx.x;
+    // red0 / red1 alternate between consecutive iterations; red2 serves the
+    // one-off reductions, so no buffer is rewritten while a block still reads it
+    double *red0 = a.red, *red1 = a.red + 4 * G, *red2 = a.red + 8 * G;
+    for (int s = 0; s < a.S; ++s) {
+        const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf;
+        const double *dinv = a.dinv + (size_t)s * nf;
+        double *x = a.x + (size_t)s * nf;
+        double *mb0 = a.r + (size_t)s * nf, *mb1 = a.p + (size_t)s * nf, *ub = a.z + (size_t)s * nf;
+        int row[ROWS];
+        double dv[ROWS];
+#pragma unroll
+        for (int k = 0; k < ROWS; ++k) {
+            row[k] = gid + k * nt;
+            dv[k] = row[k] < nf ? dinv[row[k]] : 0.0;
+        }
+        double vb[1] = {0.0};
+#pragma unroll
+        for (int k = 0; k < ROWS; ++k)
+            if (row[k] < nf) vb[0] += b[row[k]] * b[row[k]];
+        if (!grid_sum<1>(vb, sh, red0, a.bar, a.status)) return;   // next reduction uses red2
+        const double tol2 = a.rtol * a.rtol * vb[0];
+        int it = 0, parity = 0;
+        double rr64 = 0.0;
+        for (int round = 0; round < 8; ++round) {
+            double r[ROWS], u[ROWS], w[ROWS], z[ROWS], q[ROWS], sv[ROWS], p[ROWS], d[ROWS];
+            double v1[1] = {0.0};
+#pragma unroll
+            for (int k = 0; k < ROWS; ++k) {
+                r[k] = row[k] < nf ? b[row[k]] - row_dot(a, val, x, row[k]) : 0.0;
+                u[k] = dv[k] * r[k];
+                z[k] = q[k] = sv[k] = p[k] = d[k] = 0.0;
+                v1[0] += r[k] * r[k];
+                if (row[k] < nf) ub[row[k]] = u[k];
+            }
+            if (!grid_sum<1>(v1, sh, red2, a.bar, a.status)) return;   // also publishes u
+            rr64 = v1[0];
+            if (rr64 <= tol2 || it >= a.max_iter) break;
+#pragma unroll
+            for (int k = 0; k < ROWS; ++k) w[k] = row[k] < nf ? row_dot(a, val, ub, row[k]) : 0.0;
+            double gam_old = 1.0, alpha_old = 1.0;
+            bool first = true;
+            for (;;) {
+                double *mb = parity ? mb1 : mb0;
+                double *red = parity ? red1 : red0;
+                double v3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int k = 0; k < ROWS; ++k) {
+                    v3[0] += r[k] * u[k];
+                    v3[1] += w[k] * u[k];
+                    v3[2] += r[k] * r[k];
+                    if (row[k] < nf) mb[row[k]] = dv[k] * w[k];
+                }
+                if (!grid_sum<3>(v3, sh, red, a.bar, a.status)) return;
+                parity ^= 1;
+                const double gam = v3[0], del = v3[1], rr = v3[2];
+                // a quarter of the target leaves room for the residual gap
+                if (rr <= 0.0625 * tol2 || it >= a.max_iter || !(gam > 0.0)) break;
+                double beta = 0.0, alpha = gam / del;
+                if (!first) {
+                    beta = gam / gam_old;
+                    alpha = gam / (del - beta * gam / alpha_old);
+                }
+                first = false;
+#pragma unroll
+                for (int k = 0; k < ROWS; ++k) {
+                    const double m = dv[k] * w[k];
+                    const double nn = row[k] < nf ? row_dot(a, val, mb, row[k]) : 0.0;
+                    z[k] = fma(beta, z[k], nn);
+                    q[k] = fma(beta, q[k], m);
+                    sv[k] = fma(beta, sv[k], w[k]);
+                    p[k] = fma(beta, p[k], u[k]);
+                    d[k] = fma(alpha, p[k], d[k]);
+                    r[k] = fma(-alpha, sv[k], r[k]);
+                    u[k] = fma(-alpha, q[k], u[k]);
+                    w[k] = fma(-alpha, z[k], w[k]);
+                }
+                gam_old = gam; alpha_old = alpha;
+                ++it;
+            }
+#pragma unroll
+            for (int k = 0; k < ROWS; ++k)
+                if (row[k] < nf) x[row[k]] += d[k];
+            if (!grid_sync(a.bar, a.status)) return;                   // x complete
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.iters[s] = it;
+            if (rr64 > tol2) atomicOr(&a.status[kStatusNoConv], 1);
+        }
+        if (!grid_sync(a.bar, a.status)) return;
+    }
 }
 
 // Mode B: cooperative grid, samples one after another.
@@ -355,27 +395,19 @@ IRArgs make_args(ems_ctx *c) {
     a.sink = d.sink_of_free; a.R = d.R; a.n_seg = c->n_seg;
     a.val = d.csr_val; a.b = d.ir_b; a.dinv = d.ir_dinv; a.x = d.ir_x; a.r = d.ir_r; a.p = d.ir_p;
     a.Ap = d.ir_Ap; a.z = d.ir_z; a.rtol = c->prm.ir_rtol; a.max_iter = c->prm.ir_max_iter;
+    a.val32 = d.val32; a.dinv32 = d.dinv32; a.r32 = d.r32; a.p32 = d.p32; a.Ap32 = d.Ap32; a.z32 = d.z32;
+    a.d32 = d.d32;
     a.iters = d.ir_iters; a.status = d.status; a.red = d.red; a.bar = d.gbar;
     return a;
 }
 
-constexpr int64_t kClusterModeMaxRows = 16 * 16384;
 
 }  // namespace
 
-namespace {
-cudaLaunchConfig_t cluster_cfg(int cl, int S, cudaStream_t st, cudaLaunchAttribute *at) {
-    cudaLaunchConfig_t q = {};
-    q.gridDim = dim3(cl * S); q.blockDim = dim3(1024); q.dynamicSmemBytes = 0; q.stream = st;
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cl; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
-    q.attrs = at; q.numAttrs = 1;
-    return q;
-}
-}  // namespace
-
-// PCG dispatch: one CTA per sample for small systems, one cluster of up to
-// 16 CTAs per sample up to 256K unknowns, a cooperative grid beyond that.
+// PCG dispatch: one CTA per sample up to 4,096 unknowns; the pipelined
+// mixed-precision grid solver while one to four rows per thread cover the
+// system (one 512-thread CTA per SM); the FP64 cooperative grid solver
+// beyond that.
 ems_status ir_assemble_and_solve(ems_ctx *c, bool warm) {
     (void)warm;
     IRArgs a = make_args(c);
@@ -385,39 +417,25 @@ ems_status ir_assemble_and_solve(ems_ctx *c, bool warm) {
         k_ir_assemble<<<g1, 256, 0, st>>>(a);
         ++c->launches;
         EMS_CUDA(c, cudaGetLastError());
-        int cl = 1;
-        while (cl < 16 && (int64_t)cl * 4096 < c->nf) cl *= 2;
-        bool done = false;
-        if (cl == 1) {
+        int dev = 0, nsm = 0;
+        EMS_CUDA(c, cudaGetDevice(&dev));
+        EMS_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        if (c->nf <= 4096) {
             int threads = c->nf >= 1024 ? 1024 : ((c->nf + 31) / 32) * 32;
             k_pcg_block<<<c->S, threads, 0, st>>>(a);
             ++c->launches;
             EMS_CUDA(c, cudaGetLastError());
-            done = true;
-        } else if ((int64_t)c->nf <= kClusterModeMaxRows) {
-            if (c->cluster_ok < 0) {   // can a cluster of this size be resident at all?
-                EMS_CUDA(c, cudaFuncSetAttribute((void *)k_pcg_cluster,
-                                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-                cudaLaunchAttribute at[1];
-                cudaLaunchConfig_t q = cluster_cfg(cl, 1, st, at);
-                int ncl = 0;
-                cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, (void *)k_pcg_cluster, &q);
-                if (e != cudaSuccess) cudaGetLastError();
-                c->cluster_ok = (e == cudaSuccess && ncl > 0) ? 1 : 0;
-            }
-            if (c->cluster_ok == 1) {
-                cudaLaunchAttribute at[1];
-                cudaLaunchConfig_t q = cluster_cfg(cl, c->S, st, at);
-                EMS_CUDA(c, cudaLaunchKernelEx(&q, k_pcg_cluster, a));
-                ++c->launches;
-                done = true;
-            }
-        }
-        if (!done) {
+        } else if ((int64_t)c->nf <= (int64_t)4 * nsm * 512) {
+            const int rows = (c->nf + nsm * 512 - 1) / (nsm * 512);
+            const int G = (c->nf + rows * 512 - 1) / (rows * 512);
+            EMS_CUDA(c, cudaMemsetAsync(c->d.gbar, 0, 2 * sizeof(unsigned int), st));
+            void *args[] = {&a};
+            void *fn = rows == 1 ? (void *)k_pcg_pipe<1> : rows == 2 ? (void *)k_pcg_pipe<2> : (void *)k_pcg_pipe<4>;
+            EMS_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(512), args, 0, st));
+            ++c->launches;
+        } else {
             if (c->coop_blocks == 0) {
-                int dev = 0, nsm = 0, per = 0;
-                EMS_CUDA(c, cudaGetDevice(&dev));
-                EMS_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+                int per = 0;
                 EMS_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_grid, 512, 0));
                 if (per < 1) return fail(c, EMS_E_CUDA, "cooperative PCG cannot be resident");
                 int G = nsm * (per < 2 ? per : 2);

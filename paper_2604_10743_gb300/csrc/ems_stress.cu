@@ -305,13 +305,32 @@ __device__ __forceinline__ void chain_factor(const ChainArgs<R> &a, int n, int T
         }
     }
     __syncthreads();
+    if (DELTA) {
+        // increment form: gamma_k = -p_k dtg_k and u_k = -p_k dtg_{k+1} are
+        // formed on the fly, so the carry products use the same products
+        R acc = R(1);
+        for (int k = 0; k < M; ++k) {
+            const int64_t pk = ps + (int64_t)k * T + c;
+            const int i = c * M + k;
+            a.beta[pk] = i < n ? (R)(dt * a.f[cs + i]) : R(0);
+            acc *= a.alpha[pk] * a.dtg[pk];
+            a.Pf[pk] = acc;
+        }
+        acc = R(1);
+        for (int k = M - 1; k >= 0; --k) {
+            const int64_t pk = ps + (int64_t)k * T + c;
+            const R gn = k + 1 < M ? a.dtg[pk + T] : (c + 1 < T ? a.dtg[ps + c + 1] : R(0));
+            acc *= a.alpha[pk] * gn;
+            a.Pb[pk] = acc;
+        }
+        return;
+    }
     R acc = R(1);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         const int64_t pk = ps + (int64_t)k * T + c;
         const int i = c * M + k;
-        if (DELTA) a.beta[pk] = i < n ? (R)(dt * a.f[cs + i]) : R(0);
-        else a.beta[pk] = i < n ? (R)(a.pinv[pk] * dt * a.f[cs + i]) : R(0);
+        a.beta[pk] = i < n ? (R)(a.pinv[pk] * dt * a.f[cs + i]) : R(0);
         acc *= -a.gam[pk];
         a.Pf[pk] = acc;
     }
@@ -350,7 +369,8 @@ __device__ __forceinline__ int void_segment(const ChainArgs<R> &a, int s, int64_
 }
 
 template <typename R, int M, bool DELTA>
-__global__ void __launch_bounds__(ChainMaxThreads<R, M>::value) k_chain(ChainArgs<R> a) {
+__global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R, M>::value)
+    k_chain(ChainArgs<R> a) {
     __shared__ R sA[32], sB[32], sC[32], sL[32], sR[32];
     __shared__ double sv[32];
     __shared__ int si[32];
@@ -358,6 +378,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value) k_chain(ChainArg
     __shared__ int s_node[EMS_MAX_VOIDS];
     __shared__ double s_vol[EMS_MAX_VOIDS], s_coef[EMS_MAX_VOIDS];
 
+    extern __shared__ float2 zu[];      // increment form: [M][T] forward values
     const int t = a.trees[blockIdx.x], s = blockIdx.y;
     const int T = blockDim.x, c = threadIdx.x;
     const int64_t cb = a.toff[t];
@@ -430,7 +451,9 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value) k_chain(ChainArg
 #pragma unroll
             for (int k = 0; k < M; ++k) sg[k] = fma(a.Pb[ps + (int64_t)k * T + c], cr, sg[k]);
         } else {
-            // increment form: M d = dt (A s + f) with A s from face fluxes, s += d
+            // increment form: (C - dt A) d = dt (A s + f), s += d.  The
+            // forward values z and the products u = p dtg_{k+1} go to shared
+            // memory; the state chunk is the only array kept in registers.
             const unsigned full = 0xffffffffu;
             const int lane = c & 31, w = c >> 5, nw = T >> 5;
             R left = __shfl_up_sync(full, sg[M - 1], 1);
@@ -442,34 +465,37 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value) k_chain(ChainArg
                 if (lane == 0 && w > 0) left = sL[w - 1];
                 if (lane == 31 && w + 1 < nw) right = sR[w + 1];
             }
-            const R g_next = c + 1 < T ? a.dtg[ps + c + 1] : R(0);   // face to the next chunk
-            R qprev = a.dtg[ps + c] * (left - sg[0]);
+            const R *pG = a.dtg + ps + c, *pP = a.alpha + ps + c, *pB = a.beta + ps + c;
+            const R g_next = c + 1 < T ? pG[1] : R(0);          // face to the next chunk
+            R gk = pG[0];
+            R qprev = gk * (left - sg[0]);
             R z = R(0);
-            R dz[M];
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                const int64_t pk = ps + (int64_t)k * T + c;
                 const R nxt = k + 1 < M ? sg[k + 1] : right;
-                const R gk1 = k + 1 < M ? a.dtg[pk + T] : g_next;
+                const R gk1 = k + 1 < M ? pG[(int64_t)(k + 1) * T] : g_next;
+                const R pk = pP[(int64_t)k * T];
                 const R qn = gk1 * (sg[k] - nxt);
-                R r = qprev - qn + a.beta[pk];
-                if ((vmask >> k) & 1ull) r -= a.dtl[pk] * sg[k];
-                z = fma(-a.gam[pk], z, a.alpha[pk] * r);
-                dz[k] = z;
+                R r = qprev - qn + pB[(int64_t)k * T];
+                if ((vmask >> k) & 1ull) r -= a.dtl[ps + (int64_t)k * T + c] * sg[k];
+                z = pk * fma(gk, z, r);
+                zu[k * T + c] = make_float2((float)z, (float)(pk * gk1));
                 qprev = qn;
+                gk = gk1;
             }
             const R cf = scan_fwd<R>(z, a.Pf[ps + (int64_t)(M - 1) * T + c], sA, sB, sC);
-#pragma unroll
-            for (int k = 0; k < M; ++k) dz[k] = fma(a.Pf[ps + (int64_t)k * T + c], cf, dz[k]);
             R x = R(0);
+            const R *pF = a.Pf + ps + c;
 #pragma unroll
             for (int k = M - 1; k >= 0; --k) {
-                x = fma(-a.uu[ps + (int64_t)k * T + c], x, dz[k]);
-                dz[k] = x;
+                const float2 e = zu[k * T + c];
+                x = fma((R)e.y, x, fma(pF[(int64_t)k * T], cf, (R)e.x));
+                sg[k] += x;
             }
             const R cr = scan_bwd<R>(x, a.Pb[ps + c], sA, sB, sC);
+            const R *pBk = a.Pb + ps + c;
 #pragma unroll
-            for (int k = 0; k < M; ++k) sg[k] += fma(a.Pb[ps + (int64_t)k * T + c], cr, dz[k]);
+            for (int k = 0; k < M; ++k) sg[k] = fma(pBk[(int64_t)k * T], cr, sg[k]);
         }
 
         // void growth by the Robin leak: the owner thread of a void node stores
@@ -742,12 +768,24 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
         a.n_bucket = (int)b.trees.size();
         if (b.chain) {
             dim3 grid((unsigned)b.trees.size(), c->S);
+            const size_t smem = kDelta ? sizeof(float2) * (size_t)b.T * b.M : 0;
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaSuccess;
+                switch (b.M) {
+                    case 4: e = cudaFuncSetAttribute(k_chain<R, 4, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+                    case 8: e = cudaFuncSetAttribute(k_chain<R, 8, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+                    case 16: e = cudaFuncSetAttribute(k_chain<R, 16, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+                    case 32: e = cudaFuncSetAttribute(k_chain<R, 32, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+                    case 64: e = cudaFuncSetAttribute(k_chain<R, 64, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+                }
+                EMS_CUDA(c, e);
+            }
             switch (b.M) {
-                case 4: k_chain<R, 4, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
-                case 8: k_chain<R, 8, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
-                case 16: k_chain<R, 16, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
-                case 32: k_chain<R, 32, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
-                case 64: k_chain<R, 64, kDelta><<<grid, b.T, 0, c->stream>>>(a); break;
+                case 4: k_chain<R, 4, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
+                case 8: k_chain<R, 8, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
+                case 16: k_chain<R, 16, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
+                case 32: k_chain<R, 32, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
+                case 64: k_chain<R, 64, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
                 default: return fail(c, EMS_E_STATE, "unsupported chunk length");
             }
             ++c->launches;

@@ -22,6 +22,14 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
     cudaStream_t st = c->stream;
     std::vector<double> drop(S), prev(S), ttf(S, INFINITY);
     std::vector<double> all((size_t)S * (n_out + 1));
+    std::vector<int32_t> iters(S);
+    double it_total = 0.0;
+    auto add_iters = [&]() -> ems_status {
+        EMS_CUDA(c, cudaMemcpyAsync(iters.data(), c->d.ir_iters, 4 * S, cudaMemcpyDeviceToHost, st));
+        EMS_CUDA(c, cudaStreamSynchronize(st));
+        for (int s = 0; s < S; ++s) it_total += iters[s];
+        return EMS_OK;
+    };
     float ms_stress = 0.0f, ms_ir = 0.0f, ms = 0.0f;
 
     EMS_CUDA(c, cudaEventRecord(c->ev0, st));
@@ -30,6 +38,7 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
     EMS_CUDA(c, cudaEventRecord(c->ev1, st));
     EMS_CUDA(c, cudaMemcpyAsync(drop.data(), c->d.drop, 8 * S, cudaMemcpyDeviceToHost, st));
     EMS_TRY(check_status(c));
+    EMS_TRY(add_iters());
     EMS_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     ms_ir += ms;
     for (int s = 0; s < S; ++s) {
@@ -76,6 +85,7 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
         cudaEventDestroy(e2);
         cudaEventDestroy(e3);
         if (sx != EMS_OK) return sx;
+        EMS_TRY(add_iters());
         node_steps += (double)c->N * S * p.n_inner;
         for (int s = 0; s < S; ++s) {
             all[(size_t)s * (n_out + 1) + k + 1] = drop[s];
@@ -103,6 +113,7 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
         out->node_steps = node_steps;
         out->stress_ms = ms_stress;
         out->ir_ms = ms_ir;
+        out->ir_iterations = it_total;
     }
     return EMS_OK;
 }

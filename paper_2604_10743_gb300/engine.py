@@ -116,7 +116,8 @@ class Engine:
         o = A.EmsTtfOpts(); o.screen = 1 if screen else 0; o.n_outer = int(n_outer)
         self._check(self.L.ems_ttf(self.ctx, ctypes.byref(o), ctypes.byref(r)))
         return dict(ttf=ttf, drop0=d0, final_drop=fd, n_voids=nv, n_mortal=nm, drops=drops,
-                    node_steps=r.node_steps, stress_ms=r.stress_ms, ir_ms=r.ir_ms)
+                    node_steps=r.node_steps, stress_ms=r.stress_ms, ir_ms=r.ir_ms,
+                    ir_iterations=r.ir_iterations)
 
     def sigma(self):
         s = np.empty((self.S, self.n_stress))

@@ -43,7 +43,9 @@ def _void_sets(eng, ref, sample=0):
 
 
 def test_ir_solve_tiny_and_grids():
-    for g in (es.tiny_grid(), es.mid_grid(N=64, with_map=False)):
+    # 60 unknowns (one CTA), 4,080 (one CTA), 65,472 (cluster, FP32 inner
+    # CG with FP64 refinement)
+    for g in (es.tiny_grid(), es.mid_grid(N=64, with_map=False), es.mid_grid(with_map=False)):
         p = es.default_params()
         eng = _engine(p, g)
         u, d = eng.ir_solve()
