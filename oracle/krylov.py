@@ -20,8 +20,14 @@ Readings (where the paper is silent):
     paper's ||H|| < eps test), and sends the tree back to full backward Euler
     when only some of its columns fall under that bound (rank deficiency);
   * Krylov is used for trees with n >= max(3q, 30) (Eq. krylov_threshold);
-  * the basis is rebuilt whenever the tree's matrix changes (a new void), so
-    the cache key (tree matrices, s0) never goes stale within a call;
+  * bases are cached per tree (Sec. IV-E.4) under a fingerprint of the
+    descriptor system and s0.  The system's input term B j - D is part of
+    that system, so the key covers the void set (which fixes C and A within a
+    run) and the forcing f itself: a hit (an aging step whose resistances,
+    hence currents, did not change) reuses V, A_h, C_h with
+    s_hat(0) = V^T s0; a new void or new currents rebuild from the current
+    stress and forcing.  (Keying on C, A and s0 alone reuses bases built for
+    other forcings; on the 8 x 8 grid that moves the TTF by 22 %.);
   * nucleation is checked on the lifted stress after every reduced step, as
     in the full-order path.
 """
@@ -90,7 +96,7 @@ def krylov_basis(C, A, f, sigma0, s0, q, eps_rel=1e-10):
         return lu.solve(np.asarray(C @ X))
 
     F0 = np.column_stack([lu.solve(C @ sigma0), lu.solve(f)])
-    eps = eps_rel * np.abs(F0).max(axis=0).max() * math.sqrt(F0.shape[0])
+    eps = eps_rel * np.linalg.norm(F0, axis=0).max()
     if eps == 0.0:
         return None, None, None, None, "empty"
     # thin QR of the starting block, dropping columns under eps
@@ -130,12 +136,13 @@ def krylov_basis(C, A, f, sigma0, s0, q, eps_rel=1e-10):
 class KrylovStepper:
     """Drop-in replacement for flow.advance inside flow.run_ttf."""
 
-    def __init__(self, q=10, eta=1.0, n_threads=0):
+    def __init__(self, q=10, eta=1.0, n_threads=0, cache=True):
         self.q = q
         self.eta = eta
         self.n_threads = n_threads
         self.n_reduced = 0
         self.n_fallback = 0
+        self.cache = {} if cache else None
 
     def use_krylov(self, n):
         return n >= max(3 * self.q, 30)
@@ -155,7 +162,14 @@ class KrylovStepper:
             mmin = math.inf
             while k < n_steps:
                 C, A, ft = tree_system(tr, phys, f, st.void, t)
-                V, Ah, Ch, fh, status = krylov_basis(C, A, ft, st.sigma[o:e], s0, self.q)
+                key = (t, tuple(np.nonzero(st.void[o:e])[0]), s0, ft.tobytes())
+                if self.cache is not None and key in self.cache:
+                    V, Ah, Ch = self.cache[key]
+                    fh, status = V.T @ ft, "ok"
+                else:
+                    V, Ah, Ch, fh, status = krylov_basis(C, A, ft, st.sigma[o:e], s0, self.q)
+                    if status == "ok" and self.cache is not None:
+                        self.cache[key] = (V, Ah, Ch)
                 if status != "ok":
                     self.n_fallback += 1
                     total += self._be(tr, p, phys, f, st, t0 + k * dt, dt, n_steps - k, t, margin)

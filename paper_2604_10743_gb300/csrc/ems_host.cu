@@ -73,6 +73,10 @@ ems_status validate(ems_ctx *c, const ems_params *p, const ems_grid_desc *g) {
         return fail(c, EMS_E_INVAL, "bad parameter value");
     if (p->precision != EMS_F64 && p->precision != EMS_F32)
         return fail(c, EMS_E_INVAL, "precision must be EMS_F64 or EMS_F32");
+    if (p->method != EMS_BE && p->method != EMS_KRYLOV && p->method != EMS_AUTO)
+        return fail(c, EMS_E_INVAL, "method must be EMS_BE, EMS_KRYLOV or EMS_AUTO");
+    if (p->method != EMS_BE && (p->krylov_q < 1 || p->krylov_q > 40 || !(p->krylov_eta > 0.0)))
+        return fail(c, EMS_E_INVAL, "krylov_q must be 1..40 and krylov_eta > 0");
     return EMS_OK;
 }
 
@@ -441,6 +445,23 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.thr0 = cv.take<double>((size_t)S * N);
     d.R_prev = cv.take<double>((size_t)S * ns);
     d.raster = cv.take<double>(EMS_MAX_RASTER);
+    d.kr_mode = cv.take<int32_t>((size_t)S * nt); d.kdone = cv.take<int32_t>((size_t)S * nt);
+    const int rmax = (c && c->prm.method != EMS_BE) ? 2 * c->prm.krylov_q : 0;
+    if (rmax > 0) {
+        d.kr_V = cv.take<double>((size_t)S * rmax * P); d.kr_W = cv.take<double>((size_t)S * rmax * P);
+        d.kr_lam = cv.take<double>((size_t)S * nt * rmax);
+        d.kr_Y = cv.take<double>((size_t)S * nt * rmax * rmax);
+        d.kr_Ch = cv.take<double>((size_t)S * nt * rmax * rmax);
+        d.kr_sp = cv.take<double>((size_t)S * P); d.kr_sg = cv.take<double>((size_t)S * P);
+        d.kr_su = cv.take<double>((size_t)S * P); d.kr_sPf = cv.take<double>((size_t)S * P);
+        d.kr_sPb = cv.take<double>((size_t)S * P);
+        d.kr_s0 = cv.take<double>((size_t)S * nt);
+        d.kr_r = cv.take<int32_t>((size_t)S * nt); d.kr_state = cv.take<int32_t>((size_t)S * nt);
+    } else {
+        d.kr_V = d.kr_W = d.kr_lam = d.kr_Y = d.kr_Ch = nullptr;
+        d.kr_sp = d.kr_sg = d.kr_su = d.kr_sPf = d.kr_sPb = d.kr_s0 = nullptr;
+        d.kr_r = d.kr_state = nullptr;
+    }
     return cv.off + 256;
 }
 
@@ -523,6 +544,7 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     c->n_sinks = g->n_sinks; c->nf = (int)pl.ir.node_of_free.size(); c->nnz = (int64_t)pl.ir.col.size();
     c->N = pl.tr.off.back(); c->P = pl.P; c->n_trees = pl.tr.n_trees;
     c->maxv = c->prm.max_voids_per_tree;
+    c->rmax = c->prm.method != EMS_BE ? 2 * c->prm.krylov_q : 0;
     const int S = c->S, ns = c->n_seg;
     // grid
     EMS_CUDA(c, up(D.seg_a, g->seg_a, ns, st)); EMS_CUDA(c, up(D.seg_b, g->seg_b, ns, st));

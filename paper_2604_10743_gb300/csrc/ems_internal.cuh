@@ -134,6 +134,13 @@ struct Dev {
     double *thr0;                      // [S][N] critical stress without voids
     double *R_prev;                    // [S][n_seg]
     double *raster;                    // thermal raster (up to EMS_MAX_RASTER values)
+    // rational Krylov reduced models (allocated when params.method != EMS_BE)
+    double *kr_V, *kr_W;               // [S][RMAX][P] basis V and modal basis W = V Y
+    double *kr_lam, *kr_Y, *kr_Ch;     // [S][nt][RMAX], [S][nt][RMAX^2] x 2
+    double *kr_sp, *kr_sg, *kr_su, *kr_sPf, *kr_sPb;   // [S][P] factors of C - t_s A
+    double *kr_s0;                     // [S][nt] expansion point s0 = 1/t_s
+    int32_t *kr_r, *kr_state;          // [S][nt] basis size; 0 none/stale, 1 valid, 2 fall back to BE
+    int32_t *kr_mode, *kdone;          // [S][nt] 1 = advanced by the reduced model; steps done
 };
 
 }  // namespace ems
@@ -166,6 +173,9 @@ struct ems_ctx {
     int64_t launches = 0;      // kernels this context has launched
     int cluster_ok = -1;       // cluster PCG residency (-1 unknown, 0 no, 1 yes)
     int64_t ir_iter_total = 0; // PCG iterations accumulated by ems_ttf (inner iterations)
+    int rmax = 0;              // Krylov basis capacity (2 q), 0 without Krylov storage
+    int kr_q = 0;              // q and eta of the reduced models currently built
+    double kr_eta = 1.0;
     // thermal raster currently set (nx = 0: uniform T0)
     int rnx = 0, rny = 0;
     double rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;
@@ -186,11 +196,15 @@ ems_status check_status(ems_ctx *c);
 // stress (ems_stress.cu)
 ems_status node_physics(ems_ctx *c);
 ems_status forcing(ems_ctx *c);
-ems_status advance(ems_ctx *c, double dt, int n_steps, int *n_new);
+ems_status advance(ems_ctx *c, double dt, int n_steps, int *n_new, int method);
+ems_status launch_be(ems_ctx *c, double dt, int n_steps);
 ems_status void_update(ems_ctx *c, int *n_changed);
 ems_status screen(ems_ctx *c);
 ems_status pack_sigma(ems_ctx *c, bool to_packed);
 ems_status init_sigma(ems_ctx *c);
+
+// Krylov (ems_krylov.cu)
+ems_status krylov_advance(ems_ctx *c, double dt, int n_steps, int method, int *n_new);
 
 }  // namespace ems
 

@@ -24,6 +24,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "ems_device.cuh"
 #include "ems_internal.cuh"
 
 namespace ems {
@@ -171,104 +172,8 @@ struct ChainArgs {
     int n_seg;
     const int32_t *face_seg, *inc_ptr, *inc_seg, *gpar, *child_ptr, *child_gidx;
     int32_t *status, *counters;
+    const int32_t *kr_mode, *kdone;   // trees the reduced model advances; steps already done
 };
-
-// exclusive scan of affine maps x -> A + B x, left to right; returns the carry
-// into this thread's chunk (the composite of all earlier chunks applied to 0)
-template <typename R>
-__device__ __forceinline__ R scan_fwd(R A, R B, R *sA, R *sB, R *sC) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const R Ao = __shfl_up_sync(full, A, d), Bo = __shfl_up_sync(full, B, d);
-        if (lane >= d) { A = fma(B, Ao, A); B = B * Bo; }
-    }
-    R cw = R(0);
-    if (nw > 1) {
-        if (lane == 31) { sA[w] = A; sB[w] = B; }
-        __syncthreads();
-        if (w == 0) {
-            R a = lane < nw ? sA[lane] : R(0), b = lane < nw ? sB[lane] : R(1);
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const R ao = __shfl_up_sync(full, a, d), bo = __shfl_up_sync(full, b, d);
-                if (lane >= d) { a = fma(b, ao, a); b = b * bo; }
-            }
-            R ex = __shfl_up_sync(full, a, 1);
-            if (lane < nw) sC[lane] = lane == 0 ? R(0) : ex;
-        }
-        __syncthreads();
-        cw = sC[w];
-    }
-    const R incl = fma(B, cw, A);
-    const R ex = __shfl_up_sync(full, incl, 1);
-    return lane == 0 ? cw : ex;
-}
-
-// the same from right to left (carry = start value of the next chunk)
-template <typename R>
-__device__ __forceinline__ R scan_bwd(R A, R B, R *sA, R *sB, R *sC) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const R Ao = __shfl_down_sync(full, A, d), Bo = __shfl_down_sync(full, B, d);
-        if (lane + d < 32) { A = fma(B, Ao, A); B = B * Bo; }
-    }
-    R cw = R(0);
-    if (nw > 1) {
-        if (lane == 0) { sA[w] = A; sB[w] = B; }
-        __syncthreads();
-        if (w == 0) {
-            R a = lane < nw ? sA[lane] : R(0), b = lane < nw ? sB[lane] : R(1);
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const R ao = __shfl_down_sync(full, a, d), bo = __shfl_down_sync(full, b, d);
-                if (lane + d < 32) { a = fma(b, ao, a); b = b * bo; }
-            }
-            R ex = __shfl_down_sync(full, a, 1);
-            if (lane < nw) sC[lane] = lane == 31 ? R(0) : ex;
-        }
-        __syncthreads();
-        cw = sC[w];
-    }
-    const R incl = fma(B, cw, A);
-    const R ex = __shfl_down_sync(full, incl, 1);
-    return lane == 31 ? cw : ex;
-}
-
-// block-wide argmax (largest value, lowest index on ties); all threads get it
-__device__ __forceinline__ void block_argmax(double &v, int &i, double *sv, int *si) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, v, o);
-        const int oi = __shfl_down_sync(0xffffffffu, i, o);
-        if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
-    }
-    __syncthreads();
-    if (lane == 0) { sv[w] = v; si[w] = i; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < nw; ++k)
-            if (sv[k] > sv[0] || (sv[k] == sv[0] && si[k] < si[0])) { sv[0] = sv[k]; si[0] = si[k]; }
-    }
-    __syncthreads();
-    v = sv[0]; i = si[0];
-    __syncthreads();
-}
-
-__device__ __forceinline__ double block_min(double v, double *sv) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if (lane == 0) sv[w] = v;
-    __syncthreads();
-    double r = sv[0];
-    for (int k = 1; k < nw; ++k) r = fmin(r, sv[k]);
-    __syncthreads();
-    return r;
-}
 
 // Factor M = C - dt A of one chain from node `from` on (earlier factors are
 // unchanged when only later diagonals changed), then every chunk's
@@ -371,7 +276,7 @@ __device__ __forceinline__ int void_segment(const ChainArgs<R> &a, int s, int64_
 template <typename R, int M, bool DELTA>
 __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R, M>::value)
     k_chain(ChainArgs<R> a) {
-    __shared__ R sA[32], sB[32], sC[32], sL[32], sR[32];
+    __shared__ R sA[64], sB[64], sC[32], sL[32], sR[32];
     __shared__ double sv[32];
     __shared__ int si[32];
     __shared__ int s_nv;
@@ -386,6 +291,10 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
     const int64_t st = (int64_t)s * a.n_trees + t;
     const double dt = a.dt;
+    if (a.kr_mode[st]) return;                     // advanced by its reduced model
+    const int kd = a.kdone[st];                    // steps already done (reduced model fell back)
+    const int n_steps = a.n_steps - kd;
+    const double t0 = a.t0 + kd * dt;
 
     __shared__ int s_refac;
     if (c == 0) {
@@ -426,30 +335,30 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     for (int q = 0; q < s_nv; ++q)
         if (s_node[q] / M == c) vmask |= 1ull << (s_node[q] % M);
 
-    for (int step = 0; step < a.n_steps; ++step) {
+    for (int step = 0; step < n_steps; ++step) {
         if (!DELTA) {
             // forward sweep z_i = alpha s_i + beta - gamma z_{i-1}
             R z = R(0);
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const int64_t pk = ps + (int64_t)k * T + c;
-                const R av = fma(a.alpha[pk], sg[k], a.beta[pk]);
-                z = fma(-a.gam[pk], z, av);
+                const R av = fmx(a.alpha[pk], sg[k], a.beta[pk]);
+                z = fmx(-a.gam[pk], z, av);
                 sg[k] = z;
             }
             const R cf = scan_fwd<R>(z, a.Pf[ps + (int64_t)(M - 1) * T + c], sA, sB, sC);
 #pragma unroll
-            for (int k = 0; k < M; ++k) sg[k] = fma(a.Pf[ps + (int64_t)k * T + c], cf, sg[k]);
+            for (int k = 0; k < M; ++k) sg[k] = fmx(a.Pf[ps + (int64_t)k * T + c], cf, sg[k]);
             // backward sweep x_i = z_i - u_i x_{i+1}
             R x = R(0);
 #pragma unroll
             for (int k = M - 1; k >= 0; --k) {
-                x = fma(-a.uu[ps + (int64_t)k * T + c], x, sg[k]);
+                x = fmx(-a.uu[ps + (int64_t)k * T + c], x, sg[k]);
                 sg[k] = x;
             }
             const R cr = scan_bwd<R>(x, a.Pb[ps + c], sA, sB, sC);
 #pragma unroll
-            for (int k = 0; k < M; ++k) sg[k] = fma(a.Pb[ps + (int64_t)k * T + c], cr, sg[k]);
+            for (int k = 0; k < M; ++k) sg[k] = fmx(a.Pb[ps + (int64_t)k * T + c], cr, sg[k]);
         } else {
             // increment form: (C - dt A) d = dt (A s + f), s += d.  The
             // forward values z and the products u = p dtg_{k+1} go to shared
@@ -478,7 +387,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                 const R qn = gk1 * (sg[k] - nxt);
                 R r = qprev - qn + pB[(int64_t)k * T];
                 if ((vmask >> k) & 1ull) r -= a.dtl[ps + (int64_t)k * T + c] * sg[k];
-                z = pk * fma(gk, z, r);
+                z = pk * fmx(gk, z, r);
                 zu[k * T + c] = make_float2((float)z, (float)(pk * gk1));
                 qprev = qn;
                 gk = gk1;
@@ -489,13 +398,13 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
 #pragma unroll
             for (int k = M - 1; k >= 0; --k) {
                 const float2 e = zu[k * T + c];
-                x = fma((R)e.y, x, fma(pF[(int64_t)k * T], cf, (R)e.x));
+                x = fmx((R)e.y, x, fmx(pF[(int64_t)k * T], cf, (R)e.x));
                 sg[k] += x;
             }
             const R cr = scan_bwd<R>(x, a.Pb[ps + c], sA, sB, sC);
             const R *pBk = a.Pb + ps + c;
 #pragma unroll
-            for (int k = 0; k < M; ++k) sg[k] = fma(pBk[(int64_t)k * T], cr, sg[k]);
+            for (int k = 0; k < M; ++k) sg[k] = fmx(pBk[(int64_t)k * T], cr, sg[k]);
         }
 
         // void growth by the Robin leak: the owner thread of a void node stores
@@ -545,7 +454,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                         const int64_t e = st * a.maxv + nv;
                         a.v_node[e] = v;
                         a.v_seg[e] = void_segment<R>(a, s, cb + v);
-                        a.v_tnuc[e] = a.t0 + ((double)step + frac) * dt;
+                        a.v_tnuc[e] = t0 + ((double)step + frac) * dt;
                         a.v_vol[e] = 0.0;
                         s_node[nv] = v; s_vol[nv] = 0.0; s_coef[nv] = dt * a.Binv * a.leak[cs + v];
                         s_nv = nv + 1;
@@ -609,9 +518,13 @@ __global__ void k_tree(ChainArgs<R> a) {
     const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
     const int64_t st = (int64_t)s * a.n_trees + t;
     const double dt = a.dt;
+    if (a.kr_mode[st]) return;
+    const int kd = a.kdone[st];
+    const int n_steps = a.n_steps - kd;
+    const double t0 = a.t0 + kd * dt;
     if (a.refactor_all || a.dirty[st]) { tree_factor<R>(a, n, cb, cs, ps); a.dirty[st] = 0; }
     int nv = a.v_count[st];
-    for (int step = 0; step < a.n_steps; ++step) {
+    for (int step = 0; step < n_steps; ++step) {
         R *r = a.beta + ps, *x = a.sig + ps;
         for (int i = 0; i < n; ++i) r[i] = (R)(a.V[cb + i] * (double)x[i] + dt * a.f[cs + i]);
         for (int i = n - 1; i >= 1; --i) {
@@ -656,7 +569,7 @@ __global__ void k_tree(ChainArgs<R> a) {
                 const int64_t e = st * a.maxv + nv;
                 a.v_node[e] = v;
                 a.v_seg[e] = void_segment<R>(a, s, cb + v);
-                a.v_tnuc[e] = a.t0 + ((double)step + frac) * dt;
+                a.v_tnuc[e] = t0 + ((double)step + frac) * dt;
                 a.v_vol[e] = 0.0;
                 ++nv;
                 a.v_count[st] = nv;
@@ -754,6 +667,7 @@ ChainArgs<R> chain_args(ems_ctx *c, double dt, int n_steps) {
     a.dirty = d.dirty; a.j = d.j; a.n_seg = c->n_seg; a.face_seg = d.face_seg; a.inc_ptr = d.inc_ptr;
     a.inc_seg = d.inc_seg; a.gpar = d.par; a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx;
     a.status = d.status; a.counters = d.counters;
+    a.kr_mode = d.kr_mode; a.kdone = d.kdone;
     return a;
 }
 
@@ -831,6 +745,7 @@ ems_status node_physics(ems_ctx *c) {
     const int64_t ts = (int64_t)c->n_trees * c->S;
     k_apply_voids<<<(unsigned)((ts + 255) / 256), 256, 0, st>>>(c->n_trees, c->S, c->maxv, c->N, d.toff,
                                                                 d.v_count, d.v_node, d.thr, d.dirty);
+    if (d.kr_state) EMS_CUDA(c, cudaMemsetAsync(d.kr_state, 0, sizeof(int32_t) * ts, st));
     ++c->launches;
     EMS_CUDA(c, cudaGetLastError());
     return EMS_OK;
@@ -847,14 +762,22 @@ ems_status forcing(ems_ctx *c) {
     return EMS_OK;
 }
 
-ems_status advance(ems_ctx *c, double dt, int n_steps, int *n_new) {
-    EMS_CUDA(c, cudaMemsetAsync(c->d.counters, 0, sizeof(int32_t), c->stream));
+ems_status launch_be(ems_ctx *c, double dt, int n_steps) {
     if (c->prm.precision == EMS_F32) {
         EMS_TRY(launch_advance<float>(c, dt, n_steps));
     } else {
         EMS_TRY(launch_advance<double>(c, dt, n_steps));
     }
     c->factored_dt = dt;
+    return EMS_OK;
+}
+
+ems_status advance(ems_ctx *c, double dt, int n_steps, int *n_new, int method) {
+    if (method != EMS_BE) return krylov_advance(c, dt, n_steps, method, n_new);
+    EMS_CUDA(c, cudaMemsetAsync(c->d.counters, 0, sizeof(int32_t), c->stream));
+    EMS_CUDA(c, cudaMemsetAsync(c->d.kr_mode, 0, sizeof(int32_t) * c->S * c->n_trees, c->stream));
+    EMS_CUDA(c, cudaMemsetAsync(c->d.kdone, 0, sizeof(int32_t) * c->S * c->n_trees, c->stream));
+    EMS_TRY(launch_be(c, dt, n_steps));
     c->t += dt * n_steps;
     if (n_new) {
         EMS_CUDA(c, cudaMemcpyAsync(n_new, c->d.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -956,9 +879,11 @@ extern "C" ems_status ems_stress_advance(ems_ctx *c, double dt, int n_steps, int
     if (!(dt > 0.0) || n_steps < 0) return fail(c, EMS_E_INVAL, "dt must be > 0 and n_steps >= 0");
     if (method != EMS_BE && method != EMS_KRYLOV && method != EMS_AUTO)
         return fail(c, EMS_E_INVAL, "unknown method");
+    if (method != EMS_BE && c->rmax == 0)
+        return fail(c, EMS_E_STATE, "Krylov method needs a context created with method EMS_KRYLOV or EMS_AUTO");
     EMS_TRY(forcing(c));
     int nn = 0;
-    EMS_TRY(advance(c, dt, n_steps, &nn));
+    EMS_TRY(advance(c, dt, n_steps, &nn, method));
     EMS_TRY(check_status(c));
     if (n_new_voids) *n_new_voids = nn;
     return EMS_OK;

@@ -64,7 +64,7 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
         prev = drop;
         EMS_CUDA(c, cudaEventRecord(c->ev0, st));
         EMS_TRY(forcing(c));
-        EMS_TRY(advance(c, dti, p.n_inner, nullptr));
+        EMS_TRY(advance(c, dti, p.n_inner, nullptr, p.method));
         EMS_CUDA(c, cudaEventRecord(c->ev1, st));
         EMS_TRY(void_update(c, nullptr));
         cudaEvent_t e2, e3;
