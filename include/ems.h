@@ -205,6 +205,7 @@ ems_status ems_void_update(ems_ctx *ctx, int *n_segments_changed);
 typedef struct {
     int screen;        /* 1: run the immortality screen first (reported only) */
     int n_outer;       /* 0: params.n_outer */
+    int no_graph;      /* 1: drive the aging steps from the host instead of one CUDA graph */
 } ems_ttf_opts;
 
 typedef struct {
@@ -218,6 +219,11 @@ typedef struct {
     double stress_ms;     /* out: device time of the stress kernels (ms) */
     double ir_ms;         /* out: device time of the IR solves (ms) */
     double ir_iterations; /* out: PCG iterations summed over the IR solves and samples */
+    double ttf_mean;      /* out: mean TTF over uncensored samples (NaN if none) */
+    double ttf_std;       /* out: sample standard deviation (ddof 1) over uncensored samples */
+    double ttf_cov;       /* out: ttf_std / ttf_mean */
+    double n_censored;    /* out: samples that never crossed (TTF = +inf) */
+    double graph_launch;  /* out: 1 if the aging steps ran as one captured CUDA graph */
 } ems_ttf_result;
 
 /*
@@ -226,6 +232,10 @@ typedef struct {
  * n_inner steps of horizon/(n_outer n_inner), void update, IR re-solve, max
  * drop; TTF is the linear interpolation of the first crossing of
  * ir_fail_frac.  Host result arrays are caller-allocated (NULL to skip).
+ * With the backward-Euler method (and n_outer <= params.n_outer) every
+ * aging step of every sample runs inside one captured CUDA graph: the
+ * crossing detection happens on the device and the host reads the results
+ * once; Monte Carlo statistics follow Sec. V-D (uncensored samples only).
  */
 ems_status ems_ttf(ems_ctx *ctx, const ems_ttf_opts *opts, ems_ttf_result *out);
 

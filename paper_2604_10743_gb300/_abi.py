@@ -46,14 +46,15 @@ class EmsGridDesc(ctypes.Structure):
 
 
 class EmsTtfOpts(ctypes.Structure):
-    _fields_ = [("screen", ctypes.c_int), ("n_outer", ctypes.c_int)]
+    _fields_ = [("screen", ctypes.c_int), ("n_outer", ctypes.c_int), ("no_graph", ctypes.c_int)]
 
 
 class EmsTtfResult(ctypes.Structure):
     _fields_ = [("ttf", c_double_p), ("drop0", c_double_p), ("final_drop", c_double_p),
                 ("n_voids", c_int32_p), ("n_mortal", c_int32_p), ("drops", c_double_p),
                 ("node_steps", ctypes.c_double), ("stress_ms", ctypes.c_double), ("ir_ms", ctypes.c_double),
-                ("ir_iterations", ctypes.c_double)]
+                ("ir_iterations", ctypes.c_double), ("ttf_mean", ctypes.c_double), ("ttf_std", ctypes.c_double),
+                ("ttf_cov", ctypes.c_double), ("n_censored", ctypes.c_double), ("graph_launch", ctypes.c_double)]
 
 
 _LIB = None

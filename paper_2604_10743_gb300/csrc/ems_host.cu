@@ -17,6 +17,7 @@ ems_status fail(ems_ctx *c, ems_status s, const std::string &msg) {
 }
 
 ems_status cuda_check(ems_ctx *c, cudaError_t e, const char *what) {
+    cudaGetLastError();   // clear the error slot so later calls do not report it again
     return fail(c, EMS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -446,6 +447,12 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.R_prev = cv.take<double>((size_t)S * ns);
     d.raster = cv.take<double>(EMS_MAX_RASTER);
     d.kr_mode = cv.take<int32_t>((size_t)S * nt); d.kdone = cv.take<int32_t>((size_t)S * nt);
+    {
+        const int no = c ? c->prm.n_outer : 1;
+        d.gtime = cv.take<double>(1); d.gttf = cv.take<double>(S);
+        d.gdrops = cv.take<double>((size_t)S * (no + 1)); d.giters = cv.take<double>(1);
+        d.gstep = cv.take<int32_t>(1);
+    }
     const int rmax = (c && c->prm.method != EMS_BE) ? 2 * c->prm.krylov_q : 0;
     if (rmax > 0) {
         d.kr_V = cv.take<double>((size_t)S * rmax * P); d.kr_W = cv.take<double>((size_t)S * rmax * P);
@@ -511,6 +518,9 @@ extern "C" ems_status ems_destroy(ems_ctx *c) {
     if (!c) return EMS_E_INVAL;
     for (auto &b : c->buckets)
         if (b.d_trees) cudaFree(b.d_trees);
+    if (c->ttf_graph) cudaGraphExecDestroy(c->ttf_graph);
+    for (auto e : c->gev) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -639,6 +649,7 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     }
     c->trees = std::move(pl.tr);
     c->pack = std::move(pl.pack);
+    if (c->ttf_graph) { cudaGraphExecDestroy(c->ttf_graph); c->ttf_graph = nullptr; }
     c->t = 0.0;
     c->factored_dt = -1.0;
     c->have_u = false;

@@ -141,6 +141,10 @@ struct Dev {
     double *kr_s0;                     // [S][nt] expansion point s0 = 1/t_s
     int32_t *kr_r, *kr_state;          // [S][nt] basis size; 0 none/stale, 1 valid, 2 fall back to BE
     int32_t *kr_mode, *kdone;          // [S][nt] 1 = advanced by the reduced model; steps done
+    // device-side TTF bookkeeping (graph-captured runs)
+    double *gtime;                     // [1] simulated time at the start of the aging step
+    double *gttf, *gdrops, *giters;    // [S], [S][n_outer+1], [1]
+    int32_t *gstep;                    // [1] aging steps done
 };
 
 }  // namespace ems
@@ -174,6 +178,13 @@ struct ems_ctx {
     int cluster_ok = -1;       // cluster PCG residency (-1 unknown, 0 no, 1 yes)
     int64_t ir_iter_total = 0; // PCG iterations accumulated by ems_ttf (inner iterations)
     int rmax = 0;              // Krylov basis capacity (2 q), 0 without Krylov storage
+    bool graph_capturing = false;  // kernels read the time from device memory
+    cudaGraphExec_t ttf_graph = nullptr;  // captured TTF run and what it was captured for
+    cudaStream_t cap_stream = nullptr;    // library stream used only to capture graphs
+    int graph_nout = 0;
+    int64_t graph_launches = 0;   // kernels inside the captured graph
+    std::vector<cudaEvent_t> gev;  // 4 per captured aging step: stress and IR start / end
+    double graph_dt = 0.0;
     int kr_q = 0;              // q and eta of the reduced models currently built
     double kr_eta = 1.0;
     // thermal raster currently set (nx = 0: uniform T0)

@@ -173,6 +173,7 @@ struct ChainArgs {
     const int32_t *face_seg, *inc_ptr, *inc_seg, *gpar, *child_ptr, *child_gidx;
     int32_t *status, *counters;
     const int32_t *kr_mode, *kdone;   // trees the reduced model advances; steps already done
+    const double *t0p;                // when set, the aging-step start time is read here
 };
 
 // Factor M = C - dt A of one chain from node `from` on (earlier factors are
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     if (a.kr_mode[st]) return;                     // advanced by its reduced model
     const int kd = a.kdone[st];                    // steps already done (reduced model fell back)
     const int n_steps = a.n_steps - kd;
-    const double t0 = a.t0 + kd * dt;
+    const double t0 = (a.t0p ? *a.t0p : a.t0) + kd * dt;
 
     __shared__ int s_refac;
     if (c == 0) {
@@ -521,7 +522,7 @@ __global__ void k_tree(ChainArgs<R> a) {
     if (a.kr_mode[st]) return;
     const int kd = a.kdone[st];
     const int n_steps = a.n_steps - kd;
-    const double t0 = a.t0 + kd * dt;
+    const double t0 = (a.t0p ? *a.t0p : a.t0) + kd * dt;
     if (a.refactor_all || a.dirty[st]) { tree_factor<R>(a, n, cb, cs, ps); a.dirty[st] = 0; }
     int nv = a.v_count[st];
     for (int step = 0; step < n_steps; ++step) {
@@ -668,6 +669,7 @@ ChainArgs<R> chain_args(ems_ctx *c, double dt, int n_steps) {
     a.inc_seg = d.inc_seg; a.gpar = d.par; a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx;
     a.status = d.status; a.counters = d.counters;
     a.kr_mode = d.kr_mode; a.kdone = d.kdone;
+    a.t0p = c->graph_capturing ? d.gtime : nullptr;
     return a;
 }
 

@@ -104,7 +104,7 @@ class Engine:
         self._check(self.L.ems_void_update(self.ctx, ctypes.byref(n)))
         return n.value
 
-    def ttf(self, screen=False, n_outer=0, n_outer_total=None):
+    def ttf(self, screen=False, n_outer=0, graph=True):
         S = self.S
         nout = n_outer if n_outer > 0 else int(self.p["n_outer"])
         ttf = np.empty(S); d0 = np.empty(S); fd = np.empty(S)
@@ -114,10 +114,12 @@ class Engine:
         r.final_drop = fd.ctypes.data_as(A.c_double_p); r.n_voids = nv.ctypes.data_as(A.c_int32_p)
         r.n_mortal = nm.ctypes.data_as(A.c_int32_p); r.drops = drops.ctypes.data_as(A.c_double_p)
         o = A.EmsTtfOpts(); o.screen = 1 if screen else 0; o.n_outer = int(n_outer)
+        o.no_graph = 0 if graph else 1
         self._check(self.L.ems_ttf(self.ctx, ctypes.byref(o), ctypes.byref(r)))
         return dict(ttf=ttf, drop0=d0, final_drop=fd, n_voids=nv, n_mortal=nm, drops=drops,
                     node_steps=r.node_steps, stress_ms=r.stress_ms, ir_ms=r.ir_ms,
-                    ir_iterations=r.ir_iterations)
+                    ir_iterations=r.ir_iterations, ttf_mean=r.ttf_mean, ttf_std=r.ttf_std,
+                    ttf_cov=r.ttf_cov, n_censored=int(r.n_censored), graph=bool(r.graph_launch))
 
     def sigma(self):
         s = np.empty((self.S, self.n_stress))

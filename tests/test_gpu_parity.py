@@ -262,3 +262,48 @@ def test_krylov_reduce_counts():
     nr, nf = eng.krylov_reduce(10, 1.0)
     assert nr == 16 and nf == 0
     eng.close()
+
+
+def test_graph_run_equals_host_loop():
+    g = es.mc_grid(n_samples=4)
+    p = es.default_params(n_outer=16)
+    a = _engine(p, g)
+    b = _engine(p, g)
+    ra = a.ttf(graph=True)
+    rb = b.ttf(graph=False)
+    assert ra["graph"] and not rb["graph"]
+    assert np.array_equal(a.sigma(), b.sigma())
+    assert np.array_equal(ra["drops"], rb["drops"])
+    assert np.array_equal(ra["ttf"], rb["ttf"])
+    a.close(); b.close()
+
+
+def test_monte_carlo_1024_samples():
+    """Uneven trees (32-1024 cells), 1,024 kappa / sigma_crit samples, every
+    sample x tree in one graph launch; sampled outputs against the oracle and
+    the TTF statistics of Sec. V-D (uncensored mean, std with ddof 1, CoV)."""
+    g = es.mc_grid(n_samples=1024)
+    p = es.default_params()
+    from paper_2604_10743_gb300 import EMS_F32
+    eng = _engine(p, g, precision=EMS_F32)
+    r = eng.ttf()
+    assert r["graph"]
+    ttf = r["ttf"]
+    unc = ttf[np.isfinite(ttf)]
+    assert r["n_censored"] == int(np.sum(~np.isfinite(ttf)))
+    if unc.size > 1:
+        assert abs(r["ttf_mean"] - unc.mean()) <= 1e-9 * unc.mean()
+        assert abs(r["ttf_std"] - unc.std(ddof=1)) <= 1e-9 * unc.std(ddof=1)
+    sig = eng.sigma()
+    rng = np.random.default_rng(0)
+    for s in rng.choice(1024, size=6, replace=False):
+        ref = F.run_ttf(g, p, sample=int(s), keep_state=True)
+        assert _relerr(sig[s], ref["state"].sigma) < TOL32
+        amb = ref["margin"].min() < 1e-3
+        gpu, ora, _ = _void_sets(eng, ref, sample=int(s))
+        if not amb:
+            assert gpu == ora
+            assert abs(r["final_drop"][s] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+            if math.isfinite(ref["ttf"]):
+                assert abs(ttf[s] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
+    eng.close()
