@@ -262,6 +262,37 @@ ems_status ems_launch_count(const ems_ctx *ctx, int64_t *launches);
 ems_status ems_state_export(ems_ctx *ctx, void *buf, size_t *bytes);
 ems_status ems_state_import(ems_ctx *ctx, const void *buf, size_t bytes);
 
+/*
+ * Allocation-free PCG solve.  The paper has no counterpart: this is a
+ * service of this library for callers that cannot allocate device memory
+ * for it -- code that runs under another framework's allocator and may not
+ * call cudaMalloc itself, or that cannot accept the device-wide
+ * synchronisation a cudaMalloc / cudaFree can cause between its own kernels.
+ *
+ * Solves A x = b by Jacobi-preconditioned conjugate gradients in FP64 on one
+ * CTA, until ||b - A x|| <= rtol ||b|| or max_iter iterations.
+ *   n          unknowns, 1..16384
+ *   row_ptr    device [n+1], col device [nnz], val device [nnz]: CSR of a
+ *              symmetric positive definite A; every row holds its diagonal
+ *   b          device [n]
+ *   x          device [n]: initial guess in, solution out
+ *   iterations optional host: iterations used
+ *   stream     cudaStream_t (NULL = default stream); the call synchronises it
+ * Returns EMS_OK, EMS_E_INVAL (n beyond 16384, null pointer, rtol <= 0),
+ * EMS_E_NOCONV (iteration cap reached) or EMS_E_CUDA.
+ *
+ * The work vectors live in one file-scope device array (640 KB) that every
+ * GPU loading the library holds until the process exits; nothing is
+ * allocated or freed.  All calls share that array: calls whose kernels can
+ * overlap on one GPU (several streams or threads at once) race and must be
+ * serialised by the caller.  The first call on each device looks the
+ * array's device address up once, with that device current; make that first
+ * call before any stream capture.
+ */
+ems_status ems_ir_pcg_noalloc(int n, const int32_t *row_ptr, const int32_t *col, const double *val,
+                              const double *b, double *x, double rtol, int max_iter, int *iterations,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,7 +63,7 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_set_thermal_map", "ems_ir_solve", "ems_immortality_check", "ems_stress_advance",
            "ems_krylov_reduce", "ems_void_update", "ems_ttf", "ems_get_sigma", "ems_get_currents",
            "ems_get_resistance", "ems_get_voids", "ems_state_export", "ems_state_import",
-           "ems_launch_count", "ems_ir_iterations"]
+           "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc"]
 
 
 def lib(path=None):
@@ -114,6 +114,8 @@ def lib(path=None):
     L.ems_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.ems_state_import.restype = S
     L.ems_state_import.argtypes = [vp, vp, ctypes.c_size_t]
+    L.ems_ir_pcg_noalloc.restype = S
+    L.ems_ir_pcg_noalloc.argtypes = [S, vp, vp, vp, vp, vp, ctypes.c_double, S, ctypes.POINTER(ctypes.c_int), vp]
     if path is None:
         _LIB = L
     return L
