@@ -167,6 +167,30 @@ def mc_grid(seed=3, n_samples=1024, N=8, pitch=20e-6, cells_lo=32, cells_hi=1024
     return g
 
 
+def surrogate_grid(seed=11, N=128, pitch=10e-6, n_samples=32, raster=256):
+    """Training / validation meshes of the learned surrogate: N x N stripes at
+    10 um with a pad every 32 crossings, a seeded fraction (1-4 %) of the
+    crossings as lognormal sinks whose median is scaled by U(0.6, 1.6), a
+    random map of 1-8 hotspots (base U(330, 350) K, +U(20, 80) K, s = 8-20 %
+    of the die) and n_samples sets of lognormal (CoV 20 %) kappa and
+    sigma_crit factors per segment."""
+    rng = _rng(seed)
+    g = stripe_mesh(N, pitch)
+    pads = _pad_array(N, 32 if N >= 64 else max(2, N // 2))
+    g["pad_node"] = pads
+    g["pad_V"] = np.ones(pads.size)
+    free = np.setdiff1d(np.arange(N * N, dtype=np.int32), pads)
+    k = max(1, int(round(rng.uniform(0.01, 0.04) * N * N)))
+    g["sink_node"] = np.sort(rng.choice(free, size=k, replace=False)).astype(np.int32)
+    g["sink_I"] = _lognormal_currents(rng, k, median=0.707e-3 * rng.uniform(0.6, 1.6))
+    die = (N - 1) * pitch
+    g["thermal"] = hotspot_raster(rng, die, int(rng.integers(1, 9)), rng.uniform(330.0, 350.0), 20.0, 80.0,
+                                  (0.08, 0.20), nx=raster, ny=raster)
+    if n_samples > 0:
+        g["kappa_factor"], g["sigc_factor"] = mc_factors(rng, n_samples, g["seg_a"].size)
+    return g
+
+
 def large_grid(seed=5, N=2048, pitch=5e-6, n_samples=256, raster=512):
     """2048 x 2048 stripes at 5 um (10 cells per segment), a pad every 32
     crossings, 5 % lognormal sinks, 8 hotspots on 330 K with amplitudes

@@ -54,7 +54,8 @@ class EmsTtfResult(ctypes.Structure):
                 ("n_voids", c_int32_p), ("n_mortal", c_int32_p), ("drops", c_double_p),
                 ("node_steps", ctypes.c_double), ("stress_ms", ctypes.c_double), ("ir_ms", ctypes.c_double),
                 ("ir_iterations", ctypes.c_double), ("ttf_mean", ctypes.c_double), ("ttf_std", ctypes.c_double),
-                ("ttf_cov", ctypes.c_double), ("n_censored", ctypes.c_double), ("graph_launch", ctypes.c_double)]
+                ("ttf_cov", ctypes.c_double), ("n_censored", ctypes.c_double), ("graph_launch", ctypes.c_double),
+                ("node_steps_executed", ctypes.c_double)]
 
 
 _LIB = None
@@ -63,7 +64,12 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_set_thermal_map", "ems_ir_solve", "ems_immortality_check", "ems_stress_advance",
            "ems_krylov_reduce", "ems_void_update", "ems_ttf", "ems_get_sigma", "ems_get_currents",
            "ems_get_resistance", "ems_get_voids", "ems_state_export", "ems_state_import",
-           "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc"]
+           "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc",
+           # include/ems_surrogate.h
+           "ems_mlp_create", "ems_mlp_destroy", "ems_mlp_last_error", "ems_mlp_param_count",
+           "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_gradients",
+           "ems_mlp_train_step", "ems_mlp_train", "ems_mlp_predict", "ems_gemm_bf16",
+           "ems_surrogate_features", "ems_surrogate_targets", "ems_surrogate_schedule", "ems_surrogate_clear"]
 
 
 def lib(path=None):
@@ -116,6 +122,28 @@ def lib(path=None):
     L.ems_state_import.argtypes = [vp, vp, ctypes.c_size_t]
     L.ems_ir_pcg_noalloc.restype = S
     L.ems_ir_pcg_noalloc.argtypes = [S, vp, vp, vp, vp, vp, ctypes.c_double, S, ctypes.POINTER(ctypes.c_int), vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    i64, u64, f32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+    for name, res, args in (
+            ("ems_mlp_create", S, [S, u64, vp, ctypes.POINTER(vp)]),
+            ("ems_mlp_destroy", None, [vp]),
+            ("ems_mlp_last_error", ctypes.c_char_p, [vp]),
+            ("ems_mlp_param_count", i64, [vp]),
+            ("ems_mlp_set_params", S, [vp, fp]),
+            ("ems_mlp_get_params", S, [vp, fp]),
+            ("ems_mlp_set_norm", S, [vp, fp, fp, fp, fp]),
+            ("ems_mlp_gradients", S, [vp, vp, vp, S, fp, fp]),
+            ("ems_mlp_train_step", S, [vp, vp, vp, S, f32, fp]),
+            ("ems_mlp_train", S, [vp, vp, vp, i64, S, S, f32, u64, fp]),
+            ("ems_mlp_predict", S, [vp, vp, i64, vp]),
+            ("ems_gemm_bf16", S, [vp, vp, S, S, S, vp, S, f32, vp, vp, vp]),
+            ("ems_surrogate_features", S, [vp, vp]),
+            ("ems_surrogate_targets", S, [vp, ctypes.c_double, S, vp]),
+            ("ems_surrogate_schedule", S, [vp, vp, ctypes.c_double, S, ctypes.c_double, c_int32_p, vp]),
+            ("ems_surrogate_clear", S, [vp])):
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
     if path is None:
         _LIB = L
     return L

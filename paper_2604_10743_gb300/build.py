@@ -25,7 +25,7 @@ def _nvcc():
 def build(force=False, verbose=False, extra=()):
     os.makedirs(OUT, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(SRC, "*.cu")))
-    deps = srcs + glob.glob(os.path.join(SRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "ems.h")]
+    deps = srcs + glob.glob(os.path.join(SRC, "*.cuh")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
     newest = max(os.path.getmtime(p) for p in deps)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB

@@ -8,6 +8,7 @@
 #include <unordered_map>
 
 #include "ems_internal.cuh"
+#include "../../include/ems_surrogate.h"
 
 namespace ems {
 
@@ -453,6 +454,11 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
         d.gdrops = cv.take<double>((size_t)S * (no + 1)); d.giters = cv.take<double>(1);
         d.gstep = cv.take<int32_t>(1);
     }
+    d.feat = cv.take<float>((size_t)S * nt * EMS_MLP_FEATURES);
+    d.pred = cv.take<float>((size_t)S * nt * EMS_MLP_OUTPUTS);
+    d.sched = cv.take<int32_t>((size_t)S * nt);
+    d.fdt = cv.take<double>((size_t)S * nt);
+    d.work = cv.take<unsigned long long>(1);
     const int rmax = (c && c->prm.method != EMS_BE) ? 2 * c->prm.krylov_q : 0;
     if (rmax > 0) {
         d.kr_V = cv.take<double>((size_t)S * rmax * P); d.kr_W = cv.take<double>((size_t)S * rmax * P);

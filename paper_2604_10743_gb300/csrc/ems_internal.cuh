@@ -145,6 +145,11 @@ struct Dev {
     double *gtime;                     // [1] simulated time at the start of the aging step
     double *gttf, *gdrops, *giters;    // [S], [S][n_outer+1], [1]
     int32_t *gstep;                    // [1] aging steps done
+    // learned surrogate: features, predictions and the step schedule
+    float *feat, *pred;                // [S][n_trees][24], [S][n_trees][2]
+    int32_t *sched;                    // [S][n_trees] step schedule: <= 1 fine, r > 1 r-times coarser, < 0 frozen
+    double *fdt;                       // [S][n_trees] step the packed factors were built for
+    unsigned long long *work;          // [1] node-steps the stress kernels executed
 };
 
 }  // namespace ems
@@ -187,6 +192,7 @@ struct ems_ctx {
     double graph_dt = 0.0;
     int kr_q = 0;              // q and eta of the reduced models currently built
     double kr_eta = 1.0;
+    double sched_guard = 0.8;  // coarse trees turn fine once sigma >= guard * lowest sigma_crit
     // thermal raster currently set (nx = 0: uniform T0)
     int rnx = 0, rny = 0;
     double rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;

@@ -173,6 +173,10 @@ struct ChainArgs {
     const int32_t *face_seg, *inc_ptr, *inc_seg, *gpar, *child_ptr, *child_gidx;
     int32_t *status, *counters;
     const int32_t *kr_mode, *kdone;   // trees the reduced model advances; steps already done
+    int32_t *sched;                   // per-tree step schedule: <= 1 fine, r > 1 r-times coarser, < 0 frozen
+    double *fdt;                      // step the tree's factors were built for
+    double guard;                     // a coarse tree turns fine once sigma >= guard * its lowest sigma_crit
+    unsigned long long *work;         // node-steps executed
     const double *t0p;                // when set, the aging-step start time is read here
 };
 
@@ -182,9 +186,8 @@ struct ChainArgs {
 // whole block.  DELTA (increment form) stores p = 1/d', dt g, dt f, dt leak
 // instead of alpha = V/d', beta = dt f/d'.
 template <typename R, int M, bool DELTA>
-__device__ __forceinline__ void chain_factor(const ChainArgs<R> &a, int n, int T, int c, int64_t cb, int64_t cs,
-                                             int64_t ps, int from) {
-    const double dt = a.dt;
+__device__ __forceinline__ void chain_factor(const ChainArgs<R> &a, double dt, int n, int T, int c, int64_t cb,
+                                             int64_t cs, int64_t ps, int from) {
     __syncthreads();
     if (c == 0) {
         double pprev = 0.0;
@@ -291,11 +294,38 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     const int n = (int)(a.toff[t + 1] - cb);
     const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
     const int64_t st = (int64_t)s * a.n_trees + t;
-    const double dt = a.dt;
-    if (a.kr_mode[st]) return;                     // advanced by its reduced model
+    const int sm = a.sched[st];
+    if (a.kr_mode[st] || sm < 0) return;           // reduced model / frozen by the schedule
     const int kd = a.kdone[st];                    // steps already done (reduced model fell back)
-    const int n_steps = a.n_steps - kd;
-    const double t0 = (a.t0p ? *a.t0p : a.t0) + kd * dt;
+    double tcur = (a.t0p ? *a.t0p : a.t0) + kd * a.dt;   // start time of the current step
+
+    double tm = INFINITY;
+    for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
+    double thrmin = block_min(tm, sv);
+    long long thr_bits = __double_as_longlong(thrmin);
+    float thr_f = __double2float_rd(thrmin);
+    R sg[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) sg[k] = a.sig[ps + (int64_t)k * T + c];
+
+    // step schedule: rs fine steps per coarse step; a coarse tree whose
+    // stress already reaches the guard level steps finely from now on
+    int rs = sm > 1 ? sm : 1;
+    if ((a.n_steps - kd) % rs) rs = 1;
+    const double gthr = a.guard * thrmin;
+    const long long g_bits = __double_as_longlong(gthr);
+    const float g_f = __double2float_rd(gthr);
+    if (rs > 1) {
+        bool near = false;
+#pragma unroll
+        for (int k = 0; k < M; ++k) near |= above<R>(sg[k], g_bits, g_f);
+        if (__syncthreads_or(near)) {
+            rs = 1;
+            if (c == 0) a.sched[st] = 0;
+        }
+    }
+    double dt = a.dt * rs;
+    int n_steps = (a.n_steps - kd) / rs;
 
     __shared__ int s_refac;
     if (c == 0) {
@@ -307,12 +337,13 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
             s_vol[q] = a.v_vol[st * a.maxv + q];
             s_coef[q] = dt * a.Binv * a.leak[cs + v];
         }
-        s_refac = (a.refactor_all || a.dirty[st]) ? 1 : 0;
+        s_refac = (a.refactor_all || a.dirty[st] || a.fdt[st] != dt) ? 1 : 0;
         a.dirty[st] = 0;
+        a.fdt[st] = dt;
     }
     __syncthreads();
     if (s_refac) {
-        chain_factor<R, M, DELTA>(a, n, T, c, cb, cs, ps, 0);
+        chain_factor<R, M, DELTA>(a, dt, n, T, c, cb, cs, ps, 0);
     } else {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
@@ -322,16 +353,8 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
             else a.beta[pk] = i < n ? (R)(a.pinv[pk] * dt * a.f[cs + i]) : R(0);
         }
     }
-    double tm = INFINITY;
-    for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
-    double thrmin = block_min(tm, sv);
-    long long thr_bits = __double_as_longlong(thrmin);
-    float thr_f = __double2float_rd(thrmin);
-
-    R sg[M];
-#pragma unroll
-    for (int k = 0; k < M; ++k) sg[k] = a.sig[ps + (int64_t)k * T + c];
     __syncthreads();
+    int executed = 0;
     unsigned long long vmask = 0ull;     // void nodes in this thread's chunk
     for (int q = 0; q < s_nv; ++q)
         if (s_node[q] / M == c) vmask |= 1ull << (s_node[q] % M);
@@ -455,7 +478,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                         const int64_t e = st * a.maxv + nv;
                         a.v_node[e] = v;
                         a.v_seg[e] = void_segment<R>(a, s, cb + v);
-                        a.v_tnuc[e] = t0 + ((double)step + frac) * dt;
+                        a.v_tnuc[e] = tcur + frac * dt;
                         a.v_vol[e] = 0.0;
                         s_node[nv] = v; s_vol[nv] = 0.0; s_coef[nv] = dt * a.Binv * a.leak[cs + v];
                         s_nv = nv + 1;
@@ -468,7 +491,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                 }
                 __syncthreads();
                 if (arg / M == c) vmask |= 1ull << (arg % M);
-                chain_factor<R, M, DELTA>(a, n, T, c, cb, cs, ps, arg);
+                chain_factor<R, M, DELTA>(a, dt, n, T, c, cb, cs, ps, arg);
                 tm = INFINITY;
                 for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
                 thrmin = block_min(tm, sv);
@@ -476,12 +499,34 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                 thr_f = __double2float_rd(thrmin);
             }
         }
+        tcur += dt;
+        executed = step + 1;
+        if (rs > 1) {
+            // coarse tree near its critical stress: finish this call with
+            // the plain solver's fine steps and keep them
+            bool near = false;
+#pragma unroll
+            for (int k = 0; k < M; ++k) near |= above<R>(sg[k], g_bits, g_f);
+            if (__syncthreads_or(near)) {
+                n_steps = step + 1 + (n_steps - step - 1) * rs;
+                rs = 1;
+                dt = a.dt;
+                if (c == 0) {
+                    a.sched[st] = 0;
+                    a.fdt[st] = dt;
+                    for (int q = 0; q < s_nv; ++q) s_coef[q] = dt * a.Binv * a.leak[cs + s_node[q]];
+                }
+                chain_factor<R, M, DELTA>(a, dt, n, T, c, cb, cs, ps, 0);
+            }
+        }
     }
 #pragma unroll
     for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * T + c] = sg[k];
     __syncthreads();
-    if (c == 0)
+    if (c == 0) {
         for (int q = 0; q < s_nv; ++q) a.v_vol[st * a.maxv + q] = s_vol[q];
+        atomicAdd(a.work, (unsigned long long)n * (unsigned long long)executed);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -490,8 +535,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
 // uu holds e, beta is the right-hand-side scratch.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ void tree_factor(const ChainArgs<R> &a, int n, int64_t cb, int64_t cs, int64_t ps) {
-    const double dt = a.dt;
+__device__ void tree_factor(const ChainArgs<R> &a, double dt, int n, int64_t cb, int64_t cs, int64_t ps) {
     for (int i = 0; i < n; ++i) {
         double d = a.V[cb + i] + (i > 0 ? dt * a.g[cs + i] : 0.0);
         if (isinf(a.thr[cs + i])) d += dt * a.leak[cs + i];
@@ -518,14 +562,31 @@ __global__ void k_tree(ChainArgs<R> a) {
     const int n = (int)(a.toff[t + 1] - cb);
     const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
     const int64_t st = (int64_t)s * a.n_trees + t;
-    const double dt = a.dt;
-    if (a.kr_mode[st]) return;
+    const int sm = a.sched[st];
+    if (a.kr_mode[st] || sm < 0) return;
     const int kd = a.kdone[st];
-    const int n_steps = a.n_steps - kd;
-    const double t0 = (a.t0p ? *a.t0p : a.t0) + kd * dt;
-    if (a.refactor_all || a.dirty[st]) { tree_factor<R>(a, n, cb, cs, ps); a.dirty[st] = 0; }
+    double tcur = (a.t0p ? *a.t0p : a.t0) + kd * a.dt;
+    double thrmin = INFINITY;
+    for (int i = 0; i < n; ++i) thrmin = fmin(thrmin, a.thr[cs + i]);
+    const double gthr = a.guard * thrmin;
+    auto near = [&]() {
+        for (int i = 0; i < n; ++i)
+            if ((double)a.sig[ps + i] >= gthr) return true;
+        return false;
+    };
+    int rs = sm > 1 ? sm : 1;
+    if ((a.n_steps - kd) % rs) rs = 1;
+    if (rs > 1 && near()) { rs = 1; a.sched[st] = 0; }
+    double dt = a.dt * rs;
+    int n_steps = (a.n_steps - kd) / rs;
+    if (a.refactor_all || a.dirty[st] || a.fdt[st] != dt) {
+        tree_factor<R>(a, dt, n, cb, cs, ps);
+        a.dirty[st] = 0;
+        a.fdt[st] = dt;
+    }
     int nv = a.v_count[st];
-    for (int step = 0; step < n_steps; ++step) {
+    int step = 0;
+    for (; step < n_steps; ++step) {
         R *r = a.beta + ps, *x = a.sig + ps;
         for (int i = 0; i < n; ++i) r[i] = (R)(a.V[cb + i] * (double)x[i] + dt * a.f[cs + i]);
         for (int i = n - 1; i >= 1; --i) {
@@ -570,7 +631,7 @@ __global__ void k_tree(ChainArgs<R> a) {
                 const int64_t e = st * a.maxv + nv;
                 a.v_node[e] = v;
                 a.v_seg[e] = void_segment<R>(a, s, cb + v);
-                a.v_tnuc[e] = t0 + ((double)step + frac) * dt;
+                a.v_tnuc[e] = tcur + frac * dt;
                 a.v_vol[e] = 0.0;
                 ++nv;
                 a.v_count[st] = nv;
@@ -579,9 +640,19 @@ __global__ void k_tree(ChainArgs<R> a) {
                 atomicOr(&a.status[kStatusOverflow], 1);
             }
             a.thr[cs + v] = INFINITY;
-            tree_factor<R>(a, n, cb, cs, ps);
+            tree_factor<R>(a, dt, n, cb, cs, ps);
+        }
+        tcur += dt;
+        if (rs > 1 && near()) {
+            n_steps = step + 1 + (n_steps - step - 1) * rs;
+            rs = 1;
+            dt = a.dt;
+            a.sched[st] = 0;
+            a.fdt[st] = dt;
+            tree_factor<R>(a, dt, n, cb, cs, ps);
         }
     }
+    atomicAdd(a.work, (unsigned long long)n * (unsigned long long)step);
 }
 
 // ---------------------------------------------------------------------------
@@ -668,7 +739,8 @@ ChainArgs<R> chain_args(ems_ctx *c, double dt, int n_steps) {
     a.dirty = d.dirty; a.j = d.j; a.n_seg = c->n_seg; a.face_seg = d.face_seg; a.inc_ptr = d.inc_ptr;
     a.inc_seg = d.inc_seg; a.gpar = d.par; a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx;
     a.status = d.status; a.counters = d.counters;
-    a.kr_mode = d.kr_mode; a.kdone = d.kdone;
+    a.kr_mode = d.kr_mode; a.kdone = d.kdone; a.sched = d.sched; a.fdt = d.fdt;
+    a.guard = c->sched_guard; a.work = d.work;
     a.t0p = c->graph_capturing ? d.gtime : nullptr;
     return a;
 }

@@ -114,6 +114,10 @@ ems_status finish(ems_ctx *c, ems_ttf_result *out, const std::vector<double> &tt
         }
     }
     out->node_steps = node_steps;
+    unsigned long long work = 0;
+    EMS_CUDA(c, cudaMemcpyAsync(&work, c->d.work, sizeof work, cudaMemcpyDeviceToHost, c->stream));
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+    out->node_steps_executed = (double)work;
     out->stress_ms = ms_stress;
     out->ir_ms = ms_ir;
     out->ir_iterations = it_total;
@@ -228,6 +232,7 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
     const ems_params &p = c->prm;
     const int n_out = (opts && opts->n_outer > 0) ? opts->n_outer : p.n_outer;
     if (out) out->graph_launch = 0.0;
+    EMS_CUDA(c, cudaMemsetAsync(c->d.work, 0, sizeof(unsigned long long), c->stream));
     if (opts && opts->screen) {
         EMS_TRY(ir_assemble_and_solve(c, true));
         EMS_TRY(ir_currents_and_drop(c));

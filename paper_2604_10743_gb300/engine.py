@@ -119,7 +119,8 @@ class Engine:
         return dict(ttf=ttf, drop0=d0, final_drop=fd, n_voids=nv, n_mortal=nm, drops=drops,
                     node_steps=r.node_steps, stress_ms=r.stress_ms, ir_ms=r.ir_ms,
                     ir_iterations=r.ir_iterations, ttf_mean=r.ttf_mean, ttf_std=r.ttf_std,
-                    ttf_cov=r.ttf_cov, n_censored=int(r.n_censored), graph=bool(r.graph_launch))
+                    ttf_cov=r.ttf_cov, n_censored=int(r.n_censored), graph=bool(r.graph_launch),
+                    node_steps_executed=r.node_steps_executed)
 
     def sigma(self):
         s = np.empty((self.S, self.n_stress))
@@ -168,3 +169,32 @@ class Engine:
     def state_import(self, buf):
         buf = np.ascontiguousarray(buf, np.uint8)
         self._check(self.L.ems_state_import(self.ctx, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
+
+    # -- learned surrogate (include/ems_surrogate.h) ------------------------
+    def features(self):
+        """[S * n_trees, 24] float32 device tensor of the current features."""
+        import torch
+        x = torch.empty((self.S * self.n_trees, 24), dtype=torch.float32, device="cuda")
+        self._check(self.L.ems_surrogate_features(self.ctx, ctypes.c_void_p(x.data_ptr())))
+        return x
+
+    def targets(self, t_cap, freeze=False):
+        """[S * n_trees, 2] float32 device tensor (log10 t_nuc, node position)."""
+        import torch
+        t = torch.empty((self.S * self.n_trees, 2), dtype=torch.float32, device="cuda")
+        self._check(self.L.ems_surrogate_targets(self.ctx, float(t_cap), 1 if freeze else 0,
+                                                 ctypes.c_void_p(t.data_ptr())))
+        return t
+
+    def schedule(self, mlp, bound, coarsen=16, guard=0.8):
+        """Per-tree step schedule from the network; returns (coarse trees per
+        sample, predictions)."""
+        import torch
+        n = np.zeros(self.S, np.int32)
+        pred = torch.empty((self.S * self.n_trees, 2), dtype=torch.float32, device="cuda")
+        self._check(self.L.ems_surrogate_schedule(self.ctx, mlp.h, float(bound), int(coarsen), float(guard),
+                                                  A._ptr(n, ctypes.c_int32), ctypes.c_void_p(pred.data_ptr())))
+        return n, pred
+
+    def clear_schedule(self):
+        self._check(self.L.ems_surrogate_clear(self.ctx))

@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(L):
     assert "ems_stress_advance" in decl and "ems_ttf" in decl
     for name in decl:
         assert hasattr(L, name), name
-    assert decl <= set(A.EXPORTS) | decl
+    assert decl == set(A.EXPORTS)
 
 
 def _ws(L, g, **kw):
@@ -92,3 +92,19 @@ def test_branched_trees_accepted(L):
 def test_null_context_calls_fail_cleanly(L):
     assert L.ems_ir_solve(None, None, None) == 1       # EMS_E_INVAL
     assert L.ems_destroy(None) == 1
+
+
+def test_surrogate_calls_reject_bad_arguments_without_a_device(L):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert L.ems_mlp_create(0, 0, None, ctypes.byref(h)) == 1          # n_hidden out of range
+    assert L.ems_mlp_create(9, 0, None, ctypes.byref(h)) == 1
+    assert L.ems_mlp_create(4, 0, None, None) == 1
+    assert L.ems_mlp_param_count(None) == 0
+    for M, N, K in ((0, 16, 64), (8, 8, 64), (8, 264, 64), (8, 24, 64), (8, 16, 32), (8, 16, 100)):
+        assert L.ems_gemm_bf16(ctypes.c_void_p(256), ctypes.c_void_p(256), M, N, K, None, 0, 1.0,
+                               None, None, None) == 1
+    assert L.ems_surrogate_features(None, None) == 1
+    assert L.ems_surrogate_targets(None, 10.0, 0, None) == 1
+    assert L.ems_surrogate_schedule(None, None, 0.1, 16, 0.8, None, None) == 1
+    assert L.ems_surrogate_clear(None) == 1
