@@ -212,6 +212,12 @@ def run_mine(args):
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(g, p, 1)
 
+    # learned surrogate: fused tensor-core inference over 4,096 trees x 1,024
+    # Monte Carlo samples (one schedule's worth of rows)
+    surrogate = None
+    if not args.no_surrogate:
+        surrogate = surrogate_leg(peaks, src, stream, rows=args.surrogate_rows)
+
     line = {
         "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -227,12 +233,46 @@ def run_mine(args):
         "ir_ms_per_step": res["ir_ms"], "ir_iterations_per_step": res["ir_iterations"],
         "ttf_wall_ms": ms / args.steps, "plain_fp64": plain,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "surrogate": surrogate,
     }
     if rank == 0:
         print(json.dumps(line))
     eng.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def surrogate_leg(peaks, src, stream, rows=4096 * 1024, reps=10):
+    """Inference throughput of the surrogate network (24 -> 4 x 256 -> 2,
+    BF16 tensor cores, FP32 accumulate) on `rows` feature rows resident in
+    HBM; roofline against the measured dense BF16 peak."""
+    import numpy as np
+    import torch
+    from paper_2604_10743_gb300.surrogate import Mlp
+    m = Mlp(n_hidden=4, seed=0)
+    x = torch.randn(rows, 24, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    for _ in range(3):
+        m.predict(x)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        m.predict(x)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a0.elapsed_time(a1))
+    t = float(np.median(ms))
+    flop_row = 2 * (24 * 256 + 3 * 256 * 256 + 256 * 2)        # algorithmic: 406,528 per row
+    tflops = rows * flop_row / (t / 1e3) / 1e12
+    m.close()
+    return {"rows": rows, "ms_median": round(t, 4), "rows_per_s": rows / (t / 1e3),
+            "flop_per_row": flop_row,
+            "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": round(tflops / peaks["bf16_tflops"], 4), "traffic": None,
+                         "peak_source": ("measured (MEASURED_PEAKS.json bf16_tflops, burst)" if src == "measured"
+                                         else "fallback 1.9 PFLOP/s"),
+                         "kernel": "k_mlp_fused (all layers, 256 rows per CTA)"}}
 
 
 def cpu_baseline(g, p, n_outer):
@@ -289,13 +329,23 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-only", action="store_true",
+                    help="time only the surrogate inference (profiling); prints its own JSON line")
+    ap.add_argument("--surrogate-rows", type=int, default=4096 * 1024)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     else:
         import __graft_entry__ as ge
         ge.build()
-        run_mine(args)
+        if args.surrogate_only:
+            import torch
+            peaks, src = _peaks()
+            print(json.dumps({"surrogate": surrogate_leg(peaks, src, torch.cuda.current_stream(),
+                                                         rows=args.surrogate_rows, reps=max(1, args.steps))}))
+        else:
+            run_mine(args)
 
 
 if __name__ == "__main__":

@@ -277,6 +277,15 @@ __device__ __forceinline__ int void_segment(const ChainArgs<R> &a, int s, int64_
     return best;
 }
 
+// true when any of this thread's stresses reaches the guard level
+template <typename R, int M>
+__device__ __forceinline__ bool near_guard(const R (&sg)[M], double gthr) {
+    bool near = false;
+#pragma unroll
+    for (int k = 0; k < M; ++k) near |= above<R>(sg[k], __double_as_longlong(gthr), __double2float_rd(gthr));
+    return near;
+}
+
 template <typename R, int M, bool DELTA>
 __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R, M>::value)
     k_chain(ChainArgs<R> a) {
@@ -297,7 +306,6 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     const int sm = a.sched[st];
     if (a.kr_mode[st] || sm < 0) return;           // reduced model / frozen by the schedule
     const int kd = a.kdone[st];                    // steps already done (reduced model fell back)
-    double tcur = (a.t0p ? *a.t0p : a.t0) + kd * a.dt;   // start time of the current step
 
     double tm = INFINITY;
     for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
@@ -308,27 +316,28 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
 #pragma unroll
     for (int k = 0; k < M; ++k) sg[k] = a.sig[ps + (int64_t)k * T + c];
 
-    // step schedule: rs fine steps per coarse step; a coarse tree whose
-    // stress already reaches the guard level steps finely from now on
+    // Step schedule, block-uniform and kept in shared memory (read only on
+    // rare branches): s_rs fine steps per step of length s_dt; the current
+    // run of such steps began at step s_sbase, time s_tbase.  A coarse tree
+    // whose stress already reaches the guard level steps finely from now on.
+    __shared__ double s_dt, s_tbase, s_gthr;
+    __shared__ int s_rs, s_sbase;
     int rs = sm > 1 ? sm : 1;
     if ((a.n_steps - kd) % rs) rs = 1;
-    const double gthr = a.guard * thrmin;
-    const long long g_bits = __double_as_longlong(gthr);
-    const float g_f = __double2float_rd(gthr);
-    if (rs > 1) {
-        bool near = false;
-#pragma unroll
-        for (int k = 0; k < M; ++k) near |= above<R>(sg[k], g_bits, g_f);
-        if (__syncthreads_or(near)) {
-            rs = 1;
-            if (c == 0) a.sched[st] = 0;
-        }
+    if (rs > 1 && __syncthreads_or(near_guard<R, M>(sg, a.guard * thrmin))) {
+        rs = 1;
+        if (c == 0) a.sched[st] = 0;
     }
-    double dt = a.dt * rs;
     int n_steps = (a.n_steps - kd) / rs;
 
     __shared__ int s_refac;
     if (c == 0) {
+        const double dt = a.dt * rs;
+        s_dt = dt;
+        s_rs = rs;
+        s_gthr = a.guard * thrmin;
+        s_sbase = 0;
+        s_tbase = (a.t0p ? *a.t0p : a.t0) + kd * a.dt;
         const int nv = a.v_count[st];
         s_nv = nv;
         for (int q = 0; q < nv; ++q) {
@@ -343,8 +352,9 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     }
     __syncthreads();
     if (s_refac) {
-        chain_factor<R, M, DELTA>(a, dt, n, T, c, cb, cs, ps, 0);
+        chain_factor<R, M, DELTA>(a, s_dt, n, T, c, cb, cs, ps, 0);
     } else {
+        const double dt = s_dt;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
             const int64_t pk = ps + (int64_t)k * T + c;
@@ -354,7 +364,6 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
         }
     }
     __syncthreads();
-    int executed = 0;
     unsigned long long vmask = 0ull;     // void nodes in this thread's chunk
     for (int q = 0; q < s_nv; ++q)
         if (s_node[q] / M == c) vmask |= 1ull << (s_node[q] % M);
@@ -446,6 +455,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
         bool hit = false;
 #pragma unroll
         for (int k = 0; k < M; ++k) hit |= above<R>(sg[k], thr_bits, thr_f);
+        int refac_from = -1;                        // block-uniform: refactor from this node
         if (__syncthreads_or(hit)) {
             double best = -INFINITY;
             int arg = 0x7fffffff;
@@ -464,6 +474,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                 __syncthreads();
                 if (c == 0) {
                     const int v = arg;
+                    const double dt = s_dt;
                     auto S_ = [&](int i) { return (double)a.sig[ps + (int64_t)(i % M) * T + i / M]; };
                     // previous-step stress at v from the BE relation M s^{k+1} = V s^k + dt f
                     const double gl = v > 0 ? a.g[cs + v] : 0.0, gr = v + 1 < n ? a.g[cs + v + 1] : 0.0;
@@ -478,7 +489,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                         const int64_t e = st * a.maxv + nv;
                         a.v_node[e] = v;
                         a.v_seg[e] = void_segment<R>(a, s, cb + v);
-                        a.v_tnuc[e] = tcur + frac * dt;
+                        a.v_tnuc[e] = s_tbase + ((double)(step - s_sbase) + frac) * dt;
                         a.v_vol[e] = 0.0;
                         s_node[nv] = v; s_vol[nv] = 0.0; s_coef[nv] = dt * a.Binv * a.leak[cs + v];
                         s_nv = nv + 1;
@@ -489,35 +500,40 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                     }
                     a.thr[cs + v] = INFINITY;
                 }
-                __syncthreads();
                 if (arg / M == c) vmask |= 1ull << (arg % M);
-                chain_factor<R, M, DELTA>(a, dt, n, T, c, cb, cs, ps, arg);
-                tm = INFINITY;
-                for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
-                thrmin = block_min(tm, sv);
-                thr_bits = __double_as_longlong(thrmin);
-                thr_f = __double2float_rd(thrmin);
+                refac_from = arg;
             }
         }
-        tcur += dt;
-        executed = step + 1;
-        if (rs > 1) {
+        bool promoted = false;
+        if (s_rs > 1 && __syncthreads_or(near_guard<R, M>(sg, s_gthr))) {
             // coarse tree near its critical stress: finish this call with
             // the plain solver's fine steps and keep them
-            bool near = false;
-#pragma unroll
-            for (int k = 0; k < M; ++k) near |= above<R>(sg[k], g_bits, g_f);
-            if (__syncthreads_or(near)) {
-                n_steps = step + 1 + (n_steps - step - 1) * rs;
-                rs = 1;
-                dt = a.dt;
-                if (c == 0) {
-                    a.sched[st] = 0;
-                    a.fdt[st] = dt;
-                    for (int q = 0; q < s_nv; ++q) s_coef[q] = dt * a.Binv * a.leak[cs + s_node[q]];
-                }
-                chain_factor<R, M, DELTA>(a, dt, n, T, c, cb, cs, ps, 0);
+            n_steps = step + 1 + (n_steps - step - 1) * s_rs;
+            promoted = true;
+            __syncthreads();
+            if (c == 0) {
+                s_tbase += (double)(step + 1 - s_sbase) * s_dt;
+                s_sbase = step + 1;
+                s_dt = a.dt;
+                s_rs = 1;
+                a.sched[st] = 0;
+                a.fdt[st] = a.dt;
+                for (int q = 0; q < s_nv; ++q) s_coef[q] = a.dt * a.Binv * a.leak[cs + s_node[q]];
             }
+            refac_from = 0;
+        }
+        if (refac_from >= 0) {
+            // the step is passed by value, so it must not be read from
+            // shared memory that thread 0 may still be updating
+            const double dtf = promoted ? a.dt : s_dt;
+            chain_factor<R, M, DELTA>(a, dtf, n, T, c, cb, cs, ps, refac_from);
+            tm = INFINITY;
+            for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
+            thrmin = block_min(tm, sv);
+            thr_bits = __double_as_longlong(thrmin);
+            thr_f = __double2float_rd(thrmin);
+            if (c == 0) s_gthr = a.guard * thrmin;
+            __syncthreads();
         }
     }
 #pragma unroll
@@ -525,7 +541,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     __syncthreads();
     if (c == 0) {
         for (int q = 0; q < s_nv; ++q) a.v_vol[st * a.maxv + q] = s_vol[q];
-        atomicAdd(a.work, (unsigned long long)n * (unsigned long long)executed);
+        atomicAdd(a.work, (unsigned long long)n * (unsigned long long)n_steps);
     }
 }
 
