@@ -76,7 +76,12 @@ typedef struct {
     double ir_rtol;        /* PCG relative residual target (||r|| <= rtol ||b||) */
     int    ir_max_iter;    /* PCG iteration cap (EMS_E_NOCONV beyond it) */
     int    max_voids_per_tree;  /* void slots per (tree, sample) */
+    int    ir_precond;     /* EMS_PC_AUTO: smoothed-aggregation multigrid V-cycle for systems of
+                              >= 1,024 unknowns (hierarchy built once from the initial
+                              resistances), Jacobi below; EMS_PC_JACOBI: Jacobi always */
 } ems_params;
+
+enum { EMS_PC_AUTO = 0, EMS_PC_JACOBI = 1 };       /* IR preconditioner */
 
 /*
  * Extracted power-grid netlist (Sec. III-C: a resistor network with uniform

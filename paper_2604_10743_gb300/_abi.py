@@ -18,6 +18,7 @@ STATUS_NAMES = ["EMS_OK", "EMS_E_INVAL", "EMS_E_STATE", "EMS_E_NOMEM", "EMS_E_CU
                 "EMS_E_TIMEOUT", "EMS_E_BREAKDOWN", "EMS_E_OVERFLOW"]
 EMS_F64, EMS_F32 = 0, 1
 EMS_BE, EMS_KRYLOV, EMS_AUTO = 0, 1, 2
+EMS_PC_AUTO, EMS_PC_JACOBI = 0, 1
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_int32_p = ctypes.POINTER(ctypes.c_int32)
@@ -32,7 +33,7 @@ class EmsParams(ctypes.Structure):
         ("ir_fail_frac", ctypes.c_double), ("Vdd", ctypes.c_double),
         ("precision", ctypes.c_int), ("method", ctypes.c_int), ("krylov_q", ctypes.c_int),
         ("krylov_eta", ctypes.c_double), ("ir_rtol", ctypes.c_double), ("ir_max_iter", ctypes.c_int),
-        ("max_voids_per_tree", ctypes.c_int)]
+        ("max_voids_per_tree", ctypes.c_int), ("ir_precond", ctypes.c_int)]
 
 
 class EmsGridDesc(ctypes.Structure):
@@ -155,7 +156,8 @@ class EmsError(RuntimeError):
         self.status = status
 
 
-def make_params(p, precision=EMS_F64, method=EMS_BE, ir_rtol=1e-13, ir_max_iter=20000, max_voids=16):
+def make_params(p, precision=EMS_F64, method=EMS_BE, ir_rtol=1e-13, ir_max_iter=20000, max_voids=16,
+                ir_precond=0):
     """ems_params from a parameter dict (ems_synth.default_params())."""
     e = EmsParams()
     for name, _ in EmsParams._fields_:
@@ -168,6 +170,7 @@ def make_params(p, precision=EMS_F64, method=EMS_BE, ir_rtol=1e-13, ir_max_iter=
     e.ir_rtol = ir_rtol
     e.ir_max_iter = ir_max_iter
     e.max_voids_per_tree = max_voids
+    e.ir_precond = ir_precond
     return e
 
 

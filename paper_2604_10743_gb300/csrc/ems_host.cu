@@ -71,7 +71,8 @@ ems_status validate(ems_ctx *c, const ems_params *p, const ems_grid_desc *g) {
     if (!(p->sigma_crit > 0.0) || !(p->delta > 0.0) || !(p->B_modulus > 0.0) ||
         !(p->T0 > 0.0) || !(p->D0 > 0.0) || p->n_inner < 1 || p->n_outer < 1 ||
         !(p->horizon > 0.0) || p->max_voids_per_tree < 1 ||
-        p->max_voids_per_tree > EMS_MAX_VOIDS || p->ir_max_iter < 1 || !(p->ir_rtol > 0.0))
+        p->max_voids_per_tree > EMS_MAX_VOIDS || p->ir_max_iter < 1 || !(p->ir_rtol > 0.0) ||
+        (p->ir_precond != EMS_PC_AUTO && p->ir_precond != EMS_PC_JACOBI))
         return fail(c, EMS_E_INVAL, "bad parameter value");
     if (p->precision != EMS_F64 && p->precision != EMS_F32)
         return fail(c, EMS_E_INVAL, "precision must be EMS_F64 or EMS_F32");
@@ -363,6 +364,7 @@ struct Carver {
 struct Plan {
     HostTrees tr;
     HostIR ir;
+    MGHost mg;
     std::vector<TreePack> pack;
     int64_t P = 0;
     int S = 1;
@@ -373,6 +375,9 @@ ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Pl
     if (!connected_to_pads(g)) return fail(c, EMS_E_INVAL, "node not connected to any pad");
     EMS_TRY(extract_trees(c, g, pl.tr));
     build_ir(g, pl.ir);
+    if (p->ir_precond == EMS_PC_AUTO)
+        mg_build((int)pl.ir.node_of_free.size(), pl.ir.ptr, pl.ir.col, pl.ir.ent_ptr, pl.ir.ent_seg,
+                 pl.ir.ent_diag, g->seg_R0, 1024, pl.mg);
     pl.S = g->n_samples > 0 ? g->n_samples : 1;
     pl.pack.resize(pl.tr.n_trees);
     int64_t P = 0;
@@ -456,6 +461,9 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     }
     d.feat = cv.take<float>((size_t)S * nt * EMS_MLP_FEATURES);
     d.pred = cv.take<float>((size_t)S * nt * EMS_MLP_OUTPUTS);
+    d.mg_i = cv.take<int32_t>(pl.mg.ints.size() + 1);
+    d.mg_d = cv.take<double>(pl.mg.dbls.size() + 1);
+    d.mg_sc = cv.take<double>((size_t)S * pl.mg.per_sample + 1);
     d.sched = cv.take<int32_t>((size_t)S * nt);
     d.fdt = cv.take<double>((size_t)S * nt);
     d.work = cv.take<unsigned long long>(1);
@@ -587,6 +595,20 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     EMS_CUDA(c, up(D.rhs_padV, ir.rhs_padV.data(), ir.rhs_padV.size(), st));
     EMS_CUDA(c, up(D.sink_of_free, ir.sink.data(), ir.sink.size(), st));
     EMS_CUDA(c, up(D.pad_V_of_node, ir.padV_of_node.data(), ir.padV_of_node.size(), st));
+    // multigrid hierarchy of the IR system (built from R0 in make_plan)
+    c->mg = MGDevice();
+    c->mg_blocks = 0;
+    if (pl.mg.L >= 2) {
+        EMS_CUDA(c, up(D.mg_i, pl.mg.ints.data(), pl.mg.ints.size(), st));
+        EMS_CUDA(c, up(D.mg_d, pl.mg.dbls.data(), pl.mg.dbls.size(), st));
+        c->mg.L = pl.mg.L;
+        for (int l = 0; l < EMS_MG_MAXLV; ++l) c->mg.lv[l] = pl.mg.lv[l];
+        c->mg.cinv = pl.mg.cinv;
+        c->mg.per_sample = pl.mg.per_sample;
+        c->mg.I = D.mg_i;
+        c->mg.D = D.mg_d;
+        c->mg.scratch = D.mg_sc;
+    }
     // initial guess: every free node at the mean pad voltage
     {
         double vm = 0.0;

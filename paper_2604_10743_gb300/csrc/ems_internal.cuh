@@ -22,6 +22,33 @@
 
 namespace ems {
 
+// Multigrid hierarchy of the IR system (ems_mg.cu).  Offsets index the flat
+// int / double arrays of the hierarchy (levels >= 1 hold A and its inverse
+// diagonal; levels < L-1 hold the prolongation P and restriction R = P^T)
+// and the per-sample scratch (e, t on every level, r below the finest).
+#define EMS_MG_MAXLV 8
+struct MGLevelDesc {
+    int n = 0;
+    int64_t a_ptr = 0, a_col = 0, a_val = 0, dinv = 0;
+    int64_t p_ptr = 0, p_col = 0, p_val = 0, r_ptr = 0, r_col = 0, r_val = 0;
+    int64_t e = 0, t = 0, r = 0;
+};
+struct MGHost {
+    int L = 0;                                  // levels (0: no hierarchy)
+    MGLevelDesc lv[EMS_MG_MAXLV];
+    std::vector<int32_t> ints;
+    std::vector<double> dbls;
+    int64_t cinv = 0, per_sample = 0, nnz = 0; // coarsest dense inverse offset, scratch per sample
+};
+struct MGDevice {
+    int L = 0;
+    MGLevelDesc lv[EMS_MG_MAXLV];
+    int64_t cinv = 0, per_sample = 0;
+    const int32_t *I = nullptr;
+    const double *D = nullptr;
+    double *scratch = nullptr;                  // [S][per_sample]
+};
+
 // Largest team (threads per chain) each chunk length supports: the chunk's
 // stress lives in registers (M values of R per thread) and the team must fit
 // the 64K-register file of one SM.
@@ -147,6 +174,8 @@ struct Dev {
     int32_t *gstep;                    // [1] aging steps done
     // learned surrogate: features, predictions and the step schedule
     float *feat, *pred;                // [S][n_trees][24], [S][n_trees][2]
+    int32_t *mg_i;                     // multigrid hierarchy (ints, doubles, scratch)
+    double *mg_d, *mg_sc;
     int32_t *sched;                    // [S][n_trees] step schedule: <= 1 fine, r > 1 r-times coarser, < 0 frozen
     double *fdt;                       // [S][n_trees] step the packed factors were built for
     unsigned long long *work;          // [1] node-steps the stress kernels executed
@@ -179,6 +208,8 @@ struct ems_ctx {
     ems::Dev d{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int coop_blocks = 0;       // resident CTAs for the cooperative PCG
+    int mg_blocks = 0;         // resident CTAs for the cooperative multigrid PCG
+    ems::MGDevice mg;          // IR multigrid hierarchy (mg.L = 0: Jacobi only)
     int64_t launches = 0;      // kernels this context has launched
     int cluster_ok = -1;       // cluster PCG residency (-1 unknown, 0 no, 1 yes)
     int64_t ir_iter_total = 0; // PCG iterations accumulated by ems_ttf (inner iterations)
@@ -205,8 +236,12 @@ ems_status fail(ems_ctx *c, ems_status s, const std::string &msg);
 ems_status cuda_check(ems_ctx *c, cudaError_t e, const char *what);
 size_t elem_bytes(const ems_ctx *c);
 
-// IR (ems_ir.cu)
+// IR (ems_ir.cu, ems_mg.cu)
 ems_status ir_assemble_and_solve(ems_ctx *c, bool warm);
+ems_status mg_solve(ems_ctx *c);
+void mg_build(int nf, const std::vector<int32_t> &ptr, const std::vector<int32_t> &col,
+              const std::vector<int32_t> &ent_ptr, const std::vector<int32_t> &ent_seg,
+              const std::vector<int8_t> &ent_diag, const double *R0, int min_rows, MGHost &h);
 ems_status ir_currents_and_drop(ems_ctx *c);
 ems_status check_status(ems_ctx *c);
 

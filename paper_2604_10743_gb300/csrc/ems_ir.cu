@@ -427,7 +427,9 @@ ems_status ir_assemble_and_solve(ems_ctx *c, bool warm) {
         int dev = 0, nsm = 0;
         EMS_CUDA(c, cudaGetDevice(&dev));
         EMS_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        if (c->nf <= 4096) {
+        if (c->mg.L >= 2) {
+            EMS_TRY(mg_solve(c));
+        } else if (c->nf <= 4096) {
             int threads = c->nf >= 1024 ? 1024 : ((c->nf + 31) / 32) * 32;
             k_pcg_block<<<c->S, threads, 0, st>>>(a);
             ++c->launches;
