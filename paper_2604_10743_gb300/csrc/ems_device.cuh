@@ -14,7 +14,7 @@ __device__ __forceinline__ double fmx(double a, double b, double c) { return fma
 // exclusive scan of affine maps x -> A + B x, left to right; returns the carry
 // into this thread's chunk (the composite of all earlier chunks applied to 0).
 // One barrier: every warp publishes its aggregate, then composes the
-// aggregates of the warps before it itself (at most 31 compositions).
+// aggregates of the warps before it with a warp-shuffle scan.
 template <typename R>
 __device__ __forceinline__ R scan_fwd(R A, R B, R *sA, R *sB, R *sC) {
     (void)sC;
@@ -29,7 +29,15 @@ __device__ __forceinline__ R scan_fwd(R A, R B, R *sA, R *sB, R *sC) {
     if (nw > 1) {
         if (lane == 31) { sA[w] = A; sB[w] = B; }
         __syncthreads();
-        for (int k = 0; k < w; ++k) cw = fmx(sB[k], cw, sA[k]);
+        // compose the aggregates of warps 0..w-1 with a warp scan (lane k
+        // holds warp k's map, identity from lane w on)
+        R a = lane < w ? sA[lane] : R(0), b = lane < w ? sB[lane] : R(1);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const R ao = __shfl_up_sync(full, a, d), bo = __shfl_up_sync(full, b, d);
+            if (lane >= d) { a = fmx(b, ao, a); b = b * bo; }
+        }
+        cw = __shfl_sync(full, a, 31);
     }
     const R incl = fmx(B, cw, A);
     const R ex = __shfl_up_sync(full, incl, 1);
@@ -51,7 +59,15 @@ __device__ __forceinline__ R scan_bwd(R A, R B, R *sA, R *sB, R *sC) {
     if (nw > 1) {
         if (lane == 0) { sA[32 + w] = A; sB[32 + w] = B; }
         __syncthreads();
-        for (int k = nw - 1; k > w; --k) cw = fmx(sB[32 + k], cw, sA[32 + k]);
+        // warps nw-1 .. w+1 in that order: lane j holds warp nw-1-j's map
+        const int k = nw - 1 - lane;
+        R a = k > w ? sA[32 + k] : R(0), b = k > w ? sB[32 + k] : R(1);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const R ao = __shfl_up_sync(full, a, d), bo = __shfl_up_sync(full, b, d);
+            if (lane >= d) { a = fmx(b, ao, a); b = b * bo; }
+        }
+        cw = __shfl_sync(full, a, 31);
     }
     const R incl = fmx(B, cw, A);
     const R ex = __shfl_down_sync(full, incl, 1);

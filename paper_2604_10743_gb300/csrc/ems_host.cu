@@ -270,6 +270,13 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
 // EMS_CHAIN_M (environment) pins M for tuning.
 void chain_shape(int64_t n, int prec, int *T, int *M) {
     const int64_t target = prec == EMS_F32 ? 448 : 192;
+    // FP32 chains of up to 5,120 nodes: 8 nodes per thread, <= 640 threads
+    // (the register-resident kernel)
+    if (prec == EMS_F32 && !getenv("EMS_CHAIN_M") && n <= 8 * 640) {
+        *M = 8;
+        *T = (int)(((n + 7) / 8 + 31) / 32 * 32);
+        return;
+    }
     int m = 4;
     while (m < 64 && (n + m - 1) / m > target) m *= 2;
     if (const char *e = getenv("EMS_CHAIN_M")) {

@@ -185,33 +185,100 @@ struct ChainArgs {
 // right-hand-side coefficients and carry products.  Must be called by the
 // whole block.  DELTA (increment form) stores p = 1/d', dt g, dt f, dt leak
 // instead of alpha = V/d', beta = dt f/d'.
+// 2 x 2 matrix product helpers for the parallel pivot recurrence; products
+// are rescaled by exact powers of two (only ratios of entries are used)
+struct M2 { double a, b, c, d; };                 // [[a, b], [c, d]]
+__device__ __forceinline__ M2 m2mul(const M2 &x, const M2 &y) {   // x * y, every rounding explicit
+    M2 r{__fma_rn(x.a, y.a, __dmul_rn(x.b, y.c)), __fma_rn(x.a, y.b, __dmul_rn(x.b, y.d)),
+         __fma_rn(x.c, y.a, __dmul_rn(x.d, y.c)), __fma_rn(x.c, y.b, __dmul_rn(x.d, y.d))};
+    const double mx = fmax(fmax(fabs(r.a), fabs(r.b)), fmax(fabs(r.c), fabs(r.d)));
+    if (mx > 0.0 && isfinite(mx)) {
+        const int e = ilogb(mx);
+        r.a = scalbn(r.a, -e); r.b = scalbn(r.b, -e); r.c = scalbn(r.c, -e); r.d = scalbn(r.d, -e);
+    }
+    return r;
+}
+__device__ __forceinline__ M2 m2shfl_up(const M2 &x, int d) {
+    const unsigned full = 0xffffffffu;
+    return M2{__shfl_up_sync(full, x.a, d), __shfl_up_sync(full, x.b, d), __shfl_up_sync(full, x.c, d),
+              __shfl_up_sync(full, x.d, d)};
+}
+
+// Factor M = C - dt A of one chain, then every chunk's right-hand-side
+// coefficients and carry products.  Must be called by the whole block.
+// DELTA (increment form) stores p = 1/d', dt g, dt f, dt leak instead of
+// alpha = V/d', beta = dt f/d'.
+//
+// The pivots d'_i = d_i - e_i^2 / d'_{i-1} follow from the linear recurrence
+// q_i = d_i q_{i-1} - e_i^2 q_{i-2} (d'_i = q_i / q_{i-1}), i.e. from products
+// of the matrices [[d_i, -e_i^2], [1, 0]].  Each thread multiplies its
+// chunk's matrices, a block scan of the products gives the pivot entering
+// every chunk, and each thread then runs the pivot recurrence on its own
+// nodes: O(M + log T) per thread instead of O(n) on one thread.  One
+// compiled copy per instantiation (not inlined) with every rounding written
+// out, so a refactor after a nucleation and a refactor from a checkpoint
+// give the same bits.
 template <typename R, int M, bool DELTA>
-__device__ __forceinline__ void chain_factor(const ChainArgs<R> &a, double dt, int n, int T, int c, int64_t cb,
-                                             int64_t cs, int64_t ps, int from) {
+__device__ __noinline__ void chain_factor(const ChainArgs<R> &a, double dt, int n, int T, int c, int64_t cb,
+                                          int64_t cs, int64_t ps, int from) {
+    (void)from;                       // the whole chain is refactored (cheap in parallel)
+    __shared__ double sfm[4][32];
+    const int lane = c & 31, w = c >> 5, nw = T >> 5;
     __syncthreads();
-    if (c == 0) {
-        double pprev = 0.0;
-        if (from > 0) pprev = a.pinv[ps + (int64_t)((from - 1) % M) * T + (from - 1) / M];
-        for (int i = from; i < n; ++i) {
-            const double gl = i > 0 ? a.g[cs + i] : 0.0, gr = i + 1 < n ? a.g[cs + i + 1] : 0.0;
-            const bool is_void = isinf(a.thr[cs + i]);
-            double d = a.V[cb + i] + dt * (gl + gr);
-            if (is_void) d += dt * a.leak[cs + i];
-            const double em = -dt * gl, ep = -dt * gr;
-            const double p = 1.0 / (d - em * em * pprev);
-            const int64_t pk = ps + (int64_t)(i % M) * T + i / M;
-            a.pinv[pk] = p;
-            if (DELTA) {
-                a.alpha[pk] = (R)p;
-                a.dtg[pk] = (R)(dt * gl);
-                a.dtl[pk] = is_void ? (R)(dt * a.leak[cs + i]) : R(0);
-            } else {
-                a.alpha[pk] = (R)(p * a.V[cb + i]);
-            }
-            a.gam[pk] = (R)(p * em);
-            a.uu[pk] = (R)(p * ep);
-            pprev = p;
+    auto node = [&](int i, double &d, double &em, double &ep, bool &is_void) {
+        const double gl = i > 0 ? a.g[cs + i] : 0.0, gr = i + 1 < n ? a.g[cs + i + 1] : 0.0;
+        is_void = isinf(a.thr[cs + i]);
+        d = __fma_rn(dt, __dadd_rn(gl, gr), a.V[cb + i]);
+        if (is_void) d = __fma_rn(dt, a.leak[cs + i], d);
+        em = -__dmul_rn(dt, gl);
+        ep = -__dmul_rn(dt, gr);
+    };
+    // this chunk's product (later nodes on the left)
+    M2 P{1.0, 0.0, 0.0, 1.0};
+    for (int k = 0; k < M; ++k) {
+        const int i = c * M + k;
+        if (i >= n) break;
+        double d, em, ep;
+        bool v;
+        node(i, d, em, ep, v);
+        P = m2mul(M2{d, -__dmul_rn(em, em), 1.0, 0.0}, P);
+    }
+    // inclusive scan over the chunks, then the exclusive product entering c
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const M2 o = m2shfl_up(P, d);
+        if (lane >= d) P = m2mul(P, o);
+    }
+    M2 Cw{1.0, 0.0, 0.0, 1.0};
+    if (nw > 1) {
+        if (lane == 31) { sfm[0][w] = P.a; sfm[1][w] = P.b; sfm[2][w] = P.c; sfm[3][w] = P.d; }
+        __syncthreads();
+        for (int k = 0; k < w; ++k) Cw = m2mul(M2{sfm[0][k], sfm[1][k], sfm[2][k], sfm[3][k]}, Cw);
+    }
+    const M2 incl = m2mul(P, Cw);
+    const M2 prev = m2shfl_up(incl, 1);
+    const M2 Q = lane == 0 ? Cw : prev;
+    // state entering the chunk: (q_{cM-1}, q_{cM-2}) = Q (1, 0)^T
+    double pprev = c == 0 ? 0.0 : __ddiv_rn(Q.c, Q.a);   // 1 / d'_{cM-1}
+    for (int k = 0; k < M; ++k) {
+        const int i = c * M + k;
+        if (i >= n) break;
+        double d, em, ep;
+        bool is_void;
+        node(i, d, em, ep, is_void);
+        const double p = __drcp_rn(__fma_rn(-__dmul_rn(em, em), pprev, d));
+        const int64_t pk = ps + (int64_t)k * T + c;
+        a.pinv[pk] = p;
+        if (DELTA) {
+            a.alpha[pk] = (R)p;
+            a.dtg[pk] = (R)(-em);
+            a.dtl[pk] = is_void ? (R)(dt * a.leak[cs + i]) : R(0);
+        } else {
+            a.alpha[pk] = (R)(p * a.V[cb + i]);
         }
+        a.gam[pk] = (R)(p * em);
+        a.uu[pk] = (R)(p * ep);
+        pprev = p;
     }
     __syncthreads();
     if (DELTA) {
@@ -286,8 +353,12 @@ __device__ __forceinline__ bool near_guard(const R (&sg)[M], double gthr) {
     return near;
 }
 
-template <typename R, int M, bool DELTA>
-__global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R, M>::value)
+// SMC (increment form only): the tree's per-node coefficients (p, dt g,
+// dt f, carry products) are staged in shared memory once per factorisation
+// instead of being re-read from L2 on every step, and the forward values stay
+// in registers; the arithmetic is the same as with global coefficients.
+template <typename R, int M, bool DELTA, bool SMC>
+__global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, SMC ? 1 : ChainMinBlocks<R, M>::value)
     k_chain(ChainArgs<R> a) {
     __shared__ R sA[64], sB[64], sC[32], sL[32], sR[32];
     __shared__ double sv[32];
@@ -296,9 +367,11 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
     __shared__ int s_node[EMS_MAX_VOIDS];
     __shared__ double s_vol[EMS_MAX_VOIDS], s_coef[EMS_MAX_VOIDS];
 
-    extern __shared__ float2 zu[];      // increment form: [M][T] forward values
+    extern __shared__ float2 zu[];      // increment form: [M][T] forward values (SMC: coefficients)
     const int t = a.trees[blockIdx.x], s = blockIdx.y;
     const int T = blockDim.x, c = threadIdx.x;
+    R *scr = reinterpret_cast<R *>(zu);   // SMC: p, dt g, dt f, Pf, Pb, each [M][T]
+    const int MT = M * T;
     const int64_t cb = a.toff[t];
     const int n = (int)(a.toff[t + 1] - cb);
     const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
@@ -363,6 +436,24 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
             else a.beta[pk] = i < n ? (R)(a.pinv[pk] * dt * a.f[cs + i]) : R(0);
         }
     }
+    // stage the coefficients in shared memory (after every factorisation)
+    auto stage = [&]() {
+        if constexpr (SMC) {
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int64_t pk = ps + (int64_t)k * T + c;
+                const int o = k * T + c;
+                scr[o] = a.alpha[pk];
+                scr[MT + o] = a.dtg[pk];
+                scr[2 * MT + o] = a.beta[pk];
+                scr[3 * MT + o] = a.Pf[pk];
+                scr[4 * MT + o] = a.Pb[pk];
+            }
+            __syncthreads();
+        }
+    };
+    stage();
     __syncthreads();
     unsigned long long vmask = 0ull;     // void nodes in this thread's chunk
     for (int q = 0; q < s_nv; ++q)
@@ -407,11 +498,16 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                 if (lane == 0 && w > 0) left = sL[w - 1];
                 if (lane == 31 && w + 1 < nw) right = sR[w + 1];
             }
-            const R *pG = a.dtg + ps + c, *pP = a.alpha + ps + c, *pB = a.beta + ps + c;
+            const R *pG = SMC ? scr + MT + c : a.dtg + ps + c;
+            const R *pP = SMC ? scr + c : a.alpha + ps + c;
+            const R *pB = SMC ? scr + 2 * MT + c : a.beta + ps + c;
+            const R *pF = SMC ? scr + 3 * MT + c : a.Pf + ps + c;
+            const R *pBk = SMC ? scr + 4 * MT + c : a.Pb + ps + c;
             const R g_next = c + 1 < T ? pG[1] : R(0);          // face to the next chunk
             R gk = pG[0];
             R qprev = gk * (left - sg[0]);
             R z = R(0);
+            R zr[SMC ? M : 1];
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const R nxt = k + 1 < M ? sg[k + 1] : right;
@@ -421,21 +517,25 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
                 R r = qprev - qn + pB[(int64_t)k * T];
                 if ((vmask >> k) & 1ull) r -= a.dtl[ps + (int64_t)k * T + c] * sg[k];
                 z = pk * fmx(gk, z, r);
-                zu[k * T + c] = make_float2((float)z, (float)(pk * gk1));
+                if constexpr (SMC) zr[k] = z;
+                else zu[k * T + c] = make_float2((float)z, (float)(pk * gk1));
                 qprev = qn;
                 gk = gk1;
             }
-            const R cf = scan_fwd<R>(z, a.Pf[ps + (int64_t)(M - 1) * T + c], sA, sB, sC);
+            const R cf = scan_fwd<R>(z, pF[(int64_t)(M - 1) * T], sA, sB, sC);
             R x = R(0);
-            const R *pF = a.Pf + ps + c;
 #pragma unroll
             for (int k = M - 1; k >= 0; --k) {
-                const float2 e = zu[k * T + c];
-                x = fmx((R)e.y, x, fmx(pF[(int64_t)k * T], cf, (R)e.x));
+                if constexpr (SMC) {
+                    const R gk1 = k + 1 < M ? pG[(int64_t)(k + 1) * T] : g_next;
+                    x = fmx(pP[(int64_t)k * T] * gk1, x, fmx(pF[(int64_t)k * T], cf, zr[k]));
+                } else {
+                    const float2 e = zu[k * T + c];
+                    x = fmx((R)e.y, x, fmx(pF[(int64_t)k * T], cf, (R)e.x));
+                }
                 sg[k] += x;
             }
-            const R cr = scan_bwd<R>(x, a.Pb[ps + c], sA, sB, sC);
-            const R *pBk = a.Pb + ps + c;
+            const R cr = scan_bwd<R>(x, pBk[0], sA, sB, sC);
 #pragma unroll
             for (int k = 0; k < M; ++k) sg[k] = fmx(pBk[(int64_t)k * T], cr, sg[k]);
         }
@@ -527,6 +627,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
             // shared memory that thread 0 may still be updating
             const double dtf = promoted ? a.dt : s_dt;
             chain_factor<R, M, DELTA>(a, dtf, n, T, c, cb, cs, ps, refac_from);
+            stage();
             tm = INFINITY;
             for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
             thrmin = block_min(tm, sv);
@@ -534,6 +635,253 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, ChainMinBlocks<R
             thr_f = __double2float_rd(thrmin);
             if (c == 0) s_gthr = a.guard * thrmin;
             __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * T + c] = sg[k];
+    __syncthreads();
+    if (c == 0) {
+        for (int q = 0; q < s_nv; ++q) a.v_vol[st * a.maxv + q] = s_vol[q];
+        atomicAdd(a.work, (unsigned long long)n * (unsigned long long)n_steps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Register-resident FP32 chain kernel (increment form).  Thread c keeps, for
+// its M nodes, the state, the forward values and every per-node coefficient
+// of the factorisation (p = 1/d', dt g, dt f, the carry products Pf and Pb,
+// and the nucleation threshold rounded down to FP32, or dt leak at a void
+// node) in registers, so a BE step reads no memory but the two chunk scans.
+// The nucleation test compares every node with its own threshold; void
+// growth reads the void node's stress by compile-time register selection.
+// The arithmetic of a step is the same as k_chain's increment form.
+// ---------------------------------------------------------------------------
+template <int M> struct RegMaxThreads;
+template <> struct RegMaxThreads<4> { static constexpr int value = 1024; };
+template <> struct RegMaxThreads<8> { static constexpr int value = 640; };
+
+template <int M>
+__global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainArgs<float> a) {
+    using R = float;
+    __shared__ R sA[64], sB[64], sC[32], sL[32], sR[32];
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ int s_nv, s_refac;
+    __shared__ int s_node[EMS_MAX_VOIDS];
+    __shared__ double s_vol[EMS_MAX_VOIDS], s_coef[EMS_MAX_VOIDS];
+    __shared__ double s_dt, s_tbase, s_gthr;
+    __shared__ int s_rs, s_sbase;
+
+    const int t = a.trees[blockIdx.x], s = blockIdx.y;
+    const int T = blockDim.x, c = threadIdx.x;
+    const int lane = c & 31, w = c >> 5, nw = T >> 5;
+    const int64_t cb = a.toff[t];
+    const int n = (int)(a.toff[t + 1] - cb);
+    const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
+    const int64_t st = (int64_t)s * a.n_trees + t;
+    const int sm = a.sched[st];
+    if (a.kr_mode[st] || sm < 0) return;
+    const int kd = a.kdone[st];
+
+    double tm = INFINITY;
+    for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
+    double thrmin = block_min(tm, sv);
+    R sg[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) sg[k] = a.sig[ps + (int64_t)k * T + c];
+
+    int rs = sm > 1 ? sm : 1;
+    if ((a.n_steps - kd) % rs) rs = 1;
+    if (rs > 1 && __syncthreads_or(near_guard<R, M>(sg, a.guard * thrmin))) {
+        rs = 1;
+        if (c == 0) a.sched[st] = 0;
+    }
+    int n_steps = (a.n_steps - kd) / rs;
+    if (c == 0) {
+        const double dt = a.dt * rs;
+        s_dt = dt;
+        s_rs = rs;
+        s_gthr = a.guard * thrmin;
+        s_sbase = 0;
+        s_tbase = (a.t0p ? *a.t0p : a.t0) + kd * a.dt;
+        const int nv = a.v_count[st];
+        s_nv = nv;
+        for (int q = 0; q < nv; ++q) {
+            const int v = a.v_node[st * a.maxv + q];
+            s_node[q] = v;
+            s_vol[q] = a.v_vol[st * a.maxv + q];
+            s_coef[q] = dt * a.Binv * a.leak[cs + v];
+        }
+        s_refac = (a.refactor_all || a.dirty[st] || a.fdt[st] != dt) ? 1 : 0;
+        a.dirty[st] = 0;
+        a.fdt[st] = dt;
+    }
+    __syncthreads();
+    if (s_refac) {
+        chain_factor<R, M, true>(a, s_dt, n, T, c, cb, cs, ps, 0);
+    } else {
+        const double dt = s_dt;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int i = c * M + k;
+            a.beta[ps + (int64_t)k * T + c] = i < n ? (R)(dt * a.f[cs + i]) : R(0);
+        }
+    }
+
+    R cp[M], cg[M], cbt[M], cpf[M], cpb[M], cth[M], g_next;
+    unsigned vmask = 0u;
+    auto load = [&]() {
+        __syncthreads();
+        vmask = 0u;
+        for (int q = 0; q < s_nv; ++q)
+            if (s_node[q] / M == c) vmask |= 1u << (s_node[q] % M);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int64_t pk = ps + (int64_t)k * T + c;
+            const int i = c * M + k;
+            cp[k] = a.alpha[pk];
+            cg[k] = a.dtg[pk];
+            cbt[k] = a.beta[pk];
+            cpf[k] = a.Pf[pk];
+            cpb[k] = a.Pb[pk];
+            cth[k] = ((vmask >> k) & 1u) ? a.dtl[pk] : (i < n ? __double2float_rd(a.thr[cs + i]) : INFINITY);
+        }
+        g_next = c + 1 < T ? a.dtg[ps + c + 1] : R(0);
+    };
+    load();
+
+    const unsigned full = 0xffffffffu;
+    for (int step = 0; step < n_steps; ++step) {
+        // increment form: (C - dt A) d = dt (A s + f), s += d
+        R left = __shfl_up_sync(full, sg[M - 1], 1);
+        R right = __shfl_down_sync(full, sg[0], 1);
+        if (nw > 1) {
+            if (lane == 31) sL[w] = sg[M - 1];
+            if (lane == 0) sR[w] = sg[0];
+            __syncthreads();
+            if (lane == 0 && w > 0) left = sL[w - 1];
+            if (lane == 31 && w + 1 < nw) right = sR[w + 1];
+        }
+        R gk = cg[0];
+        R qprev = gk * (left - sg[0]);
+        R z = R(0);
+        R zr[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const R nxt = k + 1 < M ? sg[k + 1] : right;
+            const R gk1 = k + 1 < M ? cg[k + 1] : g_next;
+            const R qn = gk1 * (sg[k] - nxt);
+            R r = qprev - qn + cbt[k];
+            if ((vmask >> k) & 1u) r -= cth[k] * sg[k];
+            z = cp[k] * fmx(gk, z, r);
+            zr[k] = z;
+            qprev = qn;
+            gk = gk1;
+        }
+        const R cf = scan_fwd<R>(z, cpf[M - 1], sA, sB, sC);
+        R x = R(0);
+#pragma unroll
+        for (int k = M - 1; k >= 0; --k) {
+            const R gk1 = k + 1 < M ? cg[k + 1] : g_next;
+            x = fmx(cp[k] * gk1, x, fmx(cpf[k], cf, zr[k]));
+            sg[k] += x;
+        }
+        const R cr = scan_bwd<R>(x, cpb[0], sA, sB, sC);
+#pragma unroll
+        for (int k = 0; k < M; ++k) sg[k] = fmx(cpb[k], cr, sg[k]);
+
+        // void growth by the Robin leak
+        if (vmask) {
+            for (int q = 0; q < s_nv; ++q) {
+                const int v = s_node[q];
+                if (v / M == c) {
+                    R val = R(0);
+#pragma unroll
+                    for (int k = 0; k < M; ++k)
+                        if (v % M == k) val = sg[k];
+                    s_vol[q] += s_coef[q] * (double)val;
+                }
+            }
+        }
+        // nucleation: every node against its own threshold (rounded down),
+        // exact test in FP64 on a hit
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < M; ++k) hit |= !((vmask >> k) & 1u) && sg[k] >= cth[k];
+        int refac_from = -1;
+        if (__syncthreads_or(hit)) {
+            double best = -INFINITY;
+            int arg = 0x7fffffff;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int i = c * M + k;
+                if (i < n) {
+                    const double m = (double)sg[k] - a.thr[cs + i];
+                    if (m > best) { best = m; arg = i; }
+                }
+            }
+            block_argmax(best, arg, sv, si);
+            if (best >= 0.0) {
+#pragma unroll
+                for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * T + c] = sg[k];
+                __syncthreads();
+                if (c == 0) {
+                    const int v = arg;
+                    const double dt = s_dt;
+                    auto S_ = [&](int i) { return (double)a.sig[ps + (int64_t)(i % M) * T + i / M]; };
+                    // previous-step stress at v from the BE relation M s^{k+1} = V s^k + dt f
+                    const double gl = v > 0 ? a.g[cs + v] : 0.0, gr = v + 1 < n ? a.g[cs + v + 1] : 0.0;
+                    double acc = (a.V[cb + v] + dt * (gl + gr)) * S_(v);
+                    if (v > 0) acc -= dt * gl * S_(v - 1);
+                    if (v + 1 < n) acc -= dt * gr * S_(v + 1);
+                    const double s0 = (acc - dt * a.f[cs + v]) / a.V[cb + v];
+                    const double m0 = s0 - a.thr[cs + v];
+                    const double frac = m0 < 0.0 ? -m0 / (best - m0) : 0.0;
+                    const int nv = s_nv;
+                    if (nv < a.maxv) {
+                        const int64_t e = st * a.maxv + nv;
+                        a.v_node[e] = v;
+                        a.v_seg[e] = void_segment<R>(a, s, cb + v);
+                        a.v_tnuc[e] = s_tbase + ((double)(step - s_sbase) + frac) * dt;
+                        a.v_vol[e] = 0.0;
+                        s_node[nv] = v; s_vol[nv] = 0.0; s_coef[nv] = dt * a.Binv * a.leak[cs + v];
+                        s_nv = nv + 1;
+                        a.v_count[st] = nv + 1;
+                        atomicAdd(&a.counters[0], 1);
+                    } else {
+                        atomicOr(&a.status[kStatusOverflow], 1);
+                    }
+                    a.thr[cs + v] = INFINITY;
+                }
+                refac_from = arg;
+            }
+        }
+        bool promoted = false;
+        if (s_rs > 1 && __syncthreads_or(near_guard<R, M>(sg, s_gthr))) {
+            // coarse tree near its critical stress: finish this call with
+            // the plain solver's fine steps and keep them
+            n_steps = step + 1 + (n_steps - step - 1) * s_rs;
+            promoted = true;
+            __syncthreads();
+            if (c == 0) {
+                s_tbase += (double)(step + 1 - s_sbase) * s_dt;
+                s_sbase = step + 1;
+                s_dt = a.dt;
+                s_rs = 1;
+                a.sched[st] = 0;
+                a.fdt[st] = a.dt;
+                for (int q = 0; q < s_nv; ++q) s_coef[q] = a.dt * a.Binv * a.leak[cs + s_node[q]];
+            }
+            refac_from = 0;
+        }
+        if (refac_from >= 0) {
+            const double dtf = promoted ? a.dt : s_dt;
+            chain_factor<R, M, true>(a, dtf, n, T, c, cb, cs, ps, refac_from);
+            tm = INFINITY;
+            for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
+            thrmin = block_min(tm, sv);
+            if (c == 0) s_gthr = a.guard * thrmin;
+            load();
         }
     }
 #pragma unroll
@@ -761,6 +1109,21 @@ ChainArgs<R> chain_args(ems_ctx *c, double dt, int n_steps) {
     return a;
 }
 
+template <typename R, int M, bool D, bool SM>
+cudaError_t launch_chain(dim3 grid, int T, size_t smem, cudaStream_t st, const ChainArgs<R> &a) {
+    if constexpr (SM && !D) {
+        return cudaErrorInvalidValue;                 // no shared-memory variant of the state form
+    } else {
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(k_chain<R, M, D, SM>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_chain<R, M, D, SM><<<grid, T, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+}
+
 // FP64 solves the state directly; FP32 solves for the increment so that the
 // rounding of its coefficients cannot drift the conserved slow modes
 template <typename R>
@@ -772,26 +1135,34 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
         a.n_bucket = (int)b.trees.size();
         if (b.chain) {
             dim3 grid((unsigned)b.trees.size(), c->S);
-            const size_t smem = kDelta ? sizeof(float2) * (size_t)b.T * b.M : 0;
-            if (smem > 48 * 1024) {
-                cudaError_t e = cudaSuccess;
-                switch (b.M) {
-                    case 4: e = cudaFuncSetAttribute(k_chain<R, 4, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-                    case 8: e = cudaFuncSetAttribute(k_chain<R, 8, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-                    case 16: e = cudaFuncSetAttribute(k_chain<R, 16, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-                    case 32: e = cudaFuncSetAttribute(k_chain<R, 32, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-                    case 64: e = cudaFuncSetAttribute(k_chain<R, 64, kDelta>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+            cudaError_t e = cudaSuccess;
+            if constexpr (kDelta) {
+                if ((b.M == 4 && b.T <= 1024) || (b.M == 8 && b.T <= 640)) {
+                    if (b.M == 4) k_chain_reg<4><<<grid, b.T, 0, c->stream>>>(a);
+                    else k_chain_reg<8><<<grid, b.T, 0, c->stream>>>(a);
+                    ++c->launches;
+                    EMS_CUDA(c, cudaGetLastError());
+                    continue;
                 }
-                EMS_CUDA(c, e);
             }
+            // increment form: coefficients in shared memory while they fit
+            const size_t smem_c = kDelta ? 5 * sizeof(R) * (size_t)b.T * b.M : 0;
+            const bool smc = kDelta && smem_c <= 200 * 1024;
+            const size_t smem = smc ? smem_c : (kDelta ? sizeof(float2) * (size_t)b.T * b.M : 0);
             switch (b.M) {
-                case 4: k_chain<R, 4, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
-                case 8: k_chain<R, 8, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
-                case 16: k_chain<R, 16, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
-                case 32: k_chain<R, 32, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
-                case 64: k_chain<R, 64, kDelta><<<grid, b.T, smem, c->stream>>>(a); break;
+                case 4: e = smc ? launch_chain<R, 4, kDelta, true>(grid, b.T, smem, c->stream, a)
+                                : launch_chain<R, 4, kDelta, false>(grid, b.T, smem, c->stream, a); break;
+                case 8: e = smc ? launch_chain<R, 8, kDelta, true>(grid, b.T, smem, c->stream, a)
+                                : launch_chain<R, 8, kDelta, false>(grid, b.T, smem, c->stream, a); break;
+                case 16: e = smc ? launch_chain<R, 16, kDelta, true>(grid, b.T, smem, c->stream, a)
+                                 : launch_chain<R, 16, kDelta, false>(grid, b.T, smem, c->stream, a); break;
+                case 32: e = smc ? launch_chain<R, 32, kDelta, true>(grid, b.T, smem, c->stream, a)
+                                 : launch_chain<R, 32, kDelta, false>(grid, b.T, smem, c->stream, a); break;
+                case 64: e = smc ? launch_chain<R, 64, kDelta, true>(grid, b.T, smem, c->stream, a)
+                                 : launch_chain<R, 64, kDelta, false>(grid, b.T, smem, c->stream, a); break;
                 default: return fail(c, EMS_E_STATE, "unsupported chunk length");
             }
+            EMS_CUDA(c, e);
             ++c->launches;
         } else {
             const int64_t items = (int64_t)b.trees.size() * c->S;   // (tree, sample) pairs
