@@ -270,12 +270,16 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
 // EMS_CHAIN_M (environment) pins M for tuning.
 void chain_shape(int64_t n, int prec, int *T, int *M) {
     const int64_t target = prec == EMS_F32 ? 448 : 192;
-    // FP32 chains of up to 5,120 nodes: 8 nodes per thread, <= 640 threads
-    // (the register-resident kernel)
-    if (prec == EMS_F32 && !getenv("EMS_CHAIN_M") && n <= 8 * 640) {
-        *M = 8;
-        *T = (int)(((n + 7) / 8 + 31) / 32 * 32);
-        return;
+    // FP32 chains the register-resident kernel holds: 16 nodes per thread
+    // (<= 384 threads) for long chains, 8 (<= 640 threads) for short ones
+    if (prec == EMS_F32) {
+        int want = n > 2048 ? 16 : 8;
+        if (const char *e = getenv("EMS_CHAIN_M")) want = atoi(e);
+        for (int m : {want, 16, 8}) {
+            const int64_t lim = m == 16 ? 384 : m == 8 ? 640 : m == 4 ? 1024 : 0;
+            const int64_t t = ((n + m - 1) / m + 31) / 32 * 32;
+            if (t <= lim) { *T = (int)t; *M = m; return; }
+        }
     }
     int m = 4;
     while (m < 64 && (n + m - 1) / m > target) m *= 2;

@@ -659,6 +659,7 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, SMC ? 1 : ChainM
 template <int M> struct RegMaxThreads;
 template <> struct RegMaxThreads<4> { static constexpr int value = 1024; };
 template <> struct RegMaxThreads<8> { static constexpr int value = 640; };
+template <> struct RegMaxThreads<16> { static constexpr int value = 384; };
 
 template <int M>
 __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainArgs<float> a) {
@@ -751,17 +752,17 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
     load();
 
     const unsigned full = 0xffffffffu;
+    // warp-boundary stresses for the halo exchange are published before the
+    // barrier that ends every step (and once here)
+    if (lane == 31) sL[w] = sg[M - 1];
+    if (lane == 0) sR[w] = sg[0];
+    __syncthreads();
     for (int step = 0; step < n_steps; ++step) {
         // increment form: (C - dt A) d = dt (A s + f), s += d
         R left = __shfl_up_sync(full, sg[M - 1], 1);
         R right = __shfl_down_sync(full, sg[0], 1);
-        if (nw > 1) {
-            if (lane == 31) sL[w] = sg[M - 1];
-            if (lane == 0) sR[w] = sg[0];
-            __syncthreads();
-            if (lane == 0 && w > 0) left = sL[w - 1];
-            if (lane == 31 && w + 1 < nw) right = sR[w + 1];
-        }
+        if (lane == 0 && w > 0) left = sL[w - 1];
+        if (lane == 31 && w + 1 < nw) right = sR[w + 1];
         R gk = cg[0];
         R qprev = gk * (left - sg[0]);
         R z = R(0);
@@ -804,10 +805,13 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
             }
         }
         // nucleation: every node against its own threshold (rounded down),
-        // exact test in FP64 on a hit
+        // exact test in FP64 on a hit.  The barrier also publishes the
+        // boundary stresses for the next step's halo.
         bool hit = false;
 #pragma unroll
         for (int k = 0; k < M; ++k) hit |= !((vmask >> k) & 1u) && sg[k] >= cth[k];
+        if (lane == 31) sL[w] = sg[M - 1];
+        if (lane == 0) sR[w] = sg[0];
         int refac_from = -1;
         if (__syncthreads_or(hit)) {
             double best = -INFINITY;
@@ -1137,9 +1141,10 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
             dim3 grid((unsigned)b.trees.size(), c->S);
             cudaError_t e = cudaSuccess;
             if constexpr (kDelta) {
-                if ((b.M == 4 && b.T <= 1024) || (b.M == 8 && b.T <= 640)) {
+                if ((b.M == 4 && b.T <= 1024) || (b.M == 8 && b.T <= 640) || (b.M == 16 && b.T <= 384)) {
                     if (b.M == 4) k_chain_reg<4><<<grid, b.T, 0, c->stream>>>(a);
-                    else k_chain_reg<8><<<grid, b.T, 0, c->stream>>>(a);
+                    else if (b.M == 8) k_chain_reg<8><<<grid, b.T, 0, c->stream>>>(a);
+                    else k_chain_reg<16><<<grid, b.T, 0, c->stream>>>(a);
                     ++c->launches;
                     EMS_CUDA(c, cudaGetLastError());
                     continue;
