@@ -42,6 +42,7 @@ struct MGHost {
 };
 struct MGDevice {
     int L = 0;
+    int small = 1024;                           // grid mode: block 0 alone runs levels this small
     MGLevelDesc lv[EMS_MG_MAXLV];
     int64_t cinv = 0, per_sample = 0;
     const int32_t *I = nullptr;
@@ -209,6 +210,7 @@ struct ems_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int coop_blocks = 0;       // resident CTAs for the cooperative PCG
     int mg_blocks = 0;         // resident CTAs for the cooperative multigrid PCG
+    int mg_cluster = 0;        // CTAs per cluster of the cluster multigrid PCG (0 unknown, -1 none)
     ems::MGDevice mg;          // IR multigrid hierarchy (mg.L = 0: Jacobi only)
     int64_t launches = 0;      // kernels this context has launched
     int cluster_ok = -1;       // cluster PCG residency (-1 unknown, 0 no, 1 yes)

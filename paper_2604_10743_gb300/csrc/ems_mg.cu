@@ -17,13 +17,18 @@
 // smoothing (2/3), which keeps the preconditioner symmetric positive
 // definite.  Two kernels: one CTA per sample for systems of <= 4,096
 // unknowns; a cooperative grid for larger ones, where the levels above 1,024
-// unknowns run grid-wide between bounded grid barriers and block 0 runs the
-// small levels alone.  All sums are fixed-order (bitwise reproducible).
+// unknowns (MGDevice::small) run grid-wide between bounded grid barriers and
+// block 0 runs the small levels alone.  All sums are fixed-order (bitwise reproducible).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "ems_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ems {
 
@@ -31,7 +36,6 @@ namespace {
 
 constexpr double kStrength = 0.08;
 constexpr int kCoarsest = 512;
-constexpr int kSmallLevel = 1024;       // grid mode: block 0 runs levels this small
 constexpr double kSmooth = 2.0 / 3.0;   // damped-Jacobi weight of the V-cycle
 
 struct SpM {
@@ -531,7 +535,7 @@ __device__ bool vcycle_grid(const MGArgs &a, const double *val0, const double *d
                             double *z) {
     const int L = a.g.L;
     int lb = 0;                       // first level small enough for one CTA
-    while (lb < L - 1 && a.g.lv[lb].n > kSmallLevel) ++lb;
+    while (lb < L - 1 && a.g.lv[lb].n > a.g.small) ++lb;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     auto gsy = [&]() { return gsync(a.bar, a.status); };
     auto bs = []() { __syncthreads(); return true; };
@@ -551,7 +555,7 @@ __device__ bool vcycle_grid(const MGArgs &a, const double *val0, const double *d
 }
 
 // Mode B with the multigrid preconditioner: cooperative grid, samples in turn
-__global__ void __launch_bounds__(512) k_pcg_grid_mg(MGArgs a) {
+__global__ void __launch_bounds__(512, 2) k_pcg_grid_mg(MGArgs a) {
     __shared__ double sh[96];
     const int nf = a.nf, G = gridDim.x;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gs = G * blockDim.x;
@@ -614,6 +618,99 @@ __global__ void __launch_bounds__(512) k_pcg_grid_mg(MGArgs a) {
     }
 }
 
+// Mode C: one thread-block cluster per sample, for several samples at once
+// (one sample is faster on the whole grid: 16 SMs cannot hide the gather
+// latency of the finest level).  Cluster barriers are hardware barriers (no
+// spin), sums go through distributed shared memory in rank order, and every
+// level of the V-cycle runs across the cluster.
+template <int K>
+__device__ void csum(double (&v)[K], double *sh, double *slot, cg::cluster_group &cl) {
+    bsum<K>(v, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < K; ++q) slot[q] = v[q];
+    cl.sync();
+    const int CL = (int)cl.num_blocks();
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] = 0.0;
+    for (int r = 0; r < CL; ++r) {
+        const double *o = cl.map_shared_rank(slot, r);
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[q] += o[q];
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_pcg_cluster_mg(MGArgs a) {
+    __shared__ double sh[96];
+    __shared__ double slots[2][4];                 // alternate so a slot is not rewritten while read
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int s = blockIdx.x / CL, nf = a.nf;
+    const int gid = rank * blockDim.x + threadIdx.x, gs = CL * blockDim.x;
+    const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf, *dinv = a.dinv + (size_t)s * nf;
+    double *x = a.x + (size_t)s * nf, *r = a.r + (size_t)s * nf, *p = a.p + (size_t)s * nf;
+    double *q = a.q + (size_t)s * nf, *z = a.z + (size_t)s * nf;
+    double *sc = a.g.scratch + (size_t)s * a.g.per_sample;
+    auto csy = [&]() { cl.sync(); return true; };
+    const int L = a.g.L;
+    auto vcyc = [&]() {
+        vcycle(a, val, dinv, sc, 0, L - 1, r, z, gid, gs, csy);
+        coarse(a, sc, gid, gs, csy);
+        vcycle_up(a, val, dinv, sc, L - 2, 0, r, z, 0, gid, gs, csy);
+    };
+    int par = 0;
+    double v2[2] = {0.0, 0.0};
+    for (int i = gid; i < nf; i += gs) {
+        const double ri = b[i] - csr_dot(a.ptr, a.col, val, x, i);
+        r[i] = ri;
+        v2[0] += ri * ri;
+        v2[1] += b[i] * b[i];
+    }
+    csum<2>(v2, sh, slots[par], cl); par ^= 1;
+    double rr = v2[0];
+    const double tol2 = a.rtol * a.rtol * v2[1];
+    int it = 0;
+    double rz = 0.0;
+    if (rr > tol2) {
+        cl.sync();                                     // r complete
+        vcyc();
+        double v1[1] = {0.0};
+        for (int i = gid; i < nf; i += gs) { p[i] = z[i]; v1[0] += r[i] * z[i]; }
+        csum<1>(v1, sh, slots[par], cl); par ^= 1;     // also: p complete
+        rz = v1[0];
+    }
+    while (rr > tol2 && it < a.max_iter) {
+        double v1[1] = {0.0};
+        for (int i = gid; i < nf; i += gs) {
+            const double qi = csr_dot(a.ptr, a.col, val, p, i);
+            q[i] = qi;
+            v1[0] += p[i] * qi;
+        }
+        csum<1>(v1, sh, slots[par], cl); par ^= 1;
+        const double alpha = rz / v1[0];
+        for (int i = gid; i < nf; i += gs) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+        }
+        cl.sync();                                     // r complete
+        vcyc();
+        double w2[2] = {0.0, 0.0};
+        for (int i = gid; i < nf; i += gs) { w2[0] += r[i] * z[i]; w2[1] += r[i] * r[i]; }
+        csum<2>(w2, sh, slots[par], cl); par ^= 1;
+        const double beta = w2[0] / rz;
+        rz = w2[0];
+        rr = w2[1];
+        for (int i = gid; i < nf; i += gs) p[i] = z[i] + beta * p[i];
+        cl.sync();                                     // p complete
+        ++it;
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        a.iters[s] = it;
+        if (rr > tol2) atomicOr(&a.status[kStatusNoConv], 1);
+    }
+    cl.sync();                                         // no CTA leaves while its slots may be read
+}
+
 }  // namespace
 
 // PCG with the multigrid preconditioner (the hierarchy must exist)
@@ -627,11 +724,42 @@ ems_status mg_solve(ems_ctx *c) {
     a.rtol = c->prm.ir_rtol; a.max_iter = c->prm.ir_max_iter;
     a.iters = d.ir_iters; a.status = d.status; a.red = d.red; a.bar = d.gbar;
     a.g = c->mg;
+    if (const char *e = getenv("EMS_MG_SMALL")) a.g.small = std::max(0, atoi(e));   // tuning override
     if (c->nf <= 4096) {
         const int threads = c->nf >= 1024 ? 1024 : ((c->nf + 31) / 32) * 32;
         k_pcg_block_mg<<<c->S, threads, 0, st>>>(a);
         ++c->launches;
         EMS_CUDA(c, cudaGetLastError());
+        return EMS_OK;
+    }
+    // one cluster per sample when the device can hold one of 16 (or 8) CTAs
+    if (c->mg_cluster == 0) {
+        c->mg_cluster = -1;
+        if (cudaFuncSetAttribute(k_pcg_cluster_mg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+            cudaGetLastError();
+        for (int cs : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(cs); cfg.blockDim = dim3(1024); cfg.attrs = at; cfg.numAttrs = 1;
+            int nclus = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclus, k_pcg_cluster_mg, &cfg) == cudaSuccess && nclus > 0) {
+                c->mg_cluster = cs;
+                break;
+            }
+            cudaGetLastError();
+        }
+    }
+    if (c->mg_cluster > 0 && c->S > 1) {              // samples as parallel clusters
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = c->mg_cluster; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(c->mg_cluster * c->S); cfg.blockDim = dim3(1024); cfg.stream = st;
+        cfg.attrs = at; cfg.numAttrs = 1;
+        EMS_CUDA(c, cudaLaunchKernelEx(&cfg, k_pcg_cluster_mg, a));
+        ++c->launches;
         return EMS_OK;
     }
     if (c->mg_blocks == 0) {

@@ -43,11 +43,14 @@ def _void_sets(eng, ref, sample=0):
 
 
 def test_ir_solve_tiny_and_grids():
-    # 60 unknowns (one CTA), 4,080 (one CTA), 65,472 (cluster, FP32 inner
-    # CG with FP64 refinement)
-    for g in (es.tiny_grid(), es.mid_grid(N=64, with_map=False), es.mid_grid(with_map=False)):
+    # 60 unknowns (one CTA, Jacobi), 4,080 (one CTA, multigrid), 65,472
+    # (cooperative grid, multigrid), and 65,472 with the Jacobi-only option
+    # (pipelined grid CG)
+    cases = [(es.tiny_grid(), 0), (es.mid_grid(N=64, with_map=False), 0), (es.mid_grid(with_map=False), 0),
+             (es.mid_grid(with_map=False), 1)]
+    for g, pc in cases:
         p = es.default_params()
-        eng = _engine(p, g)
+        eng = _engine(p, g, ir_precond=pc)
         u, d = eng.ir_solve()
         uo = F.ir_solve(g, g["seg_R0"])
         assert np.abs(u[0] - uo).max() < 1e-11
@@ -55,6 +58,20 @@ def test_ir_solve_tiny_and_grids():
         jo = F.current_density(g, uo, g["seg_R0"])
         assert _relerr(eng.currents()[0], jo) < 1e-9
         eng.close()
+
+
+def test_ir_solve_several_samples_large_grid():
+    # 9,212 unknowns x 3 Monte Carlo samples: one thread-block cluster per
+    # sample; the factors touch kappa and sigma_crit only, so every sample has
+    # the oracle's voltages
+    g = es.grid.surrogate_grid(seed=7, N=96, n_samples=3)
+    eng = _engine(es.default_params(), g)
+    u, d = eng.ir_solve()
+    uo = F.ir_solve(g, g["seg_R0"])
+    for s in range(3):
+        assert np.abs(u[s] - uo).max() < 1e-11
+        assert abs(d[s] - F.max_drop(uo, 1.0)) < 1e-11
+    eng.close()
 
 
 def test_tiny_full_ttf_fp64():
