@@ -165,7 +165,7 @@ def run_mine(args):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src if src == "measured" else "fallback 6.8 TB/s",
-            "kernel": "k_chain (stress advance, one launch = 256 BE steps of all trees)",
+            "kernel": "k_chain_reg<16> (stress advance, one launch = 256 BE steps of all trees)",
             "alg_bytes_per_launch": alg_bytes_launch, "launch_ms": round(per_launch_ms, 4)}
 
     # end to end through the public API with host buffers: load the netlist
