@@ -212,6 +212,13 @@ def run_mine(args):
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(g, p, 1)
 
+    mc = None
+    if not args.no_mc:
+        mc = mc_leg(p, peaks, src, stream)
+    krylov = None
+    if args.krylov:
+        krylov = krylov_leg(g, p, stream, res)
+
     # learned surrogate: fused tensor-core inference over 4,096 trees x 1,024
     # Monte Carlo samples (one schedule's worth of rows)
     surrogate = None
@@ -233,7 +240,7 @@ def run_mine(args):
         "ir_ms_per_step": res["ir_ms"], "ir_iterations_per_step": res["ir_iterations"],
         "ttf_wall_ms": ms / args.steps, "plain_fp64": plain,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "surrogate": surrogate,
+        "surrogate": surrogate, "monte_carlo": mc, "krylov": krylov,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -273,6 +280,84 @@ def surrogate_leg(peaks, src, stream, rows=4096 * 1024, reps=10):
                          "peak_source": ("measured (MEASURED_PEAKS.json bf16_tflops, burst)" if src == "measured"
                                          else "fallback 1.9 PFLOP/s"),
                          "kernel": "k_mlp_fused (all layers, 256 rows per CTA)"}}
+
+
+def mc_leg(p, peaks, src, stream, n_samples=1024, reps=2):
+    """Batched Monte Carlo: the 8 x 8 grid with uneven trees (32-1,024 cells
+    per stripe) and n_samples lognormal kappa / sigma_crit samples, all
+    advanced in one graph-captured TTF run; the oracle times one sample."""
+    import torch
+    import ems_synth as es
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300.engine import Engine
+    g = es.mc_grid(n_samples=n_samples)
+    eng = Engine(p, g, precision=EMS_F32)
+    init = eng.state_export()
+    eng.ttf()                                        # warm-up (captures the graph)
+    torch.cuda.synchronize()
+    ms, r = [], None
+    for _ in range(reps):
+        eng.state_import(init)
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        r = eng.ttf()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a0.elapsed_time(a1))
+    t = min(ms)
+    out = {"workload": "8x8 grid, stripes of 32-1,024 FD cells, %d Monte Carlo samples (20 %% CoV kappa and "
+                       "sigma_crit per segment), 64 x 256 BE steps" % n_samples,
+           "samples": n_samples, "stress_nodes_per_sample": eng.n_stress, "ttf_wall_ms": round(t, 2),
+           "node_steps_per_s": r["node_steps"] / (t / 1e3), "stress_ms": round(r["stress_ms"], 2),
+           "ir_ms": round(r["ir_ms"], 2), "ttf_mean_s": r["ttf_mean"], "ttf_cov": r["ttf_cov"],
+           "censored": r["n_censored"], "graph": r["graph"]}
+    eng.close()
+    from oracle import flow as F
+    g1 = es.mc_grid(n_samples=n_samples)
+    g1["trees"] = F.build_trees(g1)
+    t0 = time.perf_counter()
+    ro = F.run_ttf(g1, p, sample=0)
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": ro["node_steps"] / dt, "unit": "node-steps/s", "cores": os.cpu_count(),
+                           "kind": "oracle", "sample": "sample 0 of the same workload, full TTF run",
+                           "seconds": round(dt, 2)}
+    return out
+
+
+def krylov_leg(g, p, stream, be):
+    """The rational Krylov reduced model (method AUTO) on the bench workload:
+    TTF wall time and its difference from the BE run; the oracle times its
+    Krylov stepper over one aging step of the same grid."""
+    import torch
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300 import _abi as A
+    from paper_2604_10743_gb300.engine import Engine
+    eng = Engine(p, g, precision=EMS_F32, method=A.EMS_AUTO)
+    init = eng.state_export()
+    eng.ttf()
+    torch.cuda.synchronize()
+    eng.state_import(init)
+    a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    r = eng.ttf()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t = a0.elapsed_time(a1)
+    eng.close()
+    out = {"ttf_wall_ms": round(t, 2), "stress_ms": round(r["stress_ms"], 2), "ir_ms": round(r["ir_ms"], 2),
+           "node_steps_per_s": r["node_steps"] / (t / 1e3),
+           "final_drop_rel_diff_vs_be": abs(r["final_drop"][0] - be["final_drop"][0]) / be["final_drop"][0]}
+    from oracle import flow as F, krylov as K
+    g1 = dict(g)
+    g1["trees"] = F.build_trees(g1)
+    t0 = time.perf_counter()
+    ro = F.run_ttf(g1, p, n_outer=1, stepper=K.KrylovStepper(q=int(p.get("krylov_q", 10)), eta=1.0,
+                                                            n_threads=os.cpu_count()))
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": ro["node_steps"] / dt, "unit": "node-steps/s (full-order equivalent)",
+                           "cores": os.cpu_count(), "kind": "oracle",
+                           "sample": "1 of 64 aging steps, all 512 trees, Krylov stepper", "seconds": round(dt, 2)}
+    return out
 
 
 def cpu_baseline(g, p, n_outer):
@@ -330,6 +415,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-mc", action="store_true")
+    ap.add_argument("--krylov", action="store_true", help="also time the Krylov reduced model (slow oracle leg)")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="time only the surrogate inference (profiling); prints its own JSON line")
     ap.add_argument("--surrogate-rows", type=int, default=4096 * 1024)
