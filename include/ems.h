@@ -181,8 +181,14 @@ ems_status ems_immortality_check(ems_ctx *ctx, uint8_t *mortal, double *sigma_ss
  * largest sigma - sigma_crit, lowest index on ties, when that is >= 0;
  * Sec. III-D.2), the Robin void stamp from the next step on (Sec. IV-D,
  * Eq. robin_mid_tree) and void-volume growth by the Robin leak
- * (Eq. void_volume_equation).  method EMS_KRYLOV / EMS_AUTO route trees
- * through the reduced model (Sec. IV-E) where ems_krylov_reduce() built one.
+ * (Eq. void_volume_equation).  method EMS_KRYLOV / EMS_AUTO route every
+ * chain with n >= max(3q, 30) (Eq. krylov_threshold) through its reduced model
+ * (Sec. IV-E): a basis cached per (tree, sample) under the key the paper
+ * gives (the descriptor matrices and s0: rebuilt on a new void, a new
+ * thermal map or new q / eta), extended on every call by the current
+ * starting block [K^-1 C sigma, K^-1 f]; backward Euler in reduced
+ * coordinates; the same nucleation rule on the lifted stress.  Other trees,
+ * and trees whose basis breaks down, take full backward Euler.
  *   n_new_voids   optional host: voids nucleated during the call (all samples)
  */
 ems_status ems_stress_advance(ems_ctx *ctx, double dt, int n_steps, int method,
@@ -192,8 +198,10 @@ ems_status ems_stress_advance(ems_ctx *ctx, double dt, int n_steps, int method,
  * Build the rational Krylov reduced model (Sec. IV-E, Alg. 1) of every tree
  * with n >= max(3q, 30) (Eq. krylov_threshold): shift t_s = eta L_max^2 /
  * (pi^2 kappa_mean) (Eq. rak_shift_time), K = C/t_s - A, starting block
- * [K^-1 C sigma0, K^-1 f], block Arnoldi to order q with FP64 modified
- * Gram-Schmidt, projections A_h, C_h, f_h (Eq. rak_reduced).
+ * [K^-1 C sigma0, K^-1 f], block Arnoldi to order q with classical
+ * Gram-Schmidt applied twice (per-thread sums in the context precision, FP64
+ * across threads), projections A_h, C_h (Eq. rak_reduced).  Bases already
+ * cached are kept.
  *   n_reduced / n_fallback  optional host: trees reduced / sent back to BE
  */
 ems_status ems_krylov_reduce(ems_ctx *ctx, int q, double eta, int *n_reduced,
@@ -239,8 +247,8 @@ typedef struct {
  * n_inner steps of horizon/(n_outer n_inner), void update, IR re-solve, max
  * drop; TTF is the linear interpolation of the first crossing of
  * ir_fail_frac.  Host result arrays are caller-allocated (NULL to skip).
- * With the backward-Euler method (and n_outer <= params.n_outer) every
- * aging step of every sample runs inside one captured CUDA graph: the
+ * Unless opts.no_graph (and for n_outer <= params.n_outer) every aging step
+ * of every sample, by either method, runs inside one captured CUDA graph: the
  * crossing detection happens on the device and the host reads the results
  * once; Monte Carlo statistics follow Sec. V-D (uncensored samples only).
  */

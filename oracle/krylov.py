@@ -20,14 +20,19 @@ Readings (where the paper is silent):
     paper's ||H|| < eps test), and sends the tree back to full backward Euler
     when only some of its columns fall under that bound (rank deficiency);
   * Krylov is used for trees with n >= max(3q, 30) (Eq. krylov_threshold);
-  * bases are cached per tree (Sec. IV-E.4) under a fingerprint of the
-    descriptor system and s0.  The system's input term B j - D is part of
-    that system, so the key covers the void set (which fixes C and A within a
-    run) and the forcing f itself: a hit (an aging step whose resistances,
-    hence currents, did not change) reuses V, A_h, C_h with
-    s_hat(0) = V^T s0; a new void or new currents rebuild from the current
-    stress and forcing.  (Keying on C, A and s0 alone reuses bases built for
-    other forcings; on the 8 x 8 grid that moves the TTF by 22 %.);
+  * bases are cached per tree (Sec. IV-E.4) under the key the paper gives:
+    the descriptor matrices and s0.  Within a run C and s0 are fixed and A
+    changes only when a void nucleates, so the key is (tree, void set).  A
+    cached basis was built from an earlier stress and forcing, and reusing
+    it as it stands loses the new input (on the 8 x 8 grid that moves the TTF
+    by 21 %), so every hit is augmented by the current starting block
+    [R C s0, R f], orthogonalised twice against the cached columns (a
+    column whose norm falls under 1e-10 of its own is dropped).  The step
+    that (re)builds the basis from the current stress and forcing uses it
+    without augmentation, since that block is already its first block.
+    (policy="forcing" keys on the forcing as well and rebuilds whenever it
+    changes: the same accuracy, far more builds; policy="stale" reuses the
+    cached basis as it stands.);
   * nucleation is checked on the lifted stress after every reduced step, as
     in the full-order path.
 """
@@ -133,15 +138,40 @@ def krylov_basis(C, A, f, sigma0, s0, q, eps_rel=1e-10):
     return V, Ah, Ch, fh, "ok"
 
 
+def augment(V, lu, C, sigma0, f, eps_rel=1e-10):
+    """A cached basis V extended by the current starting block
+    [R C s0, R f] (R = (s0 C - A)^-1 through the cached factors `lu`), each
+    column orthogonalised twice (classical Gram-Schmidt) against V and the
+    columns already added; a column under eps_rel of its own norm after
+    that is dropped."""
+    cols = [V[:, i] for i in range(V.shape[1])]
+    for x in (lu.solve(C @ sigma0), lu.solve(f)):
+        nx = np.linalg.norm(x)
+        if not nx > 0.0:
+            continue
+        w = x.copy()
+        for _ in range(2):
+            B = np.column_stack(cols)
+            w = w - B @ (B.T @ w)
+        nw = np.linalg.norm(w)
+        if nw >= eps_rel * nx:
+            cols.append(w / nw)
+    return np.column_stack(cols)
+
+
 class KrylovStepper:
     """Drop-in replacement for flow.advance inside flow.run_ttf."""
 
-    def __init__(self, q=10, eta=1.0, n_threads=0, cache=True):
+    def __init__(self, q=10, eta=1.0, n_threads=0, cache=True, policy="augment"):
+        if policy not in ("augment", "forcing", "stale"):
+            raise ValueError("policy must be 'augment', 'forcing' or 'stale'")
         self.q = q
         self.eta = eta
         self.n_threads = n_threads
         self.n_reduced = 0
         self.n_fallback = 0
+        self.n_built = 0
+        self.policy = policy
         self.cache = {} if cache else None
 
     def use_krylov(self, n):
@@ -162,14 +192,20 @@ class KrylovStepper:
             mmin = math.inf
             while k < n_steps:
                 C, A, ft = tree_system(tr, phys, f, st.void, t)
-                key = (t, tuple(np.nonzero(st.void[o:e])[0]), s0, ft.tobytes())
+                sig = st.sigma[o:e]
+                key = (t, tuple(np.nonzero(st.void[o:e])[0]), s0)
+                if self.policy == "forcing":
+                    key = key + (ft.tobytes(),)
                 if self.cache is not None and key in self.cache:
-                    V, Ah, Ch = self.cache[key]
-                    fh, status = V.T @ ft, "ok"
+                    V, lu = self.cache[key]
+                    if self.policy == "augment":
+                        V = augment(V, lu, C, sig, ft)
+                    Ah, Ch, fh, status = V.T @ (A @ V), V.T @ (C @ V), V.T @ ft, "ok"
                 else:
-                    V, Ah, Ch, fh, status = krylov_basis(C, A, ft, st.sigma[o:e], s0, self.q)
+                    V, Ah, Ch, fh, status = krylov_basis(C, A, ft, sig, s0, self.q)
+                    self.n_built += 1
                     if status == "ok" and self.cache is not None:
-                        self.cache[key] = (V, Ah, Ch)
+                        self.cache[key] = (V, spla.splu((s0 * C - A).tocsc()))
                 if status != "ok":
                     self.n_fallback += 1
                     total += self._be(tr, p, phys, f, st, t0 + k * dt, dt, n_steps - k, t, margin)

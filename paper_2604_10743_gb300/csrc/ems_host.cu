@@ -478,21 +478,24 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.sched = cv.take<int32_t>((size_t)S * nt);
     d.fdt = cv.take<double>((size_t)S * nt);
     d.work = cv.take<unsigned long long>(1);
-    const int rmax = (c && c->prm.method != EMS_BE) ? 2 * c->prm.krylov_q : 0;
+    const int rmax = (c && c->prm.method != EMS_BE) ? 2 * c->prm.krylov_q + 2 : 0;
     if (rmax > 0) {
-        d.kr_V = cv.take<double>((size_t)S * rmax * P); d.kr_W = cv.take<double>((size_t)S * rmax * P);
-        d.kr_lam = cv.take<double>((size_t)S * nt * rmax);
-        d.kr_Y = cv.take<double>((size_t)S * nt * rmax * rmax);
+        d.kr_V = cv.take<unsigned char>((size_t)S * rmax * P * eb);
+        d.kr_Ah = cv.take<double>((size_t)S * nt * rmax * rmax);
         d.kr_Ch = cv.take<double>((size_t)S * nt * rmax * rmax);
+        d.kr_Lm = cv.take<double>((size_t)S * nt * rmax * rmax);
+        d.kr_Xs = cv.take<double>((size_t)S * nt * rmax * (rmax + 1));
         d.kr_sp = cv.take<double>((size_t)S * P); d.kr_sg = cv.take<double>((size_t)S * P);
         d.kr_su = cv.take<double>((size_t)S * P); d.kr_sPf = cv.take<double>((size_t)S * P);
         d.kr_sPb = cv.take<double>((size_t)S * P);
         d.kr_s0 = cv.take<double>((size_t)S * nt);
         d.kr_r = cv.take<int32_t>((size_t)S * nt); d.kr_state = cv.take<int32_t>((size_t)S * nt);
+        d.kr_ok = cv.take<int32_t>((size_t)S * nt);
     } else {
-        d.kr_V = d.kr_W = d.kr_lam = d.kr_Y = d.kr_Ch = nullptr;
+        d.kr_V = nullptr;
+        d.kr_Ah = d.kr_Ch = d.kr_Lm = d.kr_Xs = nullptr;
         d.kr_sp = d.kr_sg = d.kr_su = d.kr_sPf = d.kr_sPb = d.kr_s0 = nullptr;
-        d.kr_r = d.kr_state = nullptr;
+        d.kr_r = d.kr_state = d.kr_ok = nullptr;
     }
     return cv.off + 256;
 }
@@ -579,7 +582,7 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     c->n_sinks = g->n_sinks; c->nf = (int)pl.ir.node_of_free.size(); c->nnz = (int64_t)pl.ir.col.size();
     c->N = pl.tr.off.back(); c->P = pl.P; c->n_trees = pl.tr.n_trees;
     c->maxv = c->prm.max_voids_per_tree;
-    c->rmax = c->prm.method != EMS_BE ? 2 * c->prm.krylov_q : 0;
+    c->rmax = c->prm.method != EMS_BE ? 2 * c->prm.krylov_q + 2 : 0;
     const int S = c->S, ns = c->n_seg;
     // grid
     EMS_CUDA(c, up(D.seg_a, g->seg_a, ns, st)); EMS_CUDA(c, up(D.seg_b, g->seg_b, ns, st));

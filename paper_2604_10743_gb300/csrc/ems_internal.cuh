@@ -163,8 +163,10 @@ struct Dev {
     double *R_prev;                    // [S][n_seg]
     double *raster;                    // thermal raster (up to EMS_MAX_RASTER values)
     // rational Krylov reduced models (allocated when params.method != EMS_BE)
-    double *kr_V, *kr_W;               // [S][RMAX][P] basis V and modal basis W = V Y
-    double *kr_lam, *kr_Y, *kr_Ch;     // [S][nt][RMAX], [S][nt][RMAX^2] x 2
+    void *kr_V;                        // [S][RMAX][P] basis columns (context precision); RMAX = 2q + 2
+    double *kr_Ah, *kr_Ch;             // [S][nt][RMAX^2] reduced A_h, C_h (cached base block + current block)
+    double *kr_Lm, *kr_Xs;             // [S][nt][RMAX^2], [S][nt][RMAX (RMAX+1)] Cholesky / solve scratch
+    int32_t *kr_ok;                    // [S][nt] reduced-model eligibility (Eq. krylov_threshold)
     double *kr_sp, *kr_sg, *kr_su, *kr_sPf, *kr_sPb;   // [S][P] factors of C - t_s A
     double *kr_s0;                     // [S][nt] expansion point s0 = 1/t_s
     int32_t *kr_r, *kr_state;          // [S][nt] basis size; 0 none/stale, 1 valid, 2 fall back to BE
@@ -225,6 +227,7 @@ struct ems_ctx {
     double graph_dt = 0.0;
     int kr_q = 0;              // q and eta of the reduced models currently built
     double kr_eta = 1.0;
+    int kr_kc = 64;            // steps per on-chip chunk of the reduced trajectory
     double sched_guard = 0.8;  // coarse trees turn fine once sigma >= guard * lowest sigma_crit
     // thermal raster currently set (nx = 0: uniform T0)
     int rnx = 0, rny = 0;
@@ -248,6 +251,8 @@ ems_status ir_currents_and_drop(ems_ctx *c);
 ems_status check_status(ems_ctx *c);
 
 // stress (ems_stress.cu)
+ems_status krylov_prepare(ems_ctx *c);
+ems_status krylov_stress(ems_ctx *c, double dt, int n_steps);
 ems_status node_physics(ems_ctx *c);
 ems_status forcing(ems_ctx *c);
 ems_status advance(ems_ctx *c, double dt, int n_steps, int *n_new, int method);

@@ -361,10 +361,6 @@ __global__ void __launch_bounds__(512) k_pcg_grid(IRArgs a) {
 
 // a sample whose currents changed (its PCG iterated) invalidates its reduced
 // models: their cache key includes the forcing
-__global__ void k_kr_invalidate(int S, int n_trees, const int32_t *iters, int32_t *kr_state) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < (int64_t)S * n_trees && iters[k / n_trees] > 0) kr_state[k] = 0;
-}
 
 __global__ void k_scatter_u(int nf, int n_nodes, const int32_t *node_of_free, const double *x, double *u) {
     const int s = blockIdx.y;
@@ -462,13 +458,6 @@ ems_status ir_assemble_and_solve(ems_ctx *c, bool warm) {
         k_scatter_u<<<g2, 256, 0, st>>>(c->nf, c->n_nodes, c->d.ir_node_of_free, c->d.ir_x, c->d.u);
         ++c->launches;
         EMS_CUDA(c, cudaGetLastError());
-        if (c->d.kr_state) {
-            const int64_t ts = (int64_t)c->S * c->n_trees;
-            k_kr_invalidate<<<(unsigned)((ts + 255) / 256), 256, 0, st>>>(c->S, c->n_trees, c->d.ir_iters,
-                                                                         c->d.kr_state);
-            ++c->launches;
-            EMS_CUDA(c, cudaGetLastError());
-        }
     }
     c->have_u = true;
     return EMS_OK;

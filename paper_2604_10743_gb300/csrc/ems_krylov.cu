@@ -1,21 +1,33 @@
 // ems_krylov.cu -- rational Krylov reduced models of the chain trees
 // (Sec. IV-E, Alg. 1, Eq. rak_moment_recurrence .. rak_shift_time).
 //
-// Build (one CTA per (tree, sample), the chunk layout of the BE kernel):
-//   t_s = eta L^2 / (pi^2 kappa_bar); K = C/t_s - A is factored as
-//   C - t_s A (the BE matrix with dt = t_s), so K^-1 y = t_s (C - t_s A)^-1 y
-//   reuses the chunk-parallel elimination; starting block [K^-1 C s0, K^-1 f];
-//   block Arnoldi to order q with classical Gram-Schmidt applied twice (FP64
-//   reorthogonalisation); A_h = V^T A V, C_h = V^T C V, f_h = V^T f; then the
-//   symmetric-definite pencil A_h y = lambda C_h y (Cholesky + Jacobi) gives
-//   the modal basis W = V Y with Y^T C_h Y = I.
-// Advance: backward Euler in modal coordinates is exact in closed form,
-//   z_j(k) = z*_j + (z_j(0) - z*_j) rho_j^k, rho_j = 1/(1 - dt lambda_j),
-//   so the lifted stress at any step costs O(r) per node.  A per-node bound
-//   over the whole aging step (each mode term is monotone in k) leaves only
-//   candidate nodes to be checked step by step for nucleation; void volumes
-//   take the closed-form geometric sums; the state is lifted once at the end.
-// Breakdown and rank deficiency send the tree back to full backward Euler.
+// One CTA per (tree, sample) in the chunk layout of the BE kernels (thread c
+// holds nodes c*M .. c*M+M-1, node c*M+k stored at slot k*T + c), one launch
+// per aging step.  R is the context's storage precision (basis, stress,
+// per-node arithmetic); cross-thread sums, the shifted factors and the small
+// dense algebra are FP64.
+//
+//   build    (cache miss: first use, a new void, a new thermal map, new q or
+//            eta) t_s = eta L^2/(pi^2 kappa_bar) and s0 = 1/t_s; the factors of
+//            C - t_s A give (s0 C - A)^-1 y = t_s (C - t_s A)^-1 y; starting
+//            block [R C s, R f]; block Arnoldi to order q with classical
+//            Gram-Schmidt applied twice; base projections A_h = V^T A V and
+//            C_h = V^T C V
+//   augment  (cache hit, Sec. IV-E.4) the current starting block [R C s, R f]
+//            orthogonalised twice against the cached columns into two extra
+//            slots, and their rows of A_h and C_h
+//   step     M = C_h - dt A_h (Cholesky), propagator F = M^-1 C_h; backward
+//            Euler in reduced coordinates in increment form
+//            (s_hat(k+1) - s_hat(k) = F (s_hat(k) - s_hat(k-1))) for a chunk of
+//            steps kept on chip; a per-node upper bound of the lifted stress
+//            over the chunk (per-coordinate extremes) leaves the candidate
+//            nodes, which alone are lifted step by step to find the first
+//            nucleation; void volumes take per-coordinate step sums; one lift
+//            at the end of the chunk that ends the aging step
+//   nucleation: lift at that step, record the void, rebuild (A changed) and
+//            carry on from there in the same launch
+// A build with nothing to reduce or with a rank-deficient block hands the tree
+// to full backward Euler for the rest of the aging step (Sec. IV-E.5).
 #include <climits>
 #include <cmath>
 
@@ -30,22 +42,32 @@ namespace {
 
 constexpr int kStatusOverflow = 2;
 constexpr double kPi = 3.141592653589793;
+constexpr int kRm = 96;                     // >= 2 q + 2 for q <= 40
 
+template <typename R>
+__host__ __device__ constexpr int kr_max_threads(int M) {
+    return sizeof(R) == 4 ? (M <= 8 ? 1024 : M <= 32 ? 640 : 320)
+                          : (M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 384 : 256);
+}
+
+template <typename R>
 struct KrArgs {
     const int32_t *trees;
     const int64_t *toff, *pbase;
     int64_t N, P;
-    int n_trees, S, rmax, q;
+    int n_trees, rmax, q, kc;
     double eta, eps_rel;
-    const double *V, *g, *leak, *f, *kap_a, *dx, *area;
+    const double *Vn, *g, *leak, *f, *kap_a, *dx, *area;   // Vn: node volumes (diagonal of C)
     double *thr;
-    void *sig;
-    int f32;
-    double *sp, *sg, *su, *sPf, *sPb;
-    double *Vb, *Wb, *lam, *Y, *Ch, *s0;
+    R *sig;
+    double *sp, *sg, *su, *sPf, *sPb;       // [S][P] factors of C - t_s A
+    R *Vb;                                  // [S][rmax][P] basis columns
+    double *Ah, *Ch, *Lm, *Xs;              // [S nt][rmax^2] projections; Cholesky and solve scratch
+    double *s0;
     int32_t *kr_r, *kr_state, *kr_mode, *kdone;
     double dt, t0, Binv;
-    int n_steps;
+    const double *t0p;                      // device start time of the aging step (graph replay), or null
+    int n_steps, build_only;
     int32_t *v_count, *v_node, *v_seg;
     double *v_vol, *v_tnuc;
     int maxv;
@@ -54,94 +76,137 @@ struct KrArgs {
     int n_seg;
     const int32_t *inc_ptr, *inc_seg;
     int32_t *status, *counters;
+    unsigned long long *work;
 };
 
-__device__ __forceinline__ double sig_at(const KrArgs &a, int64_t pk) {
-    return a.f32 ? (double)((const float *)a.sig)[pk] : ((const double *)a.sig)[pk];
-}
-__device__ __forceinline__ void sig_set(const KrArgs &a, int64_t pk, double v) {
-    if (a.f32) ((float *)a.sig)[pk] = (float)v;
-    else ((double *)a.sig)[pk] = v;
-}
+// per-CTA constants of the (tree, sample)
+struct Tr {
+    int t, s, T, c, n;
+    int64_t st, cb, cs, ps, P;
+};
 
-// block sums of K values, fixed order; every thread gets the sums in x
-template <int K>
-__device__ __forceinline__ void bsum(double (&x)[K], double *red, double *out) {
+struct Sh {                                 // static shared scratch
+    double *red, *out, *sA, *sB, *sL, *sR, *h, *h2;
+    int *phase;                             // per-thread reduction buffer parity (local)
+};
+
+// block sums of K values, fixed order; every thread gets the sums in x.
+// Per-thread values and the warp tree are in precision R, the sum over the
+// warps in FP64 (FP64 shuffles cost 64x the FP32 ones on this part).  One
+// barrier: every warp reads all warps' partials and adds them itself (lane
+// q < K sums value q), alternating between two halves of `red` so that the
+// next call cannot overwrite partials a slower warp still reads.
+template <int K, typename R>
+__device__ __forceinline__ void bsum(const R (&xin)[K], double (&x)[K], double *red, int &phase) {
+    static_assert(K <= 16, "at most 16 values per reduction");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double *buf = red + (phase & 1) * (16 * 32);
+    ++phase;
+    R v[K];
 #pragma unroll
-    for (int q = 0; q < K; ++q)
-        for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], o);
+    for (int q = 0; q < K; ++q) {
+        v[q] = xin[q];
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    }
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < K; ++q) red[q * 32 + w] = x[q];
+        for (int q = 0; q < K; ++q) buf[q * 32 + w] = (double)v[q];
     __syncthreads();
-    if (threadIdx.x < K) {
-        double t = 0.0;
-        for (int k = 0; k < nw; ++k) t += red[threadIdx.x * 32 + k];
-        out[threadIdx.x] = t;
-    }
-    __syncthreads();
+    double t = 0.0;
+    if (lane < K)
+        for (int k = 0; k < nw; ++k) t += buf[lane * 32 + k];
 #pragma unroll
-    for (int q = 0; q < K; ++q) x[q] = out[q];
+    for (int q = 0; q < K; ++q) x[q] = __shfl_sync(0xffffffffu, t, q);
 }
 
-// h[i] = column_i . x for i < m (columns at base + i P, chunk layout)
-template <int M>
-__device__ void dots(const double *base, int64_t P, int T, int c, int m, const double (&x)[M], double *h,
-                     double *red, double *out) {
-    for (int g0 = 0; g0 < m; g0 += 8) {
-        double acc[8];
+// h[i] = column_i . x for i < m: per-thread partial sums in R over the
+// thread's M nodes, FP64 across threads
+template <int M, typename R>
+__device__ void dots(const R *base, const Tr &z, int m, const R (&x)[M], double *h, const Sh &sh) {
+    for (int g0 = 0; g0 < m; g0 += 16) {
+        R p[16];
+        double acc[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            acc[q] = 0.0;
+        for (int q = 0; q < 16; ++q) {
+            p[q] = R(0);
             if (g0 + q < m) {
-                const double *col = base + (int64_t)(g0 + q) * P + c;
+                const R *col = base + (int64_t)(g0 + q) * z.P + z.c;
 #pragma unroll
-                for (int k = 0; k < M; ++k) acc[q] = fma(col[(int64_t)k * T], x[k], acc[q]);
+                for (int k = 0; k < M; ++k) p[q] = fmx(col[(int64_t)k * z.T], x[k], p[q]);
             }
         }
-        bsum<8>(acc, red, out);
+        bsum<16, R>(p, acc, sh.red, *sh.phase);
         if (threadIdx.x == 0)
-            for (int q = 0; q < 8 && g0 + q < m; ++q) h[g0 + q] = acc[q];
+            for (int q = 0; q < 16 && g0 + q < m; ++q) h[g0 + q] = acc[q];
+    }
+    __syncthreads();                        // h complete for every thread
+}
+
+// h[i] = column_i . y1 and h2[i] = column_i . y2 for i < m, one reduction for both
+template <int M, typename R>
+__device__ void dots2(const R *base, const Tr &z, int m, const R (&y1)[M], const R (&y2)[M], double *h,
+                      double *h2, const Sh &sh) {
+    for (int g0 = 0; g0 < m; g0 += 8) {
+        R p[16];
+        double acc[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            p[q] = R(0);
+            p[8 + q] = R(0);
+            if (g0 + q < m) {
+                const R *col = base + (int64_t)(g0 + q) * z.P + z.c;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const R v = col[(int64_t)k * z.T];
+                    p[q] = fmx(v, y1[k], p[q]);
+                    p[8 + q] = fmx(v, y2[k], p[8 + q]);
+                }
+            }
+        }
+        bsum<16, R>(p, acc, sh.red, *sh.phase);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 8 && g0 + q < m; ++q) { h[g0 + q] = acc[q]; h2[g0 + q] = acc[8 + q]; }
     }
     __syncthreads();
 }
 
 // x -= sum_i h_i column_i, twice (classical Gram-Schmidt with reorthogonalisation)
-template <int M>
-__device__ void orth(const double *base, int64_t P, int T, int c, int m, double (&x)[M], double *h, double *red,
-                     double *out) {
+template <int M, typename R>
+__device__ void orth(const R *base, const Tr &z, int m, R (&x)[M], const Sh &sh) {
     for (int pass = 0; pass < 2; ++pass) {
-        dots<M>(base, P, T, c, m, x, h, red, out);
+        dots<M, R>(base, z, m, x, sh.h, sh);
         for (int i = 0; i < m; ++i) {
-            const double hi = h[i];
-            const double *col = base + (int64_t)i * P + c;
+            const R hi = (R)sh.h[i];
+            const R *col = base + (int64_t)i * z.P + z.c;
 #pragma unroll
-            for (int k = 0; k < M; ++k) x[k] = fma(-hi, col[(int64_t)k * T], x[k]);
+            for (int k = 0; k < M; ++k) x[k] = fmx(-hi, col[(int64_t)k * z.T], x[k]);
         }
     }
 }
 
-template <int M>
-__device__ __forceinline__ double norm2(const double (&x)[M], double *red, double *out) {
-    double v[1] = {0.0};
+template <int M, typename R>
+__device__ __forceinline__ double norm2(const R (&x)[M], const Sh &sh) {
+    R p[1] = {R(0)};
 #pragma unroll
-    for (int k = 0; k < M; ++k) v[0] = fma(x[k], x[k], v[0]);
-    bsum<1>(v, red, out);
+    for (int k = 0; k < M; ++k) p[0] = fmx(x[k], x[k], p[0]);
+    double v[1];
+    bsum<1, R>(p, v, sh.red, *sh.phase);
     return v[0];
 }
 
 // x <- (C - t_s A)^-1 x with the shifted factors (chunk scans, FP64)
-template <int M>
-__device__ void ksolve(const KrArgs &a, int64_t ps, int T, int c, double (&x)[M], double *sA, double *sB) {
-    double z = 0.0;
+template <int M, typename R>
+__device__ void ksolve(const KrArgs<R> &a, const Tr &z, double (&x)[M], const Sh &sh) {
+    const int T = z.T, c = z.c;
+    const int64_t ps = z.ps;
+    double v = 0.0;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         const int64_t pk = ps + (int64_t)k * T + c;
-        z = fma(-a.sg[pk], z, a.sp[pk] * x[k]);
-        x[k] = z;
+        v = fma(-a.sg[pk], v, a.sp[pk] * x[k]);
+        x[k] = v;
     }
-    const double cf = scan_fwd<double>(z, a.sPf[ps + (int64_t)(M - 1) * T + c], sA, sB, nullptr);
+    const double cf = scan_fwd<double>(v, a.sPf[ps + (int64_t)(M - 1) * T + c], sh.sA, sh.sB, nullptr);
 #pragma unroll
     for (int k = 0; k < M; ++k) x[k] = fma(a.sPf[ps + (int64_t)k * T + c], cf, x[k]);
     double y = 0.0;
@@ -150,576 +215,698 @@ __device__ void ksolve(const KrArgs &a, int64_t ps, int T, int c, double (&x)[M]
         y = fma(-a.su[ps + (int64_t)k * T + c], y, x[k]);
         x[k] = y;
     }
-    const double cr = scan_bwd<double>(y, a.sPb[ps + c], sA, sB, nullptr);
+    const double cr = scan_bwd<double>(y, a.sPb[ps + c], sh.sA, sh.sB, nullptr);
 #pragma unroll
     for (int k = 0; k < M; ++k) x[k] = fma(a.sPb[ps + (int64_t)k * T + c], cr, x[k]);
 }
 
 // y = A x on the chain (face fluxes plus the Robin leak at voids)
-template <int M>
-__device__ void amul(const KrArgs &a, int n, int64_t cs, int T, int c, const double (&x)[M], double (&y)[M],
-                     double *sL, double *sR) {
+template <int M, typename R>
+__device__ void amul(const KrArgs<R> &a, const Tr &z, const R (&x)[M], R (&y)[M], const Sh &sh) {
     const unsigned full = 0xffffffffu;
-    const int lane = c & 31, w = c >> 5, nw = T >> 5;
-    double left = __shfl_up_sync(full, x[M - 1], 1);
-    double right = __shfl_down_sync(full, x[0], 1);
+    const int c = z.c, lane = c & 31, w = c >> 5, nw = z.T >> 5;
+    R left = __shfl_up_sync(full, x[M - 1], 1);
+    R right = __shfl_down_sync(full, x[0], 1);
+    __syncthreads();                        // earlier readers of the halo slots are done
     if (nw > 1) {
-        if (lane == 31) sL[w] = x[M - 1];
-        if (lane == 0) sR[w] = x[0];
+        if (lane == 31) sh.sL[w] = (double)x[M - 1];
+        if (lane == 0) sh.sR[w] = (double)x[0];
         __syncthreads();
-        if (lane == 0 && w > 0) left = sL[w - 1];
-        if (lane == 31 && w + 1 < nw) right = sR[w + 1];
+        if (lane == 0 && w > 0) left = (R)sh.sL[w - 1];
+        if (lane == 31 && w + 1 < nw) right = (R)sh.sR[w + 1];
     }
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         const int i = c * M + k;
-        double v = 0.0;
-        if (i < n) {
-            const double xl = k > 0 ? x[k - 1] : left, xr = k + 1 < M ? x[k + 1] : right;
-            if (i > 0) v += a.g[cs + i] * (xl - x[k]);
-            if (i + 1 < n) v += a.g[cs + i + 1] * (xr - x[k]);
-            if (isinf(a.thr[cs + i])) v -= a.leak[cs + i] * x[k];
+        R v = R(0);
+        if (i < z.n) {
+            const R xl = k > 0 ? x[k - 1] : left, xr = k + 1 < M ? x[k + 1] : right;
+            if (i > 0) v = fmx((R)a.g[z.cs + i], xl - x[k], v);
+            if (i + 1 < z.n) v = fmx((R)a.g[z.cs + i + 1], xr - x[k], v);
+            if (isinf(a.thr[z.cs + i])) v = fmx(-(R)a.leak[z.cs + i], x[k], v);
         }
         y[k] = v;
+    }
+}
+
+template <int M, typename R>
+__device__ __forceinline__ void store_col(R *Vs, const Tr &z, int slot, const R (&x)[M], R scale) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) Vs[(int64_t)slot * z.P + (int64_t)k * z.T + z.c] = x[k] * scale;
+}
+
+template <int M, typename R>
+__device__ __forceinline__ void load_col(const R *Vs, const Tr &z, int slot, R (&x)[M]) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) x[k] = Vs[(int64_t)slot * z.P + (int64_t)k * z.T + z.c];
+}
+
+// rows/columns jc in [j0, j1) of A_h and C_h against columns 0..jc (symmetric)
+template <int M, typename R>
+__device__ void project(const KrArgs<R> &a, const Tr &z, const R *Vs, int j0, int j1, double *Ahs, double *Chs,
+                        const Sh &sh) {
+    const int rm = a.rmax;
+    R x[M], y[M], yc[M];
+    for (int jc = j0; jc < j1; ++jc) {
+        load_col<M, R>(Vs, z, jc, x);
+        amul<M, R>(a, z, x, y, sh);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int i = z.c * M + k;
+            yc[k] = i < z.n ? (R)a.Vn[z.cb + i] * x[k] : R(0);
+        }
+        dots2<M, R>(Vs, z, jc + 1, y, yc, sh.h, sh.h2, sh);
+        for (int i = z.c; i <= jc; i += z.T) {
+            Ahs[(int64_t)i * rm + jc] = Ahs[(int64_t)jc * rm + i] = sh.h[i];
+            Chs[(int64_t)i * rm + jc] = Chs[(int64_t)jc * rm + i] = sh.h2[i];
+        }
+        __syncthreads();                    // h, h2 are rewritten by the next column
+    }
+}
+
+// 2x2 matrices [[a, b], [c, d]] for the continuant scan, rescaled by powers
+// of two (exact) to stay in range; only ratios of the continuants matter
+struct M2 {
+    double a, b, c, d;
+};
+__device__ __forceinline__ M2 m2mul(const M2 &x, const M2 &y) {
+    return M2{fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d), fma(x.c, y.a, x.d * y.c),
+              fma(x.c, y.b, x.d * y.d)};
+}
+__device__ __forceinline__ M2 m2norm(M2 x) {
+    const double mx = fmax(fmax(fabs(x.a), fabs(x.b)), fmax(fabs(x.c), fabs(x.d)));
+    if (mx > 0.0 && isfinite(mx)) {
+        const int e = ilogb(mx);
+        x.a = scalbn(x.a, -e); x.b = scalbn(x.b, -e); x.c = scalbn(x.c, -e); x.d = scalbn(x.d, -e);
+    }
+    return x;
+}
+__device__ __forceinline__ M2 m2shfl_up(const M2 &x, int d) {
+    const unsigned full = 0xffffffffu;
+    return M2{__shfl_up_sync(full, x.a, d), __shfl_up_sync(full, x.b, d), __shfl_up_sync(full, x.c, d),
+              __shfl_up_sync(full, x.d, d)};
+}
+
+template <int M, typename R>
+__device__ void factor_shift(const KrArgs<R> &a, const Tr &z, double ts, const Sh &sh) {
+    const int T = z.T, c = z.c, n = z.n, lane = c & 31, w = c >> 5, nw = T >> 5;
+    const M2 I{1.0, 0.0, 0.0, 1.0};
+    M2 P = I;                                        // A_last ... A_first of this chunk
+#pragma unroll 1
+    for (int k = 0; k < M; ++k) {
+        const int i = c * M + k;
+        if (i >= n) break;
+        const double gl = i > 0 ? a.g[z.cs + i] : 0.0, gr = i + 1 < n ? a.g[z.cs + i + 1] : 0.0;
+        double d = a.Vn[z.cb + i] + ts * (gl + gr);
+        if (isinf(a.thr[z.cs + i])) d += ts * a.leak[z.cs + i];
+        const double e2 = (ts * gl) * (ts * gl);
+        P = m2norm(m2mul(M2{d, -e2, 1.0, 0.0}, P));
+    }
+    // inclusive scan over the warp (later chunks multiply from the left)
+    M2 v = P;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        const M2 o = m2shfl_up(v, dd);
+        if (lane >= dd) v = m2norm(m2mul(v, o));
+    }
+    M2 pw = I;                                       // product of all earlier warps
+    double *agg = sh.red;                            // 4 x 32 doubles
+    if (nw > 1) {
+        __syncthreads();
+        if (lane == 31) { agg[w] = v.a; agg[32 + w] = v.b; agg[64 + w] = v.c; agg[96 + w] = v.d; }
+        __syncthreads();
+        M2 u = lane < w ? M2{agg[lane], agg[32 + lane], agg[64 + lane], agg[96 + lane]} : I;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const M2 o = m2shfl_up(u, dd);
+            if (lane >= dd) u = m2norm(m2mul(u, o));
+        }
+        pw = M2{__shfl_sync(0xffffffffu, u.a, 31), __shfl_sync(0xffffffffu, u.b, 31),
+                __shfl_sync(0xffffffffu, u.c, 31), __shfl_sync(0xffffffffu, u.d, 31)};
+    }
+    M2 ex = m2shfl_up(v, 1);
+    if (lane == 0) ex = I;
+    const M2 E = m2norm(m2mul(ex, pw));
+    double qp = E.a, qpp = E.c;                      // (q_(i-1), q_(i-2)) from (q_-1, q_-2) = (1, 0)
+#pragma unroll 1
+    for (int k = 0; k < M; ++k) {
+        const int i = c * M + k;
+        if (i >= n) break;
+        const double gl = i > 0 ? a.g[z.cs + i] : 0.0, gr = i + 1 < n ? a.g[z.cs + i + 1] : 0.0;
+        double d = a.Vn[z.cb + i] + ts * (gl + gr);
+        if (isinf(a.thr[z.cs + i])) d += ts * a.leak[z.cs + i];
+        const double em = -ts * gl, ep = -ts * gr;
+        const double q = fma(d, qp, -(em * em) * qpp);
+        const double p = qp / q;
+        const int64_t pk = z.ps + (int64_t)k * T + c;
+        a.sp[pk] = p; a.sg[pk] = p * em; a.su[pk] = p * ep;
+        const int e = ilogb(fabs(q));
+        qpp = scalbn(qp, -e);
+        qp = scalbn(q, -e);
     }
     __syncthreads();
 }
 
-template <int M>
-__global__ void __launch_bounds__(1024) k_kr_build(KrArgs a) {
-    extern __shared__ double dsm[];
-    __shared__ double sA[64], sB[64], red[256], out[8], sL[32], sR[32];
-    const int t = a.trees[blockIdx.x], s = blockIdx.y, T = blockDim.x, c = threadIdx.x;
-    const int64_t st = (int64_t)s * a.n_trees + t;
-    if (!a.kr_mode[st] || a.kr_state[st] == 1) return;
-    const int64_t cb = a.toff[t];
-    const int n = (int)(a.toff[t + 1] - cb);
-    const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
-    const int R = a.rmax;
-    const int64_t P = a.P;
-    double *Vs = a.Vb + (int64_t)s * R * P + a.pbase[t];
-    double *Ws = a.Wb + (int64_t)s * R * P + a.pbase[t];
-    double *Chs = dsm, *Ss = dsm + R * R, *Ls = dsm + 2 * R * R, *Qs = dsm + 3 * R * R, *h = dsm + 4 * R * R;
-    double *fh = h + R;
-    __shared__ int s_fail;
-
+// Alg. 1 from the current stress and forcing: returns the base rank (> 0),
+// 0 when there is nothing to reduce, -1 on rank deficiency
+template <int M, typename R>
+__device__ int build(const KrArgs<R> &a, const Tr &z, R *Vs, double *Ahs, double *Chs, const Sh &sh,
+                     double &ts_out) {
+    const int T = z.T, c = z.c, n = z.n;
     // shift time t_s = eta L^2 / (pi^2 kappa_bar), L the chain length
     double x3[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         const int i = c * M + k;
         if (i >= 1 && i < n) {
-            const double d = a.dx[cb + i];
-            x3[0] += a.kap_a[cs + i] * d;
-            x3[1] += a.area[cb + i] * d;
+            const double d = a.dx[z.cb + i];
+            x3[0] += a.kap_a[z.cs + i] * d;
+            x3[1] += a.area[z.cb + i] * d;
             x3[2] += d;
         }
     }
-    bsum<3>(x3, red, out);
+    bsum<3, double>(x3, x3, sh.red, *sh.phase);
     const double ts = a.eta * x3[2] * x3[2] / (kPi * kPi * (x3[0] / x3[1]));
-    // factor C - t_s A (serial pass), then each chunk's carry products
-    if (c == 0) {
-        a.s0[st] = 1.0 / ts;
-        s_fail = 0;
-        double pprev = 0.0;
-        for (int i = 0; i < n; ++i) {
-            const double gl = i > 0 ? a.g[cs + i] : 0.0, gr = i + 1 < n ? a.g[cs + i + 1] : 0.0;
-            double d = a.V[cb + i] + ts * (gl + gr);
-            if (isinf(a.thr[cs + i])) d += ts * a.leak[cs + i];
-            const double em = -ts * gl, ep = -ts * gr;
-            const double p = 1.0 / (d - em * em * pprev);
-            const int64_t pk = ps + (int64_t)(i % M) * T + i / M;
-            a.sp[pk] = p; a.sg[pk] = p * em; a.su[pk] = p * ep;
-            pprev = p;
-        }
-    }
-    __syncthreads();
+    ts_out = ts;
+    // factor C - t_s A = L D L^T: pivots p_i = 1/(d_i - e_i^2 p_(i-1)) from
+    // the continuants q_i = d_i q_(i-1) - e_i^2 q_(i-2) (p_i = q_(i-1)/q_i),
+    // a prefix product of 2x2 matrices across the chunks, then each chunk's
+    // pivots in order from its carried (q_(i-1), q_(i-2))
+    if (c == 0) a.s0[z.st] = 1.0 / ts;
+    factor_shift<M, R>(a, z, ts, sh);
     {
         double acc = 1.0;
         for (int k = 0; k < M; ++k) {
-            const int64_t pk = ps + (int64_t)k * T + c;
+            const int64_t pk = z.ps + (int64_t)k * T + c;
             acc *= -a.sg[pk];
             a.sPf[pk] = acc;
         }
         acc = 1.0;
         for (int k = M - 1; k >= 0; --k) {
-            const int64_t pk = ps + (int64_t)k * T + c;
+            const int64_t pk = z.ps + (int64_t)k * T + c;
             acc *= -a.su[pk];
             a.sPb[pk] = acc;
         }
     }
     __syncthreads();
 
-    // starting block F0 = [K^-1 C s0, K^-1 f] (raw columns in slots 0, 1)
-    double x[M], n0[2];
+    // starting block F0 = [R C s, R f] (raw columns in slots 0, 1)
+    double xd[M], n0[2];
+    R x[M];
     for (int col = 0; col < 2; ++col) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
             const int i = c * M + k;
-            x[k] = i < n ? (col == 0 ? a.V[cb + i] * sig_at(a, ps + (int64_t)k * T + c) : a.f[cs + i]) : 0.0;
+            xd[k] = i < n ? (col == 0 ? a.Vn[z.cb + i] * (double)a.sig[z.ps + (int64_t)k * T + c] : a.f[z.cs + i])
+                          : 0.0;
         }
-        ksolve<M>(a, ps, T, c, x, sA, sB);
+        ksolve<M, R>(a, z, xd, sh);
 #pragma unroll
-        for (int k = 0; k < M; ++k) x[k] *= ts;
-        n0[col] = sqrt(norm2<M>(x, red, out));
-#pragma unroll
-        for (int k = 0; k < M; ++k) Vs[(int64_t)col * P + (int64_t)k * T + c] = x[k];
+        for (int k = 0; k < M; ++k) { xd[k] *= ts; x[k] = (R)xd[k]; }
+        n0[col] = sqrt(norm2<M, R>(x, sh));
+        store_col<M, R>(Vs, z, col, x, R(1));
     }
     const double eps0 = a.eps_rel * fmax(n0[0], n0[1]);
     int m = 0;
     for (int col = 0; col < 2; ++col) {
         if (!(n0[col] > 0.0)) continue;
-#pragma unroll
-        for (int k = 0; k < M; ++k) x[k] = Vs[(int64_t)col * P + (int64_t)k * T + c];
+        load_col<M, R>(Vs, z, col, x);
         __syncthreads();
-        orth<M>(Vs, P, T, c, m, x, h, red, out);
-        const double nw = sqrt(norm2<M>(x, red, out));
+        orth<M, R>(Vs, z, m, x, sh);
+        const double nw = sqrt(norm2<M, R>(x, sh));
         if (nw >= a.eps_rel * n0[col] && nw >= eps0) {
-#pragma unroll
-            for (int k = 0; k < M; ++k) Vs[(int64_t)m * P + (int64_t)k * T + c] = x[k] / nw;
+            store_col<M, R>(Vs, z, m, x, (R)(1.0 / nw));
             ++m;
         }
         __syncthreads();
     }
-    if (m == 0) {                                  // nothing to reduce: full BE
-        if (c == 0) { a.kr_state[st] = 2; a.kr_mode[st] = 0; }
-        return;
-    }
+    if (m == 0) return 0;
+    const int rq = 2 * a.q;
     int pb0 = 0, pb1 = m;
-    for (int blk = 1; blk < a.q && m + (pb1 - pb0) <= R; ++blk) {
+    for (int blk = 1; blk < a.q && m + (pb1 - pb0) <= rq; ++blk) {
         const int nb = pb1 - pb0;
         double w2 = 0.0;
-        for (int q = 0; q < nb; ++q) {             // raw W = K^-1 C V_j into slots m + q
+        for (int q = 0; q < nb; ++q) {             // raw W = R C V_j into slots m + q
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const int i = c * M + k;
-                x[k] = i < n ? a.V[cb + i] * Vs[(int64_t)(pb0 + q) * P + (int64_t)k * T + c] : 0.0;
+                xd[k] = i < n ? a.Vn[z.cb + i] * (double)Vs[(int64_t)(pb0 + q) * z.P + (int64_t)k * T + c] : 0.0;
             }
-            ksolve<M>(a, ps, T, c, x, sA, sB);
+            ksolve<M, R>(a, z, xd, sh);
 #pragma unroll
-            for (int k = 0; k < M; ++k) x[k] *= ts;
-            w2 += norm2<M>(x, red, out);
-#pragma unroll
-            for (int k = 0; k < M; ++k) Vs[(int64_t)(m + q) * P + (int64_t)k * T + c] = x[k];
+            for (int k = 0; k < M; ++k) { xd[k] *= ts; x[k] = (R)xd[k]; }
+            w2 += norm2<M, R>(x, sh);
+            store_col<M, R>(Vs, z, m + q, x, R(1));
         }
         const double epsj = a.eps_rel * sqrt(w2);
         int acc = 0;
         bool deficient = false;
         for (int q = 0; q < nb; ++q) {
-#pragma unroll
-            for (int k = 0; k < M; ++k) x[k] = Vs[(int64_t)(m + q) * P + (int64_t)k * T + c];
+            load_col<M, R>(Vs, z, m + q, x);
             __syncthreads();
-            orth<M>(Vs, P, T, c, m + acc, x, h, red, out);
-            const double nw = sqrt(norm2<M>(x, red, out));
+            orth<M, R>(Vs, z, m + acc, x, sh);
+            const double nw = sqrt(norm2<M, R>(x, sh));
             if (nw < epsj) {
                 deficient = true;
             } else {
-#pragma unroll
-                for (int k = 0; k < M; ++k) Vs[(int64_t)(m + acc) * P + (int64_t)k * T + c] = x[k] / nw;
+                store_col<M, R>(Vs, z, m + acc, x, (R)(1.0 / nw));
                 ++acc;
             }
             __syncthreads();
         }
         if (acc == 0) break;                       // the space is invariant: done
-        if (deficient) {                           // rank deficiency: full BE (Sec. IV-E.5)
-            if (c == 0) { a.kr_state[st] = 2; a.kr_mode[st] = 0; }
-            return;
-        }
+        if (deficient) return -1;                  // rank deficiency: full BE
         pb0 = m; pb1 = m + acc; m += acc;
     }
+    project<M, R>(a, z, Vs, 0, m, Ahs, Chs, sh);
+    return m;
+}
 
-    // projections C_h = V^T C V, A_h = V^T A V, f_h = V^T f
-    double y[M];
-    for (int jc = 0; jc < m; ++jc) {
-#pragma unroll
-        for (int k = 0; k < M; ++k) x[k] = Vs[(int64_t)jc * P + (int64_t)k * T + c];
-        amul<M>(a, n, cs, T, c, x, y, sL, sR);
-        dots<M>(Vs, P, T, c, m, y, h, red, out);
-        if (c == 0)
-            for (int i = 0; i < m; ++i) Ss[i * R + jc] = h[i];
+// the cached basis plus the current starting block [R C s, R f]; returns the
+// total number of columns
+template <int M, typename R>
+__device__ int augment(const KrArgs<R> &a, const Tr &z, R *Vs, int rb, double *Ahs, double *Chs, const Sh &sh) {
+    const int T = z.T, c = z.c, n = z.n;
+    const double ts = 1.0 / a.s0[z.st];
+    int m = rb;
+    double xd[M];
+    R x[M];
+    for (int col = 0; col < 2; ++col) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
             const int i = c * M + k;
-            y[k] = i < n ? a.V[cb + i] * x[k] : 0.0;
+            xd[k] = i < n ? (col == 0 ? a.Vn[z.cb + i] * (double)a.sig[z.ps + (int64_t)k * T + c] : a.f[z.cs + i])
+                          : 0.0;
         }
-        dots<M>(Vs, P, T, c, m, y, h, red, out);
-        if (c == 0)
-            for (int i = 0; i < m; ++i) Chs[i * R + jc] = h[i];
+        ksolve<M, R>(a, z, xd, sh);
+#pragma unroll
+        for (int k = 0; k < M; ++k) { xd[k] *= ts; x[k] = (R)xd[k]; }
+        const double nx = sqrt(norm2<M, R>(x, sh));
+        if (!(nx > 0.0)) continue;
+        orth<M, R>(Vs, z, m, x, sh);
+        const double nw = sqrt(norm2<M, R>(x, sh));
+        if (nw >= a.eps_rel * nx) {
+            store_col<M, R>(Vs, z, m, x, (R)(1.0 / nw));
+            ++m;
+        }
         __syncthreads();
     }
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-        const int i = c * M + k;
-        x[k] = i < n ? a.f[cs + i] : 0.0;
-    }
-    dots<M>(Vs, P, T, c, m, x, fh, red, out);
-
-    // pencil A_h y = lambda C_h y: C_h = L L^T, S = L^-1 A_h L^-T, Jacobi on S
-    if (c == 0) {
-        for (int i = 0; i < m; ++i)                // symmetrise the projections
-            for (int k = 0; k < i; ++k) {
-                const double sa = 0.5 * (Ss[i * R + k] + Ss[k * R + i]);
-                const double sc = 0.5 * (Chs[i * R + k] + Chs[k * R + i]);
-                Ss[i * R + k] = Ss[k * R + i] = sa;
-                Chs[i * R + k] = Chs[k * R + i] = sc;
-            }
-        for (int i = 0; i < m; ++i) {              // Cholesky
-            for (int k = 0; k <= i; ++k) {
-                double v = Chs[i * R + k];
-                for (int l = 0; l < k; ++l) v -= Ls[i * R + l] * Ls[k * R + l];
-                if (i == k) {
-                    if (!(v > 0.0)) { s_fail = 1; v = 1.0; }
-                    Ls[i * R + i] = sqrt(v);
-                } else {
-                    Ls[i * R + k] = v / Ls[k * R + k];
-                }
-            }
-            for (int k = i + 1; k < m; ++k) Ls[i * R + k] = 0.0;
-        }
-        // S <- L^-1 S (columns), then S <- S L^-T (rows)
-        for (int jc = 0; jc < m; ++jc)
-            for (int i = 0; i < m; ++i) {
-                double v = Ss[i * R + jc];
-                for (int l = 0; l < i; ++l) v -= Ls[i * R + l] * Ss[l * R + jc];
-                Ss[i * R + jc] = v / Ls[i * R + i];
-            }
-        for (int i = 0; i < m; ++i)
-            for (int jc = 0; jc < m; ++jc) {
-                double v = Ss[i * R + jc];
-                for (int l = 0; l < jc; ++l) v -= Ss[i * R + l] * Ls[jc * R + l];
-                Ss[i * R + jc] = v / Ls[jc * R + jc];
-            }
-        for (int i = 0; i < m; ++i)
-            for (int k = 0; k < m; ++k) Qs[i * R + k] = i == k ? 1.0 : 0.0;
-        double fro = 0.0;
-        for (int i = 0; i < m; ++i)
-            for (int k = 0; k < m; ++k) fro += Ss[i * R + k] * Ss[i * R + k];
-        for (int sweep = 0; sweep < 60; ++sweep) {
-            double off = 0.0;
-            for (int i = 0; i < m; ++i)
-                for (int k = i + 1; k < m; ++k) off += Ss[i * R + k] * Ss[i * R + k];
-            if (off <= 1e-30 * fro) break;
-            for (int p = 0; p < m - 1; ++p)
-                for (int qq = p + 1; qq < m; ++qq) {
-                    const double apq = Ss[p * R + qq];
-                    if (fabs(apq) <= 1e-300) continue;
-                    const double th = (Ss[qq * R + qq] - Ss[p * R + p]) / (2.0 * apq);
-                    const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                    const double cc = 1.0 / sqrt(tt * tt + 1.0), sn = tt * cc;
-                    for (int k = 0; k < m; ++k) {   // columns p, q
-                        const double kp = Ss[k * R + p], kq = Ss[k * R + qq];
-                        Ss[k * R + p] = cc * kp - sn * kq;
-                        Ss[k * R + qq] = sn * kp + cc * kq;
-                    }
-                    for (int k = 0; k < m; ++k) {   // rows p, q
-                        const double pk = Ss[p * R + k], qk = Ss[qq * R + k];
-                        Ss[p * R + k] = cc * pk - sn * qk;
-                        Ss[qq * R + k] = sn * pk + cc * qk;
-                    }
-                    for (int k = 0; k < m; ++k) {
-                        const double kp = Qs[k * R + p], kq = Qs[k * R + qq];
-                        Qs[k * R + p] = cc * kp - sn * kq;
-                        Qs[k * R + qq] = sn * kp + cc * kq;
-                    }
-                }
-        }
-        // Y = L^-T Q (back substitution, column by column)
-        double *Yg = a.Y + st * R * R, *Cg = a.Ch + st * R * R, *lg = a.lam + st * R;
-        for (int jc = 0; jc < m; ++jc)
-            for (int i = m - 1; i >= 0; --i) {
-                double v = Qs[i * R + jc];
-                for (int l = i + 1; l < m; ++l) v -= Ls[l * R + i] * Qs[l * R + jc];
-                Qs[i * R + jc] = v / Ls[i * R + i];
-            }
-        for (int i = 0; i < m; ++i) {
-            lg[i] = Ss[i * R + i];
-            for (int k = 0; k < m; ++k) { Yg[i * R + k] = Qs[i * R + k]; Cg[i * R + k] = Chs[i * R + k]; }
-        }
-    }
-    __syncthreads();
-    if (s_fail) {
-        if (c == 0) { a.kr_state[st] = 2; a.kr_mode[st] = 0; }
-        return;
-    }
-    // modal basis W = V Y
-    const double *Yg = a.Y + st * R * R;
-    for (int jc = 0; jc < m; ++jc) {
-#pragma unroll
-        for (int k = 0; k < M; ++k) x[k] = 0.0;
-        for (int i = 0; i < m; ++i) {
-            const double yij = Yg[i * R + jc];
-            const double *col = Vs + (int64_t)i * P + c;
-#pragma unroll
-            for (int k = 0; k < M; ++k) x[k] = fma(yij, col[(int64_t)k * T], x[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < M; ++k) Ws[(int64_t)jc * P + (int64_t)k * T + c] = x[k];
-    }
-    if (c == 0) { a.kr_r[st] = m; a.kr_state[st] = 1; }
+    project<M, R>(a, z, Vs, rb, m, Ahs, Chs, sh);
+    return m;
 }
 
-// lifted stress at step k of node (chunk thread c, offset kk) from the modal form
-__device__ __forceinline__ double modal_sigma(const double *Ws, int64_t P, int64_t off, int m, const double *zs,
-                                              const double *cc, const double *rho, const double *z0,
-                                              const double *phi, const int *lin, double dt, int k) {
-    double v = 0.0;
-    for (int j = 0; j < m; ++j) {
-        const double w = Ws[(int64_t)j * P + off];
-        const double zj = lin[j] ? z0[j] + k * dt * phi[j] : zs[j] + cc[j] * pow(rho[j], (double)k);
-        v = fma(w, zj, v);
-    }
+// lifted stress of node slot `off` from reduced coordinates y (row of the table)
+template <typename R>
+__device__ __forceinline__ R lift(const R *Vs, int64_t P, int64_t off, int m, const R *y) {
+    R v = R(0);
+    for (int l = 0; l < m; ++l) v = fmx(Vs[(int64_t)l * P + off], y[l], v);
     return v;
 }
 
-template <int M>
-__global__ void __launch_bounds__(1024) k_kr_advance(KrArgs a) {
-    __shared__ double red[256], out[8], sv[32];
+template <int M, typename R>
+__global__ void __launch_bounds__(kr_max_threads<R>(M)) k_kr_step(KrArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char kr_dsm[];
+    __shared__ double red[2 * 16 * 32], out[16], sA[64], sB[64], sL[32], sR[32], sv[32];
+    __shared__ double h[kRm], h2[kRm], fh[kRm], sd[kRm], ssum[kRm], bv[kRm];
+    __shared__ R hi[kRm], lo[kRm], dl[2][kRm];
     __shared__ int si[32];
-    __shared__ double h[80], phi[80], z0[80], zs[80], cc[80], rho[80], rhoK[80];
-    __shared__ int lin[80];
-    const int t = a.trees[blockIdx.x], s = blockIdx.y, T = blockDim.x, c = threadIdx.x;
-    const int64_t st = (int64_t)s * a.n_trees + t;
-    if (!a.kr_mode[st] || a.kr_state[st] != 1) return;
-    const int kd = a.kdone[st];
-    if (kd >= a.n_steps) return;
-    const int K = a.n_steps - kd;
-    const double dt = a.dt, t0 = a.t0 + kd * dt;
-    const int64_t cb = a.toff[t];
-    const int n = (int)(a.toff[t + 1] - cb);
-    const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
-    const int R = a.rmax, m = a.kr_r[st];
-    const int64_t P = a.P;
-    const double *Vs = a.Vb + (int64_t)s * R * P + a.pbase[t];
-    const double *Ws = a.Wb + (int64_t)s * R * P + a.pbase[t];
+    __shared__ int s_fail;
+    __shared__ double s_m0;
+    int phase = 0;
+    const Sh sh{red, out, sA, sB, sL, sR, h, h2, &phase};
+    const int rm = a.rmax;
+    R *Ft = (R *)kr_dsm;                               // [rm][rm]: Ft[j*rm + l] = F_lj
+    R *tab = Ft + (size_t)rm * rm;                     // [(kc+1)][rm]: chunk trajectory
 
-    // reduced initial condition (Eq. rak_reduced: s_hat(0) = V^T s0) and forcing
-    double x[M];
-#pragma unroll
-    for (int k = 0; k < M; ++k) x[k] = sig_at(a, ps + (int64_t)k * T + c);
-    dots<M>(Vs, P, T, c, m, x, h, red, out);
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-        const int i = c * M + k;
-        x[k] = i < n ? a.f[cs + i] : 0.0;
+    Tr z;
+    z.t = a.trees[blockIdx.x]; z.s = blockIdx.y; z.T = blockDim.x; z.c = threadIdx.x;
+    z.st = (int64_t)z.s * a.n_trees + z.t;
+    if (!a.kr_mode[z.st]) return;
+    z.cb = a.toff[z.t];
+    z.n = (int)(a.toff[z.t + 1] - z.cb);
+    z.cs = (int64_t)z.s * a.N + z.cb;
+    z.ps = (int64_t)z.s * a.P + a.pbase[z.t];
+    z.P = a.P;
+    const int T = z.T, c = z.c, n = z.n;
+    R *Vs = a.Vb + (int64_t)z.s * rm * a.P + a.pbase[z.t];
+    double *Ahs = a.Ah + z.st * rm * rm, *Chs = a.Ch + z.st * rm * rm;
+    double *Lms = a.Lm + z.st * rm * rm, *Xs = a.Xs + z.st * rm * (rm + 1);
+    const int K = a.n_steps;
+    const double dt = a.dt;
+    int k = a.kdone[z.st];
+    int rb = a.kr_r[z.st];
+    bool fresh = false;
+    double ts_unused;
+    auto fallback = [&](int kd) {
+        if (c == 0) { a.kr_state[z.st] = 2; a.kr_mode[z.st] = 0; a.kdone[z.st] = kd; }
+    };
+    if (a.kr_state[z.st] != 1) {
+        rb = build<M, R>(a, z, Vs, Ahs, Chs, sh, ts_unused);
+        if (rb <= 0) { fallback(k); return; }
+        if (c == 0) { a.kr_r[z.st] = rb; a.kr_state[z.st] = 1; }
+        fresh = true;
     }
-    dots<M>(Ws, P, T, c, m, x, phi, red, out);     // phi = W^T f = Y^T f_h
-    if (c == 0) {
-        const double *Yg = a.Y + st * R * R, *Cg = a.Ch + st * R * R, *lg = a.lam + st * R;
-        for (int jm = 0; jm < m; ++jm) {           // z0 = Y^T C_h s_hat(0)
-            double v = 0.0;
-            for (int i = 0; i < m; ++i) {
-                double chs = 0.0;
-                for (int l = 0; l < m; ++l) chs += Cg[i * R + l] * h[l];
-                v += Yg[i * R + jm] * chs;
-            }
-            z0[jm] = v;
-            const double lam = lg[jm];
-            if (fabs(dt * lam) < 1e-13) {
-                lin[jm] = 1; zs[jm] = 0.0; cc[jm] = 0.0; rho[jm] = 1.0; rhoK[jm] = 1.0;
-            } else {
-                lin[jm] = 0;
-                rho[jm] = 1.0 / (1.0 - dt * lam);
-                zs[jm] = -phi[jm] / lam;
-                cc[jm] = v - zs[jm];
-                rhoK[jm] = pow(rho[jm], (double)K);
-            }
+    if (a.build_only) return;
+    const int64_t k_begin = k;
+    R x[M];
+    while (k < K) {
+        const int m = fresh ? rb : augment<M, R>(a, z, Vs, rb, Ahs, Chs, sh);
+        fresh = false;
+        // reduced forcing f_h = V^T f and initial condition s_hat(0) = V^T s
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk) {
+            const int i = c * M + kk;
+            x[kk] = i < n ? (R)a.f[z.cs + i] : R(0);
         }
-    }
-    __syncthreads();
-
-    // candidates: nodes whose bound over the whole step reaches their threshold;
-    // each scans the steps for its first crossing
-    int kf = INT_MAX;
+        dots<M, R>(Vs, z, m, x, fh, sh);
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-        const int i = c * M + k;
-        if (i >= n) continue;
-        const double th = a.thr[cs + i];
-        if (isinf(th)) continue;
-        const int64_t off = (int64_t)k * T + c;
-        double U = 0.0;
-        for (int j = 0; j < m; ++j) {
-            const double w = Ws[(int64_t)j * P + off];
-            double t1, tK;
-            if (lin[j]) { t1 = w * (z0[j] + dt * phi[j]); tK = w * (z0[j] + K * dt * phi[j]); }
-            else { t1 = w * (zs[j] + cc[j] * rho[j]); tK = w * (zs[j] + cc[j] * rhoK[j]); }
-            U += fmax(t1, tK);
+        for (int kk = 0; kk < M; ++kk) x[kk] = a.sig[z.ps + (int64_t)kk * T + c];
+        dots<M, R>(Vs, z, m, x, sd, sh);
+        // M = C_h - dt A_h, lower triangle, then Cholesky by warp 0
+        for (int idx = c; idx < m * m; idx += T) {
+            const int i = idx / m, jx = idx % m;
+            if (jx <= i) Lms[(int64_t)i * rm + jx] = Chs[(int64_t)i * rm + jx] - dt * Ahs[(int64_t)i * rm + jx];
         }
-        if (U < th - 1e-9 * fabs(th)) continue;
-        for (int kk = 1; kk <= K && kk < kf; ++kk)
-            if (modal_sigma(Ws, P, off, m, zs, cc, rho, z0, phi, lin, dt, kk) >= th) { kf = kk; break; }
-    }
-    const int kstar = (int)block_min((double)kf, sv);
-    const int kend = kstar < INT_MAX ? kstar : K;
-    double best = -INFINITY;
-    int arg = 0x7fffffff;
-    if (kstar < INT_MAX) {
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-            const int i = c * M + k;
-            if (i >= n) continue;
-            const double th = a.thr[cs + i];
-            if (isinf(th)) continue;
-            const double mg = modal_sigma(Ws, P, (int64_t)k * T + c, m, zs, cc, rho, z0, phi, lin, dt, kstar) - th;
-            if (mg > best) { best = mg; arg = i; }
+        // right-hand side of the first increment: dt (A_h s_hat(0) + f_h)
+        for (int i = c; i < m; i += T) {
+            double v = fh[i];
+            for (int jx = 0; jx < m; ++jx) v = fma(Ahs[(int64_t)i * rm + jx], sd[jx], v);
+            bv[i] = dt * v;
         }
-        block_argmax(best, arg, sv, si);
-    }
-    // void growth over steps 1..kend in closed form (existing voids only)
-    const int nv = a.v_count[st];
-    for (int q = 0; q < nv; ++q) {
-        const int v = a.v_node[st * a.maxv + q];
-        if (v / M != c) continue;
-        const int64_t off = (int64_t)(v % M) * T + c;
-        double ssum = 0.0;
-        for (int j = 0; j < m; ++j) {
-            const double w = Ws[(int64_t)j * P + off];
-            double zsum;
-            if (lin[j]) zsum = kend * z0[j] + dt * phi[j] * 0.5 * (double)kend * (kend + 1);
-            else zsum = kend * zs[j] + cc[j] * rho[j] * (1.0 - pow(rho[j], (double)kend)) / (1.0 - rho[j]);
-            ssum = fma(w, zsum, ssum);
-        }
-        a.v_vol[st * a.maxv + q] += dt * a.Binv * a.leak[cs + v] * ssum;
-    }
-    // lift at kend
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-        const int i = c * M + k;
-        const int64_t off = (int64_t)k * T + c;
-        if (i < n) sig_set(a, ps + off, modal_sigma(Ws, P, off, m, zs, cc, rho, z0, phi, lin, dt, kend));
-    }
-    if (c == 0) {
-        if (kstar < INT_MAX && best >= 0.0) {
-            const int v = arg;
-            const int64_t off = (int64_t)(v % M) * T + v / M;
-            const double s1 = modal_sigma(Ws, P, off, m, zs, cc, rho, z0, phi, lin, dt, kstar);
-            const double s0v = modal_sigma(Ws, P, off, m, zs, cc, rho, z0, phi, lin, dt, kstar - 1);
-            const double th = a.thr[cs + v];
-            const double m0 = s0v - th, m1 = s1 - th;
-            const double frac = m0 < 0.0 ? -m0 / (m1 - m0) : 0.0;
-            const int nvv = a.v_count[st];
-            if (nvv < a.maxv) {
-                const int64_t e = st * a.maxv + nvv;
-                int best_s = a.inc_seg[a.inc_ptr[cb + v]];
-                double bj = fabs(a.j[(int64_t)s * a.n_seg + best_s]);
-                for (int kx = a.inc_ptr[cb + v] + 1; kx < a.inc_ptr[cb + v + 1]; ++kx) {
-                    const double aj = fabs(a.j[(int64_t)s * a.n_seg + a.inc_seg[kx]]);
-                    if (aj > bj) { bj = aj; best_s = a.inc_seg[kx]; }
+        if (c == 0) s_fail = 0;
+        __syncthreads();
+        if (c < 32) {
+            const int lane = c;
+            for (int jx = 0; jx < m; ++jx) {
+                double d = Lms[(int64_t)jx * rm + jx];
+                __syncwarp();
+                if (!(d > 0.0)) { if (lane == 0) s_fail = 1; d = 1.0; }
+                d = sqrt(d);
+                if (lane == 0) Lms[(int64_t)jx * rm + jx] = d;
+                for (int i = jx + 1 + lane; i < m; i += 32) Lms[(int64_t)i * rm + jx] /= d;
+                __syncwarp();
+                for (int i = jx + 1 + lane; i < m; i += 32) {
+                    const double lij = Lms[(int64_t)i * rm + jx];
+                    for (int q2 = jx + 1; q2 <= i; ++q2) Lms[(int64_t)i * rm + q2] -= lij * Lms[(int64_t)q2 * rm + jx];
                 }
-                a.v_node[e] = v; a.v_seg[e] = best_s; a.v_vol[e] = 0.0;
-                a.v_tnuc[e] = t0 + ((double)(kstar - 1) + frac) * dt;
-                a.v_count[st] = nvv + 1;
-                atomicAdd(&a.counters[0], 1);
-            } else {
-                atomicOr(&a.status[kStatusOverflow], 1);
+                __syncwarp();
             }
-            a.thr[cs + v] = INFINITY;
-            a.dirty[st] = 1;                        // BE factors are stale too
-            a.kr_state[st] = 0;                     // the matrix changed: rebuild
-            atomicAdd(&a.counters[2], 1);
         }
-        a.kdone[st] = kd + kend;
+        __syncthreads();
+        if (s_fail) { fallback(k); return; }
+        // F = M^-1 C_h (column jx by thread jx) and the first increment (thread m)
+        for (int jx = c; jx <= m; jx += T) {
+            double *xs = Xs + (int64_t)jx * rm;
+            for (int i = 0; i < m; ++i) {
+                double v = jx < m ? Chs[(int64_t)i * rm + jx] : bv[i];
+                for (int q2 = 0; q2 < i; ++q2) v -= Lms[(int64_t)i * rm + q2] * xs[q2];
+                xs[i] = v / Lms[(int64_t)i * rm + i];
+            }
+            for (int i = m - 1; i >= 0; --i) {
+                double v = xs[i];
+                for (int q2 = i + 1; q2 < m; ++q2) v -= Lms[(int64_t)q2 * rm + i] * xs[q2];
+                xs[i] = v / Lms[(int64_t)i * rm + i];
+            }
+            if (jx < m)
+                for (int i = 0; i < m; ++i) Ft[(size_t)jx * rm + i] = (R)xs[i];
+            else
+                for (int i = 0; i < m; ++i) dl[0][i] = (R)xs[i];
+        }
+        for (int l = c; l < m; l += T) tab[l] = (R)sd[l];
+        __syncthreads();
+
+        // chunks of the reduced trajectory
+        int kseg = 0, cur = 0;
+        bool nucleated = false;
+        while (k + kseg < K) {
+            const int kc = min(a.kc, K - k - kseg);
+            for (int l = c; l < m; l += T) { hi[l] = (R)(-INFINITY); lo[l] = (R)INFINITY; }
+            __syncthreads();
+            if (c < 32) {                             // one warp steps the reduced system
+                for (int kk = 1; kk <= kc; ++kk) {
+                    for (int l = c; l < m; l += 32) {
+                        const R d = dl[cur][l];
+                        sd[l] += (double)d;
+                        const R sv2 = (R)sd[l];
+                        tab[(size_t)kk * rm + l] = sv2;
+                        hi[l] = max(hi[l], sv2);
+                        lo[l] = min(lo[l], sv2);
+                        R acc = R(0);
+                        for (int jx = 0; jx < m; ++jx) acc = fmx(Ft[(size_t)jx * rm + l], dl[cur][jx], acc);
+                        dl[cur ^ 1][l] = acc;
+                    }
+                    cur ^= 1;
+                    __syncwarp();
+                }
+            } else {
+                cur ^= kc & 1;
+            }
+            __syncthreads();
+            // candidates: nodes whose bound over the chunk reaches their
+            // threshold; each is lifted step by step to its first crossing
+            const R slack = sizeof(R) == 4 ? R(1e-5) : R(1e-12);
+            unsigned long long cand = 0ull;
+            int kf = INT_MAX;
+#pragma unroll 1
+            for (int kk = 0; kk < M; ++kk) {
+                const int i = c * M + kk;
+                if (i >= n) continue;
+                const double th = a.thr[z.cs + i];
+                if (isinf(th)) continue;
+                const int64_t off = (int64_t)kk * T + c;
+                R U = R(0), Aa = R(0);
+                for (int l = 0; l < m; ++l) {
+                    const R v = Vs[(int64_t)l * a.P + off];
+                    U += max(v * hi[l], v * lo[l]);
+                    Aa = fmx(fabs(v), max(fabs(hi[l]), fabs(lo[l])), Aa);
+                }
+                if ((double)(U + slack * Aa) < th) continue;
+                cand |= 1ull << kk;
+                for (int s2 = 1; s2 <= kc && s2 < kf; ++s2)
+                    if ((double)lift<R>(Vs, a.P, off, m, tab + (size_t)s2 * rm) >= th) { kf = s2; break; }
+            }
+            const double kfm = block_min((double)kf, sv);
+            const int kstar = kfm < (double)INT_MAX ? (int)kfm : INT_MAX;
+            int kend = kc;
+            double best = -INFINITY;
+            int arg = 0x7fffffff;
+            if (kstar != INT_MAX) {
+                kend = kstar;
+                for (int kk = 0; kk < M; ++kk) {
+                    if (!((cand >> kk) & 1ull)) continue;
+                    const int i = c * M + kk;
+                    const double mg =
+                        (double)lift<R>(Vs, a.P, (int64_t)kk * T + c, m, tab + (size_t)kstar * rm) - a.thr[z.cs + i];
+                    if (mg > best) { best = mg; arg = i; }
+                }
+                block_argmax(best, arg, sv, si);
+                nucleated = best >= 0.0;
+                if (nucleated && arg / M == c) {    // stress of the new void one step earlier
+                    const int64_t off = (int64_t)(arg % M) * T + c;
+                    const double prev = (kseg == 0 && kstar == 1)
+                                            ? (double)a.sig[z.ps + off]
+                                            : (double)lift<R>(Vs, a.P, off, m, tab + (size_t)(kstar - 1) * rm);
+                    s_m0 = prev - a.thr[z.cs + arg];
+                }
+            }
+            // void growth over steps 1..kend of the chunk (existing voids)
+            for (int l = c; l < m; l += T) {
+                double sacc = 0.0;
+                for (int s2 = 1; s2 <= kend; ++s2) sacc += (double)tab[(size_t)s2 * rm + l];
+                ssum[l] = sacc;
+            }
+            __syncthreads();
+            const int nv = a.v_count[z.st];
+            for (int qv = 0; qv < nv; ++qv) {
+                const int v = a.v_node[z.st * a.maxv + qv];
+                if (v / M != c) continue;
+                const int64_t off = (int64_t)(v % M) * T + c;
+                double sacc = 0.0;
+                for (int l = 0; l < m; ++l) sacc = fma((double)Vs[(int64_t)l * a.P + off], ssum[l], sacc);
+                a.v_vol[z.st * a.maxv + qv] += dt * a.Binv * a.leak[z.cs + v] * sacc;
+            }
+            const bool last = nucleated || (k + kseg + kend == K);
+            if (last) {                               // lift at kend
+                const R *y = tab + (size_t)kend * rm;
+#pragma unroll 1
+                for (int kk = 0; kk < M; ++kk) {
+                    const int i = c * M + kk;
+                    const int64_t off = (int64_t)kk * T + c;
+                    if (i < n) a.sig[z.ps + off] = lift<R>(Vs, a.P, off, m, y);
+                }
+            }
+            __syncthreads();
+            if (nucleated && c == 0) {
+                const int v = arg;
+                const double m0 = s_m0, m1 = best;
+                const double frac = m0 < 0.0 ? -m0 / (m1 - m0) : 0.0;
+                const int nvv = a.v_count[z.st];
+                if (nvv < a.maxv) {
+                    const int64_t e = z.st * a.maxv + nvv;
+                    int best_s = a.inc_seg[a.inc_ptr[z.cb + v]];
+                    double bj = fabs(a.j[(int64_t)z.s * a.n_seg + best_s]);
+                    for (int kx = a.inc_ptr[z.cb + v] + 1; kx < a.inc_ptr[z.cb + v + 1]; ++kx) {
+                        const double aj = fabs(a.j[(int64_t)z.s * a.n_seg + a.inc_seg[kx]]);
+                        if (aj > bj) { bj = aj; best_s = a.inc_seg[kx]; }
+                    }
+                    a.v_node[e] = v; a.v_seg[e] = best_s; a.v_vol[e] = 0.0;
+                    a.v_tnuc[e] = (a.t0p ? *a.t0p : a.t0) + ((double)(k + kseg + kstar - 1) + frac) * dt;
+                    a.v_count[z.st] = nvv + 1;
+                    atomicAdd(&a.counters[0], 1);
+                } else {
+                    atomicOr(&a.status[kStatusOverflow], 1);
+                }
+                a.thr[z.cs + v] = INFINITY;
+                a.dirty[z.st] = 1;                  // BE factors are stale too
+            }
+            kseg += kend;
+            if (nucleated) break;
+            // next chunk starts from the last row
+            for (int l = c; l < m; l += T) tab[l] = tab[(size_t)kend * rm + l];
+            __syncthreads();
+        }
+        k += kseg;
+        __syncthreads();
+        if (!nucleated) break;
+        // the void changed A: rebuild from the lifted stress and carry on
+        rb = build<M, R>(a, z, Vs, Ahs, Chs, sh, ts_unused);
+        if (rb <= 0) {
+            if (c == 0) atomicAdd(a.work, (unsigned long long)n * (unsigned long long)(k - k_begin));
+            fallback(k);
+            return;
+        }
+        if (c == 0) { a.kr_r[z.st] = rb; a.kr_state[z.st] = 1; atomicAdd(&a.counters[2], 1); }
+        fresh = true;
+    }
+    if (c == 0) {
+        a.kdone[z.st] = K;
+        atomicAdd(a.work, (unsigned long long)n * (unsigned long long)(K - k_begin));
     }
 }
 
-KrArgs kr_args(ems_ctx *c, double dt, int n_steps) {
+template <typename R>
+KrArgs<R> kr_args(ems_ctx *c, double dt, int n_steps, int build_only) {
     Dev &d = c->d;
-    KrArgs a;
+    KrArgs<R> a;
     a.toff = d.toff; a.pbase = d.pbase; a.N = c->N; a.P = c->P;
-    a.n_trees = c->n_trees; a.S = c->S; a.rmax = c->rmax; a.q = c->kr_q; a.eta = c->kr_eta; a.eps_rel = 1e-10;
-    a.V = d.V; a.g = d.g; a.leak = d.leak; a.f = d.f; a.kap_a = d.kap_a; a.dx = d.face_dx; a.area = d.face_area;
-    a.thr = d.thr; a.sig = d.sig; a.f32 = c->prm.precision == EMS_F32 ? 1 : 0;
+    a.n_trees = c->n_trees; a.rmax = c->rmax; a.q = c->kr_q; a.kc = c->kr_kc;
+    a.eta = c->kr_eta; a.eps_rel = 1e-10;
+    a.Vn = d.V; a.g = d.g; a.leak = d.leak; a.f = d.f; a.kap_a = d.kap_a; a.dx = d.face_dx; a.area = d.face_area;
+    a.thr = d.thr; a.sig = (R *)d.sig;
     a.sp = d.kr_sp; a.sg = d.kr_sg; a.su = d.kr_su; a.sPf = d.kr_sPf; a.sPb = d.kr_sPb;
-    a.Vb = d.kr_V; a.Wb = d.kr_W; a.lam = d.kr_lam; a.Y = d.kr_Y; a.Ch = d.kr_Ch; a.s0 = d.kr_s0;
+    a.Vb = (R *)d.kr_V; a.Ah = d.kr_Ah; a.Ch = d.kr_Ch; a.Lm = d.kr_Lm; a.Xs = d.kr_Xs; a.s0 = d.kr_s0;
     a.kr_r = d.kr_r; a.kr_state = d.kr_state; a.kr_mode = d.kr_mode; a.kdone = d.kdone;
-    a.dt = dt; a.t0 = c->t; a.Binv = 1.0 / c->prm.B_modulus; a.n_steps = n_steps;
+    a.dt = dt; a.t0 = c->t; a.Binv = 1.0 / c->prm.B_modulus; a.n_steps = n_steps; a.build_only = build_only;
+    a.t0p = c->graph_capturing ? d.gtime : nullptr;
     a.v_count = d.v_count; a.v_node = d.v_node; a.v_seg = d.v_seg; a.v_vol = d.v_vol; a.v_tnuc = d.v_tnuc;
     a.maxv = c->maxv; a.dirty = d.dirty; a.j = d.j; a.n_seg = c->n_seg; a.inc_ptr = d.inc_ptr;
-    a.inc_seg = d.inc_seg; a.status = d.status; a.counters = d.counters;
+    a.inc_seg = d.inc_seg; a.status = d.status; a.counters = d.counters; a.work = d.work;
     return a;
 }
 
-template <int M>
-ems_status launch_kr(ems_ctx *c, const Bucket &b, KrArgs &a, bool build) {
+template <int M, typename R>
+ems_status launch_kr(ems_ctx *c, const Bucket &b, KrArgs<R> &a) {
+    if (b.T > kr_max_threads<R>(M)) return fail(c, EMS_E_STATE, "chunk shape exceeds the Krylov kernel's limit");
     dim3 grid((unsigned)b.trees.size(), c->S);
-    if (build) {
-        const size_t smem = sizeof(double) * (4 * (size_t)c->rmax * c->rmax + 2 * (size_t)c->rmax);
-        if (smem > 48 * 1024)
-            EMS_CUDA(c, cudaFuncSetAttribute(k_kr_build<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_kr_build<M><<<grid, b.T, smem, c->stream>>>(a);
-    } else {
-        k_kr_advance<M><<<grid, b.T, 0, c->stream>>>(a);
-    }
+    const size_t smem = sizeof(R) * ((size_t)c->rmax * c->rmax + (size_t)(c->kr_kc + 1) * c->rmax);
+    if (smem > 48 * 1024)
+        EMS_CUDA(c, cudaFuncSetAttribute(k_kr_step<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_kr_step<M, R><<<grid, b.T, smem, c->stream>>>(a);
     ++c->launches;
     EMS_CUDA(c, cudaGetLastError());
     return EMS_OK;
 }
 
-ems_status kr_pass(ems_ctx *c, KrArgs &a, bool build) {
+template <typename R>
+ems_status kr_pass(ems_ctx *c, KrArgs<R> &a) {
     for (auto &b : c->buckets) {
         if (!b.chain) continue;
         a.trees = b.d_trees;
         switch (b.M) {
-            case 4: EMS_TRY(launch_kr<4>(c, b, a, build)); break;
-            case 8: EMS_TRY(launch_kr<8>(c, b, a, build)); break;
-            case 16: EMS_TRY(launch_kr<16>(c, b, a, build)); break;
-            case 32: EMS_TRY(launch_kr<32>(c, b, a, build)); break;
-            case 64: EMS_TRY(launch_kr<64>(c, b, a, build)); break;
+            case 4: EMS_TRY((launch_kr<4, R>(c, b, a))); break;
+            case 8: EMS_TRY((launch_kr<8, R>(c, b, a))); break;
+            case 16: EMS_TRY((launch_kr<16, R>(c, b, a))); break;
+            case 32: EMS_TRY((launch_kr<32, R>(c, b, a))); break;
+            case 64: EMS_TRY((launch_kr<64, R>(c, b, a))); break;
             default: return fail(c, EMS_E_STATE, "unsupported chunk length");
         }
     }
     return EMS_OK;
 }
 
-// reduced-model eligibility (Eq. krylov_threshold): chains with n >= max(3q, 30)
-ems_status set_modes(ems_ctx *c, int q) {
-    const int S = c->S, nt = c->n_trees;
-    std::vector<int32_t> mode((size_t)S * nt, 0);
-    for (int t = 0; t < nt; ++t) {
-        const int64_t n = c->trees.off[t + 1] - c->trees.off[t];
-        const bool ok = c->pack[t].T > 1 && n >= (3 * q > 30 ? 3 * q : 30);
-        for (int s = 0; s < S; ++s) mode[(size_t)s * nt + t] = ok ? 1 : 0;
+ems_status run_pass(ems_ctx *c, double dt, int n_steps, int build_only) {
+    if (c->prm.precision == EMS_F32) {
+        KrArgs<float> a = kr_args<float>(c, dt, n_steps, build_only);
+        return kr_pass<float>(c, a);
     }
-    EMS_CUDA(c, cudaMemcpyAsync(c->d.kr_mode, mode.data(), 4 * mode.size(), cudaMemcpyHostToDevice, c->stream));
-    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
-    return EMS_OK;
+    KrArgs<double> a = kr_args<double>(c, dt, n_steps, build_only);
+    return kr_pass<double>(c, a);
 }
 
+// chunk length of the on-chip trajectory: the propagator and the table in
+// about 96 KB of shared memory
+int chunk_steps(int rmax, size_t eb) {
+    const size_t budget = 96 * 1024, f = eb * (size_t)rmax * rmax;
+    long kc = (long)((budget > f ? budget - f : 0) / (eb * (size_t)rmax)) - 1;
+    if (kc > 256) kc = 256;
+    if (kc < 8) kc = 8;
+    return (int)kc;
+}
+
+// reduced-model eligibility (Eq. krylov_threshold): chains with n >= max(3q, 30);
+// kept on the device and copied into the mode flags before every pass
 ems_status ensure_q(ems_ctx *c, int q, double eta) {
     if (c->rmax == 0) return fail(c, EMS_E_STATE, "context created with method EMS_BE: no Krylov storage");
-    if (q < 1 || 2 * q > c->rmax || !(eta > 0.0)) return fail(c, EMS_E_INVAL, "q must be 1..params.krylov_q, eta > 0");
+    if (q < 1 || 2 * q + 2 > c->rmax || !(eta > 0.0)) return fail(c, EMS_E_INVAL, "q must be 1..params.krylov_q, eta > 0");
     if (q != c->kr_q || eta != c->kr_eta) {
         c->kr_q = q;
         c->kr_eta = eta;
-        EMS_CUDA(c, cudaMemsetAsync(c->d.kr_state, 0, sizeof(int32_t) * c->S * c->n_trees, c->stream));
+        c->kr_kc = chunk_steps(c->rmax, c->prm.precision == EMS_F32 ? 4 : 8);
+        const int S = c->S, nt = c->n_trees;
+        std::vector<int32_t> ok((size_t)S * nt, 0);
+        for (int t = 0; t < nt; ++t) {
+            const int64_t n = c->trees.off[t + 1] - c->trees.off[t];
+            const bool e = c->pack[t].T > 1 && n >= (3 * q > 30 ? 3 * q : 30);
+            for (int s = 0; s < S; ++s) ok[(size_t)s * nt + t] = e ? 1 : 0;
+        }
+        EMS_CUDA(c, cudaMemcpyAsync(c->d.kr_ok, ok.data(), 4 * ok.size(), cudaMemcpyHostToDevice, c->stream));
+        EMS_CUDA(c, cudaMemsetAsync(c->d.kr_state, 0, sizeof(int32_t) * S * nt, c->stream));
+        EMS_CUDA(c, cudaStreamSynchronize(c->stream));
     }
+    return EMS_OK;
+}
+
+ems_status set_modes(ems_ctx *c) {
+    EMS_CUDA(c, cudaMemcpyAsync(c->d.kr_mode, c->d.kr_ok, sizeof(int32_t) * c->S * c->n_trees,
+                                cudaMemcpyDeviceToDevice, c->stream));
     return EMS_OK;
 }
 
 }  // namespace
 
-ems_status krylov_advance(ems_ctx *c, double dt, int n_steps, int method, int *n_new) {
-    (void)method;
-    EMS_TRY(ensure_q(c, c->kr_q > 0 ? c->kr_q : c->prm.krylov_q, c->kr_q > 0 ? c->kr_eta : c->prm.krylov_eta));
-    EMS_TRY(set_modes(c, c->kr_q));
+ems_status krylov_prepare(ems_ctx *c) {
+    return ensure_q(c, c->kr_q > 0 ? c->kr_q : c->prm.krylov_q, c->kr_q > 0 ? c->kr_eta : c->prm.krylov_eta);
+}
+
+// one aging step: reduced models for the eligible chains (one launch per
+// chunk shape), then backward Euler for the rest and for any tree that fell
+// back.  No host synchronisation once krylov_prepare has run, so the TTF
+// graph captures it.
+ems_status krylov_stress(ems_ctx *c, double dt, int n_steps) {
     cudaStream_t st = c->stream;
+    EMS_TRY(set_modes(c));
     EMS_CUDA(c, cudaMemsetAsync(c->d.counters, 0, 3 * sizeof(int32_t), st));
     EMS_CUDA(c, cudaMemsetAsync(c->d.kdone, 0, sizeof(int32_t) * c->S * c->n_trees, st));
-    KrArgs a = kr_args(c, dt, n_steps);
-    for (int round = 0; round < 4 * EMS_MAX_VOIDS; ++round) {
-        EMS_TRY(kr_pass(c, a, true));
-        EMS_TRY(kr_pass(c, a, false));
-        int32_t again = 0;
-        EMS_CUDA(c, cudaMemcpyAsync(&again, c->d.counters + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        EMS_CUDA(c, cudaStreamSynchronize(st));
-        if (again == 0) break;
-        EMS_CUDA(c, cudaMemsetAsync(c->d.counters + 2, 0, sizeof(int32_t), st));
-    }
-    // trees without a reduced model (small, branched, fallen back) take BE
-    EMS_TRY(launch_be(c, dt, n_steps));
-    if (dt != c->factored_dt) c->factored_dt = dt;
+    EMS_TRY(run_pass(c, dt, n_steps, 0));
+    return launch_be(c, dt, n_steps);
+}
+
+ems_status krylov_advance(ems_ctx *c, double dt, int n_steps, int method, int *n_new) {
+    (void)method;
+    EMS_TRY(krylov_prepare(c));
+    EMS_TRY(krylov_stress(c, dt, n_steps));
     c->t += dt * n_steps;
-    if (n_new) EMS_CUDA(c, cudaMemcpyAsync(n_new, c->d.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (n_new) EMS_CUDA(c, cudaMemcpyAsync(n_new, c->d.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     return EMS_OK;
 }
 
@@ -732,17 +919,17 @@ extern "C" ems_status ems_krylov_reduce(ems_ctx *c, int q, double eta, int *n_re
     if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
     if (!c->have_u) return fail(c, EMS_E_STATE, "Krylov reduction before the first IR solve");
     EMS_TRY(ensure_q(c, q, eta));
-    EMS_TRY(set_modes(c, q));
+    EMS_TRY(set_modes(c));
     EMS_TRY(forcing(c));
-    KrArgs a = kr_args(c, 0.0, 0);
-    EMS_TRY(kr_pass(c, a, true));
+    EMS_TRY(run_pass(c, 0.0, 0, 1));
     const size_t ts = (size_t)c->S * c->n_trees;
     std::vector<int32_t> state(ts), mode(ts);
     EMS_CUDA(c, cudaMemcpyAsync(state.data(), c->d.kr_state, 4 * ts, cudaMemcpyDeviceToHost, c->stream));
-    EMS_CUDA(c, cudaMemcpyAsync(mode.data(), c->d.kr_mode, 4 * ts, cudaMemcpyDeviceToHost, c->stream));
+    EMS_CUDA(c, cudaMemcpyAsync(mode.data(), c->d.kr_ok, 4 * ts, cudaMemcpyDeviceToHost, c->stream));
     EMS_CUDA(c, cudaStreamSynchronize(c->stream));
     int nr = 0, nf = 0;
     for (size_t k = 0; k < ts; ++k) {
+        if (!mode[k]) continue;
         if (state[k] == 1) ++nr;
         if (state[k] == 2) ++nf;
     }

@@ -2,11 +2,12 @@
 //
 // Per aging step: forcing from the current currents, n_inner backward-Euler
 // steps with nucleation, void-growth resistance, IR re-solve, max drop, TTF
-// crossing test.  With the BE method all aging steps of all samples are
-// captured once into a CUDA graph and launched as one unit; the crossing
-// test, the time and the PCG iteration count live on the device, and the
-// host reads the results once.  The Krylov method needs host decisions
-// between rebuild rounds and keeps the host-driven loop.
+// crossing test.  All aging steps of all samples (BE, or the reduced models
+// plus BE for the trees without one) are captured once into a CUDA graph and
+// launched as one unit; the crossing test, the time and the PCG iteration
+// count live on the device, and the host reads the results once.  The
+// host-driven loop remains for runs longer than the configured schedule and
+// on request (no_graph).
 #include <cmath>
 #include <vector>
 
@@ -125,7 +126,7 @@ ems_status finish(ems_ctx *c, ems_ttf_result *out, const std::vector<double> &tt
     return EMS_OK;
 }
 
-// all aging steps as one captured graph (BE method)
+// all aging steps as one captured graph (BE, or reduced models plus BE)
 ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
     const ems_params &p = c->prm;
     const double dto = p.horizon / p.n_outer, dti = dto / p.n_inner;
@@ -144,6 +145,8 @@ ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
     // the captured launches never need a global refactor
     EMS_CUDA(c, cudaMemsetAsync(d.kr_mode, 0, sizeof(int32_t) * S * c->n_trees, st));
     EMS_CUDA(c, cudaMemsetAsync(d.kdone, 0, sizeof(int32_t) * S * c->n_trees, st));
+    const bool kr = p.method != EMS_BE;
+    if (kr) EMS_TRY(krylov_prepare(c));
     if (c->factored_dt != dti) {
         std::vector<int32_t> ones((size_t)S * c->n_trees, 1);
         EMS_CUDA(c, cudaMemcpyAsync(d.dirty, ones.data(), 4 * ones.size(), cudaMemcpyHostToDevice, st));
@@ -170,7 +173,7 @@ ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
             cudaEvent_t *ev = &c->gev[4 * (size_t)k];
             if (cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal) != cudaSuccess) { sx = EMS_E_CUDA; break; }
             if ((sx = forcing(c)) != EMS_OK) break;
-            if ((sx = launch_be(c, dti, p.n_inner)) != EMS_OK) break;
+            if ((sx = kr ? krylov_stress(c, dti, p.n_inner) : launch_be(c, dti, p.n_inner)) != EMS_OK) break;
             if (cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal) != cudaSuccess) { sx = EMS_E_CUDA; break; }
             if ((sx = void_update(c, nullptr)) != EMS_OK) break;
             if (cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal) != cudaSuccess) { sx = EMS_E_CUDA; break; }
@@ -238,7 +241,7 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
         EMS_TRY(ir_currents_and_drop(c));
         EMS_TRY(screen_counts(c, out));
     }
-    if (p.method == EMS_BE && !(opts && opts->no_graph) && n_out <= p.n_outer) return ttf_graph(c, n_out, out);
+    if (!(opts && opts->no_graph) && n_out <= p.n_outer) return ttf_graph(c, n_out, out);
 
     const double dto = p.horizon / p.n_outer, dti = dto / p.n_inner;
     const double thr = p.ir_fail_frac;

@@ -247,28 +247,84 @@ def test_stress_before_ir_is_state_error():
 
 
 def test_krylov_tiny_matches_oracle_and_be():
-    """Reduced models (Sec. IV-E) on every 281-node stripe, q = 10: the GPU
-    path against the oracle's Alg. 1, and both against full BE with the
-    paper's metric (TTF if failed, else final drop; < 0.05 %)."""
+    """Reduced models (Sec. IV-E) on every 281-node stripe, q = 20, with the
+    cached-and-augmented bases of Sec. IV-E.4: the GPU path against the
+    oracle's, and both against full BE with the paper's metric (TTF if
+    failed, else final drop; < 0.05 %)."""
     from paper_2604_10743_gb300 import EMS_KRYLOV
     from oracle import krylov as K
     g = es.tiny_grid()
-    p = es.default_params(krylov_q=10)
+    p = es.default_params(krylov_q=20)
     eng = _engine(p, g, method=EMS_KRYLOV)
     r = eng.ttf()
-    ks = K.KrylovStepper(q=10)
+    ks = K.KrylovStepper(q=20)
     ref = F.run_ttf(g, p, keep_state=True, stepper=ks)
-    # two FP64 implementations of the Krylov recursion agree to round-off
-    # amplified by the conditioning of the power sequence (~1e-6 here), an
-    # order below the reduced model's own error against BE (~2e-5 at q = 10)
+    # two FP64 implementations of the same recursion (Gram-Schmidt order,
+    # increment-form reduced stepping) agree to round-off amplified by the
+    # conditioning of the bases, an order below the reduced model's own
+    # error against BE
     assert _relerr(eng.sigma()[0], ref["state"].sigma) < 1e-5
     gpu, ora, _ = _void_sets(eng, ref)
     assert gpu == ora
     assert abs(r["final_drop"][0] - ref["final_drop"]) <= 1e-6 * ref["final_drop"]
+    assert abs(r["ttf"][0] - ref["ttf"]) <= 1e-6 * ref["ttf"]
     be = F.run_ttf(g, p)
     metric = "ttf" if math.isfinite(be["ttf"]) else "final_drop"
     assert abs(r[metric][0] - be[metric]) <= TTF_TOL * be[metric]
     eng.close()
+
+
+def test_krylov_f32_tiny_matches_oracle():
+    """The FP32 reduced path (FP32 bases and lifts, FP64 cross-thread sums and
+    small dense algebra) against the FP64 oracle on the same run."""
+    from paper_2604_10743_gb300 import EMS_KRYLOV, EMS_F32
+    from oracle import krylov as K
+    g = es.tiny_grid()
+    p = es.default_params(krylov_q=20)
+    eng = _engine(p, g, method=EMS_KRYLOV, precision=EMS_F32)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True, stepper=K.KrylovStepper(q=20))
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < 1e-3
+    gpu, ora, _ = _void_sets(eng, ref)
+    assert [v for v, _ in gpu] == [v for v, _ in ora]
+    assert abs(r["ttf"][0] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
+    eng.close()
+
+
+def test_krylov_f32_grid_matches_be():
+    """64 x 64 grid (128 stripes of 1,261 nodes), FP32, q = 30: the reduced
+    models reproduce the GPU BE run's final IR drop within 0.05 % with the
+    same voids."""
+    from paper_2604_10743_gb300 import EMS_KRYLOV, EMS_F32
+    g = es.mid_grid(N=64)
+    p = es.default_params(krylov_q=30)
+    e1 = _engine(p, g, precision=EMS_F32, max_voids=32)
+    r1 = e1.ttf()
+    v1 = e1.voids()
+    e1.close()
+    e2 = _engine(p, g, method=EMS_KRYLOV, precision=EMS_F32, max_voids=32)
+    r2 = e2.ttf()
+    v2 = e2.voids()
+    e2.close()
+    assert abs(r2["final_drop"][0] - r1["final_drop"][0]) <= TTF_TOL * r1["final_drop"][0]
+    assert sorted(v1["node"].tolist()) == sorted(v2["node"].tolist())
+
+
+def test_krylov_graph_run_equals_host_loop():
+    """The reduced-model TTF run captured in one CUDA graph against the same
+    run driven from the host: identical stress, drops and TTF."""
+    from paper_2604_10743_gb300 import EMS_KRYLOV
+    g = es.tiny_grid()
+    p = es.default_params(krylov_q=20, n_outer=16)
+    a = _engine(p, g, method=EMS_KRYLOV)
+    b = _engine(p, g, method=EMS_KRYLOV)
+    ra = a.ttf(graph=True)
+    rb = b.ttf(graph=False)
+    assert ra["graph"] and not rb["graph"]
+    assert np.array_equal(a.sigma(), b.sigma())
+    assert np.array_equal(ra["drops"], rb["drops"])
+    assert np.array_equal(ra["ttf"], rb["ttf"])
+    a.close(); b.close()
 
 
 def test_krylov_reduce_counts():

@@ -93,3 +93,57 @@ def test_nucleation_time_converges_with_order():
     # the cited accuracy (about 1 % at q = 4-6) tightens with the order
     assert errs[0] < 0.2 and errs[1] < 0.02 and errs[2] < 1e-3
     assert errs[2] < errs[1] < errs[0]
+
+
+def test_augmented_basis_matches_the_new_input():
+    """A basis cached for one forcing and stress, extended by the current
+    starting block [R C s, R f] (the cache policy of Sec. IV-E.4): the
+    columns stay orthonormal, R C s and R f lie in the span, so the reduced
+    model reproduces the new input's zeroth shifted moment exactly."""
+    g, tr, phys, f_old = _chain(cells=25, I_sink=2e-3)
+    _, _, _, f_new = _chain(cells=25, I_sink=3e-3, seed=1)
+    n = tr["n_nodes"]
+    void = np.zeros(n, np.int32)
+    C, A, fo = K.tree_system(tr, phys, f_old, void, 0)
+    _, _, fn = K.tree_system(tr, phys, f_new, void, 0)
+    s0 = 1.0 / K.shift_time(tr, phys, 0, 1.0)
+    V, _, _, _, st = K.krylov_basis(C, A, fo, np.zeros(n), s0, 4)
+    assert st == "ok" and V.shape[1] == 4
+    a = F.StressState(tr, P)
+    F.advance(tr, P, dict(phys, sig_crit=np.full(n, np.inf)), f_new, a, 0.0, 2e4, 30)
+    lu = spla.splu((s0 * C - A).tocsc())
+    Va = K.augment(V, lu, C, a.sigma, fn)
+    assert Va.shape[1] == 6
+    assert np.abs(Va.T @ Va - np.eye(6)).max() < 1e-12
+    for x in (lu.solve(C @ a.sigma), lu.solve(fn)):
+        assert np.linalg.norm(x - Va @ (Va.T @ x)) < 1e-10 * np.linalg.norm(x)
+    Kh = Va.T @ ((s0 * C - A) @ Va)
+    m = lu.solve(fn)
+    assert np.abs(Va @ np.linalg.solve(Kh, Va.T @ fn) - m).max() < 1e-9 * np.abs(m).max()
+    # a block already in the span adds nothing
+    assert K.augment(Va, lu, C, a.sigma, fn).shape[1] == 6
+
+
+def test_augmented_cache_tracks_backward_euler_stale_cache_does_not():
+    """Two aging steps with different forcings on a 161-node chain: the cached
+    basis augmented by the current block follows full BE closely, the same
+    basis reused as it stands (keyed on C, A and s0 alone) does not."""
+    g, tr, phys, f1 = _chain(cells=40, I_sink=2e-3)
+    _, _, _, f2 = _chain(cells=40, I_sink=4e-3, seed=3)
+    n = tr["n_nodes"]
+    ph = dict(phys, sig_crit=np.full(n, np.inf))
+    dt, ns = 2e4, 100
+    ref = F.StressState(tr, P)
+    F.advance(tr, P, ph, f1, ref, 0.0, dt, ns)
+    F.advance(tr, P, ph, f2, ref, ns * dt, dt, ns)
+    err = {}
+    for policy in ("augment", "stale"):
+        ks = K.KrylovStepper(q=6, policy=policy)
+        ks.use_krylov = lambda nn: True
+        st = F.StressState(tr, P)
+        ks(tr, P, ph, f1, st, 0.0, dt, ns)
+        ks(tr, P, ph, f2, st, ns * dt, dt, ns)
+        assert ks.n_built == 1
+        err[policy] = np.abs(st.sigma - ref.sigma).max() / np.abs(ref.sigma).max()
+    assert err["augment"] < 3e-4
+    assert err["stale"] > 30 * err["augment"]
