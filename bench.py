@@ -324,7 +324,7 @@ def mc_leg(p, peaks, src, stream, n_samples=1024, reps=2):
     return out
 
 
-def krylov_leg(g, p, stream, be, q=20):
+def krylov_leg(g, p, stream, be, q=20, oracle=True):
     """The rational Krylov reduced models (method AUTO, order q, cached bases
     extended by the current starting block) on the bench workload: TTF wall
     time and the final-drop difference from the BE run (the paper's metric
@@ -351,6 +351,8 @@ def krylov_leg(g, p, stream, be, q=20):
     out = {"q": q, "ttf_wall_ms": round(t, 2), "stress_ms": round(r["stress_ms"], 2), "ir_ms": round(r["ir_ms"], 2),
            "node_steps_per_s": r["node_steps"] / (t / 1e3), "graph": r["graph"], "voids": nv,
            "final_drop_rel_diff_vs_be": abs(r["final_drop"][0] - be["final_drop"][0]) / be["final_drop"][0]}
+    if not oracle:
+        return out
     from oracle import flow as F, krylov as K
     g1 = dict(g)
     g1["trees"] = F.build_trees(g1)
@@ -421,6 +423,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--krylov", action="store_true", help="also time the Krylov reduced model (slow oracle leg)")
+    ap.add_argument("--krylov-only", action="store_true",
+                    help="time only the Krylov TTF run and its BE reference (profiling); prints its own JSON line")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="time only the surrogate inference (profiling); prints its own JSON line")
     ap.add_argument("--surrogate-rows", type=int, default=4096 * 1024)
@@ -430,7 +434,17 @@ def main():
     else:
         import __graft_entry__ as ge
         ge.build()
-        if args.surrogate_only:
+        if args.krylov_only:
+            import torch
+            import ems_synth as es
+            from paper_2604_10743_gb300 import EMS_F32
+            from paper_2604_10743_gb300.engine import Engine
+            g, p = es.mid_grid(), es.default_params()
+            e = Engine(p, g, precision=EMS_F32)
+            be = e.ttf()
+            e.close()
+            print(json.dumps({"krylov": krylov_leg(g, p, torch.cuda.current_stream(), be, oracle=not args.no_cpu)}))
+        elif args.surrogate_only:
             import torch
             peaks, src = _peaks()
             print(json.dumps({"surrogate": surrogate_leg(peaks, src, torch.cuda.current_stream(),

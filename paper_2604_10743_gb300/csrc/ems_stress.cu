@@ -767,17 +767,31 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
         R qprev = gk * (left - sg[0]);
         R z = R(0);
         R zr[M];
+        if (vmask == 0u) {                     // no void in this chunk (the common case)
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-            const R nxt = k + 1 < M ? sg[k + 1] : right;
-            const R gk1 = k + 1 < M ? cg[k + 1] : g_next;
-            const R qn = gk1 * (sg[k] - nxt);
-            R r = qprev - qn + cbt[k];
-            if ((vmask >> k) & 1u) r -= cth[k] * sg[k];
-            z = cp[k] * fmx(gk, z, r);
-            zr[k] = z;
-            qprev = qn;
-            gk = gk1;
+            for (int k = 0; k < M; ++k) {
+                const R nxt = k + 1 < M ? sg[k + 1] : right;
+                const R gk1 = k + 1 < M ? cg[k + 1] : g_next;
+                const R qn = gk1 * (sg[k] - nxt);
+                const R r = qprev - qn + cbt[k];
+                z = cp[k] * fmx(gk, z, r);
+                zr[k] = z;
+                qprev = qn;
+                gk = gk1;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const R nxt = k + 1 < M ? sg[k + 1] : right;
+                const R gk1 = k + 1 < M ? cg[k + 1] : g_next;
+                const R qn = gk1 * (sg[k] - nxt);
+                R r = qprev - qn + cbt[k];
+                if ((vmask >> k) & 1u) r -= cth[k] * sg[k];
+                z = cp[k] * fmx(gk, z, r);
+                zr[k] = z;
+                qprev = qn;
+                gk = gk1;
+            }
         }
         const R cf = scan_fwd<R>(z, cpf[M - 1], sA, sB, sC);
         R x = R(0);
@@ -808,8 +822,13 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
         // exact test in FP64 on a hit.  The barrier also publishes the
         // boundary stresses for the next step's halo.
         bool hit = false;
+        if (vmask == 0u) {
 #pragma unroll
-        for (int k = 0; k < M; ++k) hit |= !((vmask >> k) & 1u) && sg[k] >= cth[k];
+            for (int k = 0; k < M; ++k) hit |= sg[k] >= cth[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < M; ++k) hit |= !((vmask >> k) & 1u) && sg[k] >= cth[k];
+        }
         if (lane == 31) sL[w] = sg[M - 1];
         if (lane == 0) sR[w] = sg[0];
         int refac_from = -1;
