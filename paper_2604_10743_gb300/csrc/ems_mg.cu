@@ -400,33 +400,50 @@ __device__ __forceinline__ Lv level(const MGArgs &a, const double *val0, const d
 // Phase sequence of the V-cycle from level l0 (input r_l0, output out) over
 // the rows [start, n) in steps of `stride`, with `sync` between phases.
 // Level l's result lands in t_l (out for l0); the coarsest level's in e.
+// fused: the caller has already set e_l0 = w D^-1 r_l0, and each restriction
+// also sets the next level's e (the pre-smoothing needs no phase of its own).
 template <class Sync>
 __device__ bool vcycle(const MGArgs &a, const double *val0, const double *dinv0, double *sc, int l0, int l1,
-                       const double *r_l0, double *out, int start, int stride, Sync sync) {
+                       const double *r_l0, double *out, int start, int stride, Sync sync, bool fused = false) {
     const int L = a.g.L;
     const double *r = r_l0;
     for (int l = l0; l < l1 && l < L - 1; ++l) {
         const Lv A = level(a, val0, dinv0, l);
         const MGLevelDesc &d = a.g.lv[l];
         double *e = sc + d.e, *t = sc + d.t;
-        for (int i = start; i < A.n; i += stride) e[i] = kSmooth * A.dv[i] * r[i];
-        if (!sync()) return false;
+        if (!fused) {
+            for (int i = start; i < A.n; i += stride) e[i] = kSmooth * A.dv[i] * r[i];
+            if (!sync()) return false;
+        }
         for (int i = start; i < A.n; i += stride) t[i] = r[i] - csr_dot(A.ap, A.ac, A.av, e, i);
         if (!sync()) return false;
         const MGLevelDesc &dn = a.g.lv[l + 1];
         double *rn = sc + dn.r;
         const int32_t *rp = a.g.I + d.r_ptr, *rc = a.g.I + d.r_col;
         const double *rv = a.g.D + d.r_val;
-        for (int i = start; i < dn.n; i += stride) rn[i] = csr_dot(rp, rc, rv, t, i);
+        if (fused && l + 1 < L - 1) {
+            const double *dvn = a.g.D + dn.dinv;
+            double *en = sc + dn.e;
+            for (int i = start; i < dn.n; i += stride) {
+                const double v = csr_dot(rp, rc, rv, t, i);
+                rn[i] = v;
+                en[i] = kSmooth * dvn[i] * v;
+            }
+        } else {
+            for (int i = start; i < dn.n; i += stride) rn[i] = csr_dot(rp, rc, rv, t, i);
+        }
         if (!sync()) return false;
         r = rn;
     }
     return true;
 }
 
+// acc (optional): the last phase also accumulates r.z and r.r of the rows it
+// writes into acc[0], acc[1] and leaves the closing barrier to the caller
 template <class Sync>
 __device__ bool vcycle_up(const MGArgs &a, const double *val0, const double *dinv0, double *sc, int l_hi, int l_lo,
-                          const double *r_l0, double *out, int l0, int start, int stride, Sync sync) {
+                          const double *r_l0, double *out, int l0, int start, int stride, Sync sync,
+                          double *acc = nullptr) {
     const int L = a.g.L;
     for (int l = l_hi; l >= l_lo; --l) {
         const Lv A = level(a, val0, dinv0, l);
@@ -439,9 +456,18 @@ __device__ bool vcycle_up(const MGArgs &a, const double *val0, const double *din
         if (!sync()) return false;
         const double *rl = l == l0 ? r_l0 : sc + d.r;
         double *o = l == l0 ? out : sc + d.t;
-        for (int i = start; i < A.n; i += stride)
-            o[i] = e[i] + kSmooth * A.dv[i] * (rl[i] - csr_dot(A.ap, A.ac, A.av, e, i));
-        if (!sync()) return false;
+        if (acc && l == l_lo) {
+            for (int i = start; i < A.n; i += stride) {
+                const double oi = e[i] + kSmooth * A.dv[i] * (rl[i] - csr_dot(A.ap, A.ac, A.av, e, i));
+                o[i] = oi;
+                acc[0] += rl[i] * oi;
+                acc[1] += rl[i] * rl[i];
+            }
+        } else {
+            for (int i = start; i < A.n; i += stride)
+                o[i] = e[i] + kSmooth * A.dv[i] * (rl[i] - csr_dot(A.ap, A.ac, A.av, e, i));
+            if (!sync()) return false;
+        }
     }
     return true;
 }
@@ -530,28 +556,30 @@ __global__ void __launch_bounds__(1024) k_pcg_block_mg(MGArgs a) {
     }
 }
 
-// grid-wide V-cycle: large levels across the grid, small ones in block 0
+// grid-wide V-cycle: large levels across the grid, small ones in block 0.
+// The caller has set e_0 = w D^-1 r (fused pre-smoothing); with acc the last
+// phase accumulates (r.z, r.r) and the caller's reduction closes it.
 __device__ bool vcycle_grid(const MGArgs &a, const double *val0, const double *dinv0, double *sc, const double *r,
-                            double *z) {
+                            double *z, double *acc) {
     const int L = a.g.L;
     int lb = 0;                       // first level small enough for one CTA
     while (lb < L - 1 && a.g.lv[lb].n > a.g.small) ++lb;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     auto gsy = [&]() { return gsync(a.bar, a.status); };
     auto bs = []() { __syncthreads(); return true; };
-    if (!vcycle(a, val0, dinv0, sc, 0, lb, r, z, gid, gs, gsy)) return false;
+    if (!vcycle(a, val0, dinv0, sc, 0, lb, r, z, gid, gs, gsy, true)) return false;
     if (blockIdx.x == 0) {
         // levels lb..L-1 in this CTA; level lb's input sits in its r slot
         // (lb > 0 always: the finest level is above the small threshold)
         const double *rl = sc + a.g.lv[lb].r;
         double *ol = sc + a.g.lv[lb].t;
-        vcycle(a, val0, dinv0, sc, lb, L - 1, rl, ol, threadIdx.x, blockDim.x, bs);
+        vcycle(a, val0, dinv0, sc, lb, L - 1, rl, ol, threadIdx.x, blockDim.x, bs, true);
         coarse(a, sc, threadIdx.x, blockDim.x, bs);
         if (lb <= L - 2) vcycle_up(a, val0, dinv0, sc, L - 2, lb, rl, ol, lb, threadIdx.x, blockDim.x, bs);
         __threadfence();
     }
     if (!gsy()) return false;
-    return vcycle_up(a, val0, dinv0, sc, lb - 1, 0, r, z, 0, gid, gs, gsy);
+    return vcycle_up(a, val0, dinv0, sc, lb - 1, 0, r, z, 0, gid, gs, gsy, acc);
 }
 
 // Mode B with the multigrid preconditioner: cooperative grid, samples in turn
@@ -566,10 +594,12 @@ __global__ void __launch_bounds__(512, 2) k_pcg_grid_mg(MGArgs a) {
         double *x = a.x + (size_t)s * nf, *r = a.r + (size_t)s * nf, *p = a.p + (size_t)s * nf;
         double *q = a.q + (size_t)s * nf, *z = a.z + (size_t)s * nf;
         double *sc = a.g.scratch + (size_t)s * a.g.per_sample;
+        double *e0 = sc + a.g.lv[0].e;             // pre-smoothing of the V-cycle, fused below
         double v2[2] = {0.0, 0.0};
         for (int i = gid; i < nf; i += gs) {
             const double ri = b[i] - csr_dot(a.ptr, a.col, val, x, i);
             r[i] = ri;
+            e0[i] = kSmooth * dinv[i] * ri;
             v2[0] += ri * ri;
             v2[1] += b[i] * b[i];
         }
@@ -579,7 +609,7 @@ __global__ void __launch_bounds__(512, 2) k_pcg_grid_mg(MGArgs a) {
         int it = 0;
         double rz = 0.0;
         if (rr > tol2) {
-            if (!vcycle_grid(a, val, dinv, sc, r, z)) return;
+            if (!vcycle_grid(a, val, dinv, sc, r, z, nullptr)) return;
             double v1[1] = {0.0};
             for (int i = gid; i < nf; i += gs) { p[i] = z[i]; v1[0] += r[i] * z[i]; }
             if (!gsum<1>(v1, sh, redB, a.bar, a.status)) return;
@@ -596,12 +626,13 @@ __global__ void __launch_bounds__(512, 2) k_pcg_grid_mg(MGArgs a) {
             const double alpha = rz / v1[0];
             for (int i = gid; i < nf; i += gs) {
                 x[i] += alpha * p[i];
-                r[i] -= alpha * q[i];
+                const double ri = r[i] - alpha * q[i];
+                r[i] = ri;
+                e0[i] = kSmooth * dinv[i] * ri;
             }
-            if (!gsync(a.bar, a.status)) return;          // r complete
-            if (!vcycle_grid(a, val, dinv, sc, r, z)) return;
+            if (!gsync(a.bar, a.status)) return;          // r, e0 complete
             double w2[2] = {0.0, 0.0};
-            for (int i = gid; i < nf; i += gs) { w2[0] += r[i] * z[i]; w2[1] += r[i] * r[i]; }
+            if (!vcycle_grid(a, val, dinv, sc, r, z, w2)) return;
             if (!gsum<2>(w2, sh, redB, a.bar, a.status)) return;
             const double beta = w2[0] / rz;
             rz = w2[0];
