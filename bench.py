@@ -366,6 +366,41 @@ def krylov_leg(g, p, stream, be, q=20, oracle=True):
     return out
 
 
+def large_leg(p, stream):
+    """The 2048 x 2048 full chip (4,096 stripes of 20,471 stress nodes,
+    83.8 M nodes; 4.19 M IR nodes), one sample, FP32: load time, workspace
+    and one graph-captured TTF run of 64 x 256 steps."""
+    import torch
+    import ems_synth as es
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300.engine import Engine
+    g = es.grid.large_grid(n_samples=0)
+    t0 = time.perf_counter()
+    eng = Engine(p, g, precision=EMS_F32, max_voids=32)
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t0
+    init = eng.state_export()
+    eng.ttf()                                        # warm-up (captures the graph)
+    torch.cuda.synchronize()
+    eng.state_import(init)
+    a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    r = eng.ttf()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t = a0.elapsed_time(a1)
+    out = {"workload": "2048x2048-stripe two-layer mesh at 5 um: 4,096 trees x 20,471 stress nodes (83.8 M), "
+                       "4.19 M IR nodes, 5 % lognormal sinks, 330 K + 8 hotspots; one sample, FP32; "
+                       "64 aging steps x 256 BE steps",
+           "stress_nodes": eng.n_stress, "workspace_gb": round(eng.ws_bytes / 1e9, 2), "load_s": round(t_load, 1),
+           "ttf_wall_ms": round(t, 1), "node_steps_per_s": r["node_steps"] / (t / 1e3),
+           "stress_ms": round(r["stress_ms"], 1), "ir_ms": round(r["ir_ms"], 1),
+           "ir_iterations": r["ir_iterations"], "ttf_s": float(r["ttf"][0]), "drop0": float(r["drop0"][0]),
+           "final_drop": float(r["final_drop"][0]), "voids": int(r["n_voids"][0]), "graph": r["graph"]}
+    eng.close()
+    return out
+
+
 def cpu_baseline(g, p, n_outer):
     """The CPU oracle, as it stands, on a bounded sample of the same workload:
     the full grid (all 512 trees) for n_outer aging steps."""
@@ -423,6 +458,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--krylov", action="store_true", help="also time the Krylov reduced model (slow oracle leg)")
+    ap.add_argument("--large-only", action="store_true",
+                    help="time only the 2048 x 2048 full chip (one sample); prints its own JSON line")
     ap.add_argument("--krylov-only", action="store_true",
                     help="time only the Krylov TTF run and its BE reference (profiling); prints its own JSON line")
     ap.add_argument("--surrogate-only", action="store_true",
@@ -434,7 +471,11 @@ def main():
     else:
         import __graft_entry__ as ge
         ge.build()
-        if args.krylov_only:
+        if args.large_only:
+            import torch
+            import ems_synth as es
+            print(json.dumps({"large": large_leg(es.default_params(), torch.cuda.current_stream())}))
+        elif args.krylov_only:
             import torch
             import ems_synth as es
             from paper_2604_10743_gb300 import EMS_F32

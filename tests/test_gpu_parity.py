@@ -118,6 +118,29 @@ def test_tiny_full_ttf_fp32():
     eng.close()
 
 
+def test_long_fp32_chains_full_chip_length():
+    """FP32 stripes as long as the 2048 x 2048 chip's (20,469 stress nodes):
+    past the register-resident kernel's reach, so they take the L2-streaming
+    chunk kernel (64 nodes per thread); four aging steps against the oracle."""
+    from paper_2604_10743_gb300 import EMS_F32
+    g = es.stripe_mesh(8, 20e-6)
+    g["seg_cells"][:] = 2924
+    t = es.tiny_grid()
+    g["pad_node"], g["pad_V"], g["sink_node"], g["sink_I"] = t["pad_node"], t["pad_V"], t["sink_node"], t["sink_I"]
+    g["thermal"] = es.hotspot_raster(np.random.default_rng(4), 140e-6, 2, 360.0, 20.0, 40.0, 0.2, nx=33, ny=33)
+    p = es.default_params(n_outer=4, n_inner=64)
+    eng = _engine(p, g, precision=EMS_F32)
+    assert eng.n_stress == 16 * (7 * 2924 + 1)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True, n_threads=8)
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+    gpu, ora, _ = _void_sets(eng, ref)
+    if ref["margin"].min() >= 1e-3:
+        assert gpu == ora
+    assert abs(r["final_drop"][0] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+    eng.close()
+
+
 @pytest.mark.parametrize("kind", ["T", "comb", "star", "chain"])
 def test_branched_trees_with_voids(kind):
     g = es.tree_grid(kind, cells=12, seed=5, I_sink=6e-3)
