@@ -350,6 +350,43 @@ def test_krylov_graph_run_equals_host_loop():
     a.close(); b.close()
 
 
+def test_krylov_mc_samples_mixed_with_be():
+    """Three Monte Carlo samples of the uneven 8 x 8 grid (stripes of 43-883
+    nodes; at q = 20 the four stripes under n = 3q stay on BE within the same
+    aging steps): every sample against the oracle's Krylov run of it."""
+    from paper_2604_10743_gb300 import EMS_KRYLOV
+    from oracle import krylov as K
+    g = es.mc_grid(n_samples=3)
+    p = es.default_params(krylov_q=20, n_outer=16)
+    eng = _engine(p, g, method=EMS_KRYLOV)
+    r = eng.ttf()
+    sig = eng.sigma()
+    for s in range(3):
+        ref = F.run_ttf(g, p, sample=s, keep_state=True, stepper=K.KrylovStepper(q=20))
+        assert _relerr(sig[s], ref["state"].sigma) < 1e-5, s
+        gpu, ora, _ = _void_sets(eng, ref, sample=s)
+        assert gpu == ora, s
+        assert abs(r["final_drop"][s] - ref["final_drop"]) <= 1e-6 * ref["final_drop"], s
+    eng.close()
+
+
+def test_krylov_zero_forcing_falls_back_to_be():
+    """No sink current: the starting block is zero, there is nothing to
+    reduce, every tree is handed to backward Euler and the stress stays 0."""
+    from paper_2604_10743_gb300 import EMS_KRYLOV
+    g = dict(es.tiny_grid())
+    g["sink_I"] = np.zeros_like(g["sink_I"])
+    p = es.default_params(krylov_q=10, n_outer=2)
+    eng = _engine(p, g, method=EMS_KRYLOV)
+    eng.ir_solve()
+    nr, nf = eng.krylov_reduce(10, 1.0)
+    assert nr == 0 and nf == 16
+    r = eng.ttf()
+    assert np.all(eng.sigma() == 0.0)
+    assert r["n_voids"][0] == 0 and math.isinf(r["ttf"][0])
+    eng.close()
+
+
 def test_krylov_reduce_counts():
     from paper_2604_10743_gb300 import EMS_KRYLOV
     g = es.tiny_grid()
