@@ -118,6 +118,24 @@ def test_tiny_full_ttf_fp32():
     eng.close()
 
 
+def test_fp32_register_kernel_16_nodes_per_thread():
+    """128 x 128 grid (256 stripes of 2,541 nodes): FP32 chains past 2,048
+    nodes take the register-resident kernel with 16 nodes per thread; three
+    aging steps with the thermal map against the oracle."""
+    from paper_2604_10743_gb300 import EMS_F32
+    g = es.mid_grid(N=128)
+    p = es.default_params(n_outer=3, n_inner=128)
+    eng = _engine(p, g, precision=EMS_F32)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True, n_threads=8)
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+    gpu, ora, _ = _void_sets(eng, ref)
+    if ref["margin"].min() >= 1e-3:
+        assert gpu == ora
+    assert abs(r["final_drop"][0] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+    eng.close()
+
+
 def test_long_fp32_chains_full_chip_length():
     """FP32 stripes as long as the 2048 x 2048 chip's (20,469 stress nodes):
     past the register-resident kernel's reach, so they take the L2-streaming
