@@ -401,6 +401,72 @@ def large_leg(p, stream):
     return out
 
 
+def schedule_leg(p, stream, n_train=24, n_valid=3, test_seed=3000, N=64, S=32):
+    """What the learned part buys: the surrogate trained on the plain
+    solver's records of n_train seeded N x N grids (S Monte Carlo samples
+    each), its skip bound validated end to end on n_valid more, then the
+    S-sample TTF run of an unseen grid with and without the step schedule:
+    wall time, executed node-steps and the largest TTF / final-drop error."""
+    import numpy as np
+    import torch
+    import ems_synth as es
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300 import surrogate as sg
+    from paper_2604_10743_gb300.engine import Engine
+
+    def grid(seed):
+        g = es.grid.surrogate_grid(seed=seed, N=N, n_samples=S)
+        return sg.scale_to_drop(g, p, np.random.default_rng(seed + 7).uniform(0.07, 0.095))
+
+    t0 = time.perf_counter()
+    xs, ts = [], []
+    for seed in range(1000, 1000 + n_train):
+        x, t = sg.generate_records(grid(seed), p)
+        xs.append(x); ts.append(t)
+    X, T = torch.cat(xs), torch.cat(ts)
+    m = sg.Mlp(n_hidden=4, seed=0)
+    m.set_norm(*sg.fit_norm(X, T))
+    losses = m.train(X, T, batch=1024, epochs=30, lr=1e-3, seed=1)
+    bound, _ = sg.validate_bound(m, [grid(2000 + k) for k in range(n_valid)], p, coarsen=16, guard=0.8,
+                                 candidates=(-0.3, 0.0, 0.3, 0.6, 1.0))
+    t_prep = time.perf_counter() - t0
+    g = grid(test_seed)
+
+    def run(scheduled):
+        eng = Engine(p, g, precision=EMS_F32, max_voids=32)
+        init = eng.state_export()
+        ms, r = [], None
+        for rep in range(3):
+            eng.state_import(init)
+            eng.ir_solve()
+            n = None
+            if scheduled:
+                n, _ = eng.schedule(m, bound, 16, 0.8)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            r = eng.ttf()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                ms.append(a0.elapsed_time(a1))
+        eng.close()
+        return min(ms), r, n
+
+    t_plain, r_plain, _ = run(False)
+    t_sched, r_sched, n_coarse = run(True)
+    return {"workload": "%d x %d stripes at 10 um, %d Monte Carlo samples, unseen test grid (seed %d); network "
+                        "trained on %d grids, bound validated on %d" % (N, N, S, test_seed, n_train, n_valid),
+            "records": int(X.shape[0]), "final_loss_ratio": float(losses[-1] / losses[0]),
+            "bound": bound, "prep_s": round(t_prep, 1),
+            "coarse_trees_frac": float(np.asarray(n_coarse.cpu() if hasattr(n_coarse, "cpu") else n_coarse).sum())
+                                 / (S * 2 * N),
+            "plain_ttf_ms": round(t_plain, 2), "scheduled_ttf_ms": round(t_sched, 2),
+            "speedup": round(t_plain / t_sched, 3),
+            "node_steps_executed_ratio": r_sched["node_steps_executed"] / r_plain["node_steps_executed"],
+            "max_rel_err_ttf_or_final_drop": sg.result_error(r_plain, r_sched)}
+
+
 def cpu_baseline(g, p, n_outer):
     """The CPU oracle, as it stands, on a bounded sample of the same workload:
     the full grid (all 512 trees) for n_outer aging steps."""
@@ -458,6 +524,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--krylov", action="store_true", help="also time the Krylov reduced model (slow oracle leg)")
+    ap.add_argument("--schedule-only", action="store_true",
+                    help="train the surrogate and time a Monte Carlo TTF run with and without its step schedule")
     ap.add_argument("--large-only", action="store_true",
                     help="time only the 2048 x 2048 full chip (one sample); prints its own JSON line")
     ap.add_argument("--krylov-only", action="store_true",
@@ -471,7 +539,11 @@ def main():
     else:
         import __graft_entry__ as ge
         ge.build()
-        if args.large_only:
+        if args.schedule_only:
+            import torch
+            import ems_synth as es
+            print(json.dumps({"surrogate_schedule": schedule_leg(es.default_params(), torch.cuda.current_stream())}))
+        elif args.large_only:
             import torch
             import ems_synth as es
             print(json.dumps({"large": large_leg(es.default_params(), torch.cuda.current_stream())}))
