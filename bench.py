@@ -38,6 +38,22 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(ms, dist, device):
+    """The step time every rank reports is the slowest rank's (replicas: each
+    rank times its own copy of the workload; one all-reduce on the timing,
+    none on the data path)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(node_steps_per_step, steps, world, ms):
+    """Whole-job throughput: the node-steps of all ranks over the slowest
+    rank's time (weak scaling: every rank runs the full workload)."""
+    return node_steps_per_step * steps * world / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons while the timed region runs."""
 
@@ -135,12 +151,10 @@ def run_mine(args):
     launches = eng.launch_count() - l0
     ms = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         dist.barrier()
     node_steps = res["node_steps"]
-    value = node_steps * args.steps * world / (ms / 1e3)
+    value = job_value(node_steps, args.steps, world, ms)
 
     # dominant kernel: the chain stress kernel; one launch advances every tree
     # by n_inner steps.  Algorithmic bytes per node-step: state in + out (2w)

@@ -237,8 +237,9 @@ typedef struct {
     double ttf_cov;       /* out: ttf_std / ttf_mean */
     double n_censored;    /* out: samples that never crossed (TTF = +inf) */
     double graph_launch;  /* out: 1 if the aging steps ran as one captured CUDA graph */
-    double node_steps_executed; /* out: stress node-steps the kernels ran (less than node_steps
-                                   under a surrogate step schedule or the Krylov method) */
+    double node_steps_executed; /* out: stress node-steps the kernels ran: less than node_steps
+                                   under a surrogate step schedule (coarse steps); the reduced
+                                   models count their steps as full-order ones */
 } ems_ttf_result;
 
 /*
