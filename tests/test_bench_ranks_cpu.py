@@ -60,3 +60,22 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
         steps, warmup, gpus = 1, 0, 2
     bench.run_reference(Args())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the bench contract's keys, on the same metric and workload
+    as the GPU arm."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
