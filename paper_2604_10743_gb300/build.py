@@ -41,7 +41,7 @@ def build(force=False, verbose=False, extra=()):
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(srcs))) as ex:
         objs = list(ex.map(comp, srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

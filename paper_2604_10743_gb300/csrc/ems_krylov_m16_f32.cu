@@ -1,0 +1,10 @@
+// ems_krylov_m16_f32.cu -- the reduced-model kernel for FP32 contexts with chunks
+// of 16 nodes per thread; see ems_krylov_kernels.cuh.
+#include "ems_krylov_kernels.cuh"
+
+namespace ems {
+template <>
+ems_status kr_launch<16, float>(ems_ctx *c, const Bucket &b, KrArgs<float> &a) {
+    return launch_kr<16, float>(c, b, a);
+}
+}  // namespace ems
