@@ -55,7 +55,7 @@ int orc_advance(int n_trees, const long *off, const int *par,
                 const double *leak, const double *sig_crit,
                 double *sigma, int *void_flag, double *void_vol, double *t_nuc,
                 double t0, double dt, int n_steps, double B_modulus,
-                double *margin, int n_threads)
+                double *margin, double *gap, int n_threads)
 {
     int total = 0;
     int t;
@@ -75,7 +75,7 @@ int orc_advance(int n_trees, const long *off, const int *par,
         double *d = (double *)malloc(sizeof(double) * (size_t)n);
         double *r = (double *)malloc(sizeof(double) * (size_t)n);
         double *prev = (double *)malloc(sizeof(double) * (size_t)n);
-        double mmin = INFINITY;
+        double mmin = INFINITY, gmin = INFINITY;
         int k, i;
         for (k = 0; k < n_steps; ++k) {
             memcpy(prev, s, sizeof(double) * (size_t)n);
@@ -86,18 +86,21 @@ int orc_advance(int n_trees, const long *off, const int *par,
             /* nucleation: argmax over non-void nodes, lowest index on ties */
             {
                 int arg = -1;
-                double best = -INFINITY;
+                double best = -INFINITY, second = -INFINITY;
                 for (i = 0; i < n; ++i) {
                     double m;
                     if (vf[i]) continue;
                     m = s[i] - sig_crit[b + i];
-                    if (m > best) { best = m; arg = i; }
+                    if (m > best) { second = best; best = m; arg = i; }
+                    else if (m > second) second = m;
                 }
                 if (arg >= 0) {
                     double rel = fabs(best) / sig_crit[b + arg];
                     if (rel < mmin) mmin = rel;
                     if (best >= 0.0) {
                         double m0 = prev[arg] - sig_crit[b + arg];
+                        double gp = (best - second) / sig_crit[b + arg];
+                        if (gp < gmin) gmin = gp;
                         double frac = (m0 < 0.0) ? (-m0) / (best - m0) : 0.0;
                         vf[arg] = 1;
                         vv[arg] = 0.0;
@@ -108,6 +111,7 @@ int orc_advance(int n_trees, const long *off, const int *par,
             }
         }
         if (margin) margin[t] = mmin;
+        if (gap) gap[t] = gmin;
         free(d); free(r); free(prev);
     }
     return total;

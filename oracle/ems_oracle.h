@@ -40,6 +40,11 @@ extern "C" {
  *   t_nuc          out, set at nodes that nucleate during this call
  *   margin         out per tree (may be NULL): min over steps of
  *                  |max_i (sigma_i - sig_crit_i)| / sig_crit at the argmax
+ *   gap            out per tree (may be NULL): min over the nucleations of
+ *                  the lead of the chosen node over the runner-up,
+ *                  (best - second) / sig_crit at the chosen node (+inf if
+ *                  none); small values mark node choices that rounding of
+ *                  the stress could change (test bookkeeping only)
  *   n_threads      OpenMP threads over trees (<= 0: library default)
  * Returns the number of voids nucleated.
  */
@@ -48,7 +53,7 @@ int orc_advance(int n_trees, const long *off, const int *par,
                 const double *leak, const double *sig_crit,
                 double *sigma, int *void_flag, double *void_vol, double *t_nuc,
                 double t0, double dt, int n_steps, double B_modulus,
-                double *margin, int n_threads);
+                double *margin, double *gap, int n_threads);
 
 /*
  * Steady-state stress of each tree with blocking ends and no voids

@@ -44,7 +44,7 @@ def lib():
         L.orc_advance.restype = ctypes.c_int
         L.orc_advance.argtypes = [ctypes.c_int, lp, ip, dp, dp, dp, dp, dp, dp, ip, dp, dp,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                  ctypes.c_double, dp, ctypes.c_int]
+                                  ctypes.c_double, dp, dp, ctypes.c_int]
         L.orc_steady.restype = None
         L.orc_steady.argtypes = [ctypes.c_int, lp, ip, dp, dp, ctypes.c_double, dp]
         _LIB = L
@@ -342,7 +342,7 @@ class StressState:
         return c
 
 
-def advance(tr, p, phys, f, st, t0, dt, n_steps, margin=None, n_threads=0):
+def advance(tr, p, phys, f, st, t0, dt, n_steps, margin=None, n_threads=0, gap=None):
     """n_steps backward-Euler steps of every tree; returns new void count."""
     L = lib()
     return L.orc_advance(
@@ -356,7 +356,8 @@ def advance(tr, p, phys, f, st, t0, dt, n_steps, margin=None, n_threads=0):
         _p(st.sigma, ctypes.c_double), _p(st.void, ctypes.c_int),
         _p(st.vol, ctypes.c_double), _p(st.t_nuc, ctypes.c_double),
         float(t0), float(dt), int(n_steps), float(p["B_modulus"]),
-        None if margin is None else _p(margin, ctypes.c_double), int(n_threads))
+        None if margin is None else _p(margin, ctypes.c_double),
+        None if gap is None else _p(gap, ctypes.c_double), int(n_threads))
 
 
 def assign_void_segments(tr, st, j_seg, new_nodes):
@@ -427,17 +428,20 @@ def run_ttf(grid, p, sample=None, screen_first=False, record=False, n_threads=0,
     if screen_first:
         mortal, _, _ = screen(tr, p, phys, face_G(tr, p, phys, j))
     margin = np.full(tr["n_trees"], np.inf)
+    gap = np.full(tr["n_trees"], np.inf)
     node_steps = 0
     for k in range(n_out):
         G = face_G(tr, p, phys, j)
         f = forcing(tr, phys, G)
         before = st.void.copy()
         mk = np.zeros(tr["n_trees"])
+        gk = np.full(tr["n_trees"], np.inf)
         if stepper is None:
-            advance(tr, p, phys, f, st, k * dto, dti, p["n_inner"], margin=mk, n_threads=n_threads)
+            advance(tr, p, phys, f, st, k * dto, dti, p["n_inner"], margin=mk, n_threads=n_threads, gap=gk)
         else:
             stepper(tr, p, phys, f, st, k * dto, dti, p["n_inner"], margin=mk)
         margin = np.minimum(margin, mk)
+        gap = np.minimum(gap, gk)
         node_steps += tr["n_nodes"] * p["n_inner"]
         new = np.nonzero(st.void & ~before)[0]
         assign_void_segments(tr, st, j, new)
@@ -450,7 +454,7 @@ def run_ttf(grid, p, sample=None, screen_first=False, record=False, n_threads=0,
         if math.isinf(ttf) and drops[-2] < thr <= drops[-1]:
             ttf = crossing_time(k * dto, drops[-2], drops[-1], dto, thr)
     res = dict(ttf=ttf, drop0=drops[0], final_drop=drops[-1], drops=np.array(drops),
-               n_voids=int(st.void.sum()), margin=margin, node_steps=node_steps,
+               n_voids=int(st.void.sum()), margin=margin, gap=gap, node_steps=node_steps,
                mortal=mortal)
     tn = np.full(tr["n_trees"], np.inf)
     for t in range(tr["n_trees"]):

@@ -938,6 +938,13 @@ __device__ void tree_factor(const ChainArgs<R> &a, double dt, int n, int64_t cb,
         a.uu[ps + i] = (R)e;
     }
     for (int i = 0; i < n; ++i) a.pinv[ps + i] = 1.0 / a.pinv[ps + i];
+    if (sizeof(R) == 4) {
+        // increment form: dt g of the face to the parent and dt leak at a void
+        for (int i = 0; i < n; ++i) {
+            a.dtg[ps + i] = i > 0 ? (R)(dt * a.g[cs + i]) : R(0);
+            a.dtl[ps + i] = isinf(a.thr[cs + i]) ? (R)(dt * a.leak[cs + i]) : R(0);
+        }
+    }
 }
 
 template <typename R>
@@ -975,15 +982,39 @@ __global__ void k_tree(ChainArgs<R> a) {
     int step = 0;
     for (; step < n_steps; ++step) {
         R *r = a.beta + ps, *x = a.sig + ps;
-        for (int i = 0; i < n; ++i) r[i] = (R)(a.V[cb + i] * (double)x[i] + dt * a.f[cs + i]);
-        for (int i = n - 1; i >= 1; --i) {
-            const int q = (int)(a.gpar[cb + i] - cb);
-            r[q] -= a.gam[ps + i] * r[i];
-        }
-        x[0] = (R)((double)r[0] * a.pinv[ps]);
-        for (int i = 1; i < n; ++i) {
-            const int q = (int)(a.gpar[cb + i] - cb);
-            x[i] = (R)(((double)r[i] - (double)a.uu[ps + i] * (double)x[q]) * a.pinv[ps + i]);
+        if constexpr (sizeof(R) == 4) {
+            // increment form (C - dt A) d = dt (A s + f), s += d: the residual
+            // from face fluxes (each face's flux added to one end and taken
+            // from the other), so the rounding of the FP32 factors touches
+            // only the increment and the conserved slow modes stay exact
+            for (int i = 0; i < n; ++i) r[i] = (R)(dt * a.f[cs + i]) - a.dtl[ps + i] * x[i];
+            for (int i = 1; i < n; ++i) {
+                const int q = (int)(a.gpar[cb + i] - cb);
+                const R fl = a.dtg[ps + i] * (x[q] - x[i]);
+                r[i] += fl;
+                r[q] -= fl;
+            }
+            for (int i = n - 1; i >= 1; --i) {
+                const int q = (int)(a.gpar[cb + i] - cb);
+                r[q] -= a.gam[ps + i] * r[i];
+            }
+            r[0] = (R)((double)r[0] * a.pinv[ps]);
+            for (int i = 1; i < n; ++i) {
+                const int q = (int)(a.gpar[cb + i] - cb);
+                r[i] = (R)(((double)r[i] - (double)a.uu[ps + i] * (double)r[q]) * a.pinv[ps + i]);
+            }
+            for (int i = 0; i < n; ++i) x[i] += r[i];
+        } else {
+            for (int i = 0; i < n; ++i) r[i] = (R)(a.V[cb + i] * (double)x[i] + dt * a.f[cs + i]);
+            for (int i = n - 1; i >= 1; --i) {
+                const int q = (int)(a.gpar[cb + i] - cb);
+                r[q] -= a.gam[ps + i] * r[i];
+            }
+            x[0] = (R)((double)r[0] * a.pinv[ps]);
+            for (int i = 1; i < n; ++i) {
+                const int q = (int)(a.gpar[cb + i] - cb);
+                x[i] = (R)(((double)r[i] - (double)a.uu[ps + i] * (double)x[q]) * a.pinv[ps + i]);
+            }
         }
         for (int q = 0; q < nv; ++q) {
             const int64_t e = st * a.maxv + q;

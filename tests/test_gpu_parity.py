@@ -42,6 +42,42 @@ def _void_sets(eng, ref, sample=0):
     return gpu, ora, v
 
 
+GAP32 = 1e-3      # node choices whose lead over the runner-up is below this (relative
+                  # to sigma_crit) may differ under FP32 rounding of the stress
+
+
+def _f32_voids(eng, ref, sample=0):
+    """FP32 void check: per tree, the (node, segment) pairs must equal the
+    oracle's unless one of the tree's nucleations chose its node by a lead
+    under GAP32 over the runner-up (ref["gap"]).  Returns (trees compared,
+    voids compared)."""
+    v = eng.voids()
+    m = v["sample"] == sample
+    off = np.asarray(ref["trees"]["off"])
+    gt = np.searchsorted(off, v["node"][m], side="right") - 1
+    ot = np.searchsorted(off, ref["void_nodes"], side="right") - 1
+    n_trees = n_voids = 0
+    for t in range(len(off) - 1):
+        if ref["gap"][t] < GAP32:
+            continue
+        gpu = sorted(zip(v["node"][m][gt == t].tolist(), v["seg"][m][gt == t].tolist()))
+        ora = sorted(zip(ref["void_nodes"][ot == t].tolist(), ref["void_seg"][ot == t].tolist()))
+        assert gpu == ora, (sample, t)
+        n_trees += 1
+        n_voids += len(ora)
+    return n_trees, n_voids
+
+
+def _metric_close(r, ref, s=0, tol=None):
+    """TTF (or censoring) and final IR drop within the 0.05 % bar."""
+    tol = TTF_TOL if tol is None else tol
+    assert abs(r["final_drop"][s] - ref["final_drop"]) <= tol * ref["final_drop"], s
+    if math.isfinite(ref["ttf"]):
+        assert abs(r["ttf"][s] - ref["ttf"]) <= tol * ref["ttf"], s
+    else:
+        assert math.isinf(r["ttf"][s]), s
+
+
 def test_ir_solve_tiny_and_grids():
     # 60 unknowns (one CTA, Jacobi), 4,080 (one CTA, multigrid), 65,472
     # (cooperative grid, multigrid), and 65,472 with the Jacobi-only option
@@ -108,13 +144,9 @@ def test_tiny_full_ttf_fp32():
     r = eng.ttf()
     ref = F.run_ttf(g, p, keep_state=True)
     assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
-    gpu, ora, _ = _void_sets(eng, ref)
-    ambiguous = ref["margin"].min() < 1e-3
-    if not ambiguous:
-        assert gpu == ora
-    assert abs(r["final_drop"][0] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
-    if math.isfinite(ref["ttf"]):
-        assert abs(r["ttf"][0] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
+    nt, nv = _f32_voids(eng, ref)
+    assert nt >= 12 and nv >= 10
+    _metric_close(r, ref)
     eng.close()
 
 
@@ -129,10 +161,9 @@ def test_fp32_register_kernel_16_nodes_per_thread():
     r = eng.ttf()
     ref = F.run_ttf(g, p, keep_state=True, n_threads=8)
     assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
-    gpu, ora, _ = _void_sets(eng, ref)
-    if ref["margin"].min() >= 1e-3:
-        assert gpu == ora
-    assert abs(r["final_drop"][0] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+    nt, _ = _f32_voids(eng, ref)
+    assert nt >= 200
+    _metric_close(r, ref)
     eng.close()
 
 
@@ -152,24 +183,34 @@ def test_long_fp32_chains_full_chip_length():
     r = eng.ttf()
     ref = F.run_ttf(g, p, keep_state=True, n_threads=8)
     assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
-    gpu, ora, _ = _void_sets(eng, ref)
-    if ref["margin"].min() >= 1e-3:
-        assert gpu == ora
-    assert abs(r["final_drop"][0] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
+    nt, _ = _f32_voids(eng, ref)
+    assert nt >= 12
+    _metric_close(r, ref)
     eng.close()
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("kind", ["T", "comb", "star", "chain"])
-def test_branched_trees_with_voids(kind):
+def test_branched_trees_with_voids(kind, prec):
+    """Branched trees (leaf-to-root elimination; the FP32 path solves for
+    the increment) with voids, against the oracle."""
+    from paper_2604_10743_gb300 import EMS_F32, EMS_F64
     g = es.tree_grid(kind, cells=12, seed=5, I_sink=6e-3)
     p = es.default_params(n_outer=8, n_inner=64, sigma_crit=150e6)
-    eng = _engine(p, g)
+    eng = _engine(p, g, precision=EMS_F32 if prec == "f32" else EMS_F64)
     r = eng.ttf()
     ref = F.run_ttf(g, p, keep_state=True)
-    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
-    gpu, ora, _ = _void_sets(eng, ref)
-    assert gpu == ora
-    assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    assert ref["n_voids"] >= 1
+    if prec == "f64":
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+        gpu, ora, _ = _void_sets(eng, ref)
+        assert gpu == ora
+        assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    else:
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+        nt, nv = _f32_voids(eng, ref)
+        assert nt == 1 and nv == ref["n_voids"]
+        _metric_close(r, ref)
     eng.close()
 
 
@@ -222,6 +263,48 @@ def test_mid_grid_one_aging_step_fp64():
     gpu, ora, _ = _void_sets(eng, ref)
     assert gpu == ora
     assert abs(r["final_drop"][0] - ref["final_drop"]) < 1e-9
+    eng.close()
+
+
+_MID_REF = {}
+
+
+def _mid_ref():
+    """The oracle's full run (64 aging steps x 256 BE steps) of the 256 x 256
+    workload, computed once per session on all host cores."""
+    if not _MID_REF:
+        import os
+        g = es.mid_grid()
+        g["trees"] = F.build_trees(g)
+        p = es.default_params()
+        _MID_REF["g"], _MID_REF["p"] = g, p
+        _MID_REF["ref"] = F.run_ttf(g, p, keep_state=True, n_threads=os.cpu_count() or 0)
+    return _MID_REF["g"], _MID_REF["p"], _MID_REF["ref"]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mid_grid_full_run(prec):
+    """The 256 x 256 workload (512 stripes x 5,101 nodes, hotspot map) over
+    the whole horizon, FP64 and FP32 (the register-resident increment-form
+    kernel with 16 nodes per thread), against the oracle's full run: stress
+    at every node, the voids, the drop after every aging step, final drop."""
+    from paper_2604_10743_gb300 import EMS_F32, EMS_F64
+    g, p, ref = _mid_ref()
+    eng = _engine(p, g, precision=EMS_F32 if prec == "f32" else EMS_F64, max_voids=32)
+    r = eng.ttf()
+    assert r["graph"]
+    assert ref["n_voids"] >= 50
+    if prec == "f64":
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+        gpu, ora, _ = _void_sets(eng, ref)
+        assert gpu == ora
+        assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    else:
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+        nt, nv = _f32_voids(eng, ref)
+        assert nt >= 500 and nv >= 40
+        assert np.all(np.abs(r["drops"][0] - ref["drops"]) <= TTF_TOL * ref["drops"])
+    _metric_close(r, ref)
     eng.close()
 
 
@@ -447,14 +530,16 @@ def test_monte_carlo_1024_samples():
         assert abs(r["ttf_std"] - unc.std(ddof=1)) <= 1e-9 * unc.std(ddof=1)
     sig = eng.sigma()
     rng = np.random.default_rng(0)
-    for s in rng.choice(1024, size=6, replace=False):
+    g["trees"] = F.build_trees(g)
+    n_finite = n_trees = 0
+    for s in rng.choice(1024, size=10, replace=False):
         ref = F.run_ttf(g, p, sample=int(s), keep_state=True)
         assert _relerr(sig[s], ref["state"].sigma) < TOL32
-        amb = ref["margin"].min() < 1e-3
-        gpu, ora, _ = _void_sets(eng, ref, sample=int(s))
-        if not amb:
-            assert gpu == ora
-            assert abs(r["final_drop"][s] - ref["final_drop"]) <= TTF_TOL * ref["final_drop"]
-            if math.isfinite(ref["ttf"]):
-                assert abs(ttf[s] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
+        nt, _ = _f32_voids(eng, ref, sample=int(s))
+        n_trees += nt
+        _metric_close(r, ref, s=int(s))
+        n_finite += math.isfinite(ref["ttf"])
+    # every sample's TTF and final drop compared; void sets on all but the
+    # trees with a near-tied node choice
+    assert n_finite >= 5 and n_trees >= 10 * 16 - 5
     eng.close()

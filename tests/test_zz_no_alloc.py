@@ -81,3 +81,34 @@ def test_noalloc_rejects_oversized_systems():
     one = ctypes.c_void_p(1)
     assert L.ems_ir_pcg_noalloc(16385, one, one, one, one, one, 1e-12, 10, None, None) == 1
     assert L.ems_ir_pcg_noalloc(0, one, one, one, one, one, 1e-12, 10, None, None) == 1
+
+
+def test_noalloc_iteration_cap_then_normal_call():
+    """A call stopped by its iteration cap reports EMS_E_NOCONV and the
+    iterations it ran (read back from the shared array's info slots); the
+    next call on the same array still converges to the context solve."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2604_10743_gb300 import _abi
+    from paper_2604_10743_gb300.engine import Engine
+    L = _abi.lib()
+    stream = torch.cuda.current_stream()
+    g = es.tiny_grid()
+    eng = Engine(es.default_params(), g)
+    u, _ = eng.ir_solve()
+    eng.close()
+    rp, col, val, rhs, free = _free_node_system(g)
+    dev = [torch.from_numpy(x).cuda() for x in (rp, col, val, rhs)]
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in dev]
+    x = torch.ones(free.size, dtype=torch.float64, device="cuda")
+    its = ctypes.c_int()
+    st = L.ems_ir_pcg_noalloc(int(free.size), *ptrs, ctypes.c_void_p(x.data_ptr()), 1e-13, 2,
+                              ctypes.byref(its), ctypes.c_void_p(stream.cuda_stream))
+    assert st == 5 and its.value == 2
+    x2 = torch.ones(free.size, dtype=torch.float64, device="cuda")
+    st = L.ems_ir_pcg_noalloc(int(free.size), *ptrs, ctypes.c_void_p(x2.data_ptr()), 1e-13, 20000,
+                              ctypes.byref(its), ctypes.c_void_p(stream.cuda_stream))
+    assert st == 0 and its.value > 2
+    assert np.abs(x2.cpu().numpy() - u[0][free]).max() < 1e-11
