@@ -79,6 +79,18 @@ typedef struct {
     int    ir_precond;     /* EMS_PC_AUTO: smoothed-aggregation multigrid V-cycle for systems of
                               >= 1,024 unknowns (hierarchy built once from the initial
                               resistances), Jacobi below; EMS_PC_JACOBI: Jacobi always */
+    int    window_samples; /* Monte Carlo memory layout (Sec. IV-F).  0 (or >= n_samples):
+                              every per-node coefficient array (kappa a, conductances, leak,
+                              thresholds, forcing, factors) and the IR work vectors are held
+                              for all samples at once.  W in 1..n_samples-1: only the
+                              per-sample state is held for all samples -- packed stress,
+                              resistances, node voltages, the kappa / sigma_crit factors per
+                              segment, voids -- and the per-node coefficients and IR vectors
+                              exist for W samples at a time: every call that steps, solves or
+                              reports per-node data walks the samples in windows of W and
+                              rebuilds the window's coefficients from the per-segment factors
+                              first.  Results are the same as with the full layout; the
+                              reduced models (EMS_KRYLOV / EMS_AUTO) need the full layout. */
 } ems_params;
 
 enum { EMS_PC_AUTO = 0, EMS_PC_JACOBI = 1 };       /* IR preconditioner */
@@ -110,8 +122,9 @@ typedef struct {
 
 typedef struct ems_ctx ems_ctx;
 
-/* Bytes of device workspace a context needs for this grid.  Returns 0 if
- * the descriptor is invalid. */
+/* Bytes of device workspace a context needs for this grid (with the Monte
+ * Carlo layout params->window_samples selects).  Returns 0 if the
+ * descriptor is invalid. */
 size_t ems_workspace_bytes(const ems_params *params, const ems_grid_desc *grid);
 
 /*
@@ -153,9 +166,11 @@ ems_status ems_set_thermal_map(ems_ctx *ctx, const double *T, int nx, int ny,
 
 /*
  * IR-drop solve (Sec. III-C, Eq. ir_drop_mna) for every sample with the
- * current resistances: PCG (Jacobi) on the conductance matrix of the
- * non-pad nodes, FP64, warm-started from the previous solution; then the
- * segment current densities j = (u_a - u_b) / (R W H).
+ * current resistances: preconditioned CG in FP64 on the conductance matrix of
+ * the non-pad nodes (params.ir_precond: a smoothed-aggregation multigrid
+ * V-cycle for systems of >= 1,024 unknowns by default, Jacobi below or on
+ * request), warm-started from the previous solution; then the segment
+ * current densities j = (u_a - u_b) / (R W H).
  *   u_out         optional host [S][n_nodes] node voltages
  *   max_drop_frac optional host [S]: max over nodes of (Vdd - u) / Vdd
  * EMS_E_NOCONV if a sample misses ir_rtol within ir_max_iter iterations.

@@ -33,7 +33,8 @@ class EmsParams(ctypes.Structure):
         ("ir_fail_frac", ctypes.c_double), ("Vdd", ctypes.c_double),
         ("precision", ctypes.c_int), ("method", ctypes.c_int), ("krylov_q", ctypes.c_int),
         ("krylov_eta", ctypes.c_double), ("ir_rtol", ctypes.c_double), ("ir_max_iter", ctypes.c_int),
-        ("max_voids_per_tree", ctypes.c_int), ("ir_precond", ctypes.c_int)]
+        ("max_voids_per_tree", ctypes.c_int), ("ir_precond", ctypes.c_int),
+        ("window_samples", ctypes.c_int)]
 
 
 class EmsGridDesc(ctypes.Structure):
@@ -157,7 +158,7 @@ class EmsError(RuntimeError):
 
 
 def make_params(p, precision=EMS_F64, method=EMS_BE, ir_rtol=1e-13, ir_max_iter=20000, max_voids=16,
-                ir_precond=0):
+                ir_precond=0, window=0):
     """ems_params from a parameter dict (ems_synth.default_params())."""
     e = EmsParams()
     for name, _ in EmsParams._fields_:
@@ -171,6 +172,7 @@ def make_params(p, precision=EMS_F64, method=EMS_BE, ir_rtol=1e-13, ir_max_iter=
     e.ir_max_iter = ir_max_iter
     e.max_voids_per_tree = max_voids
     e.ir_precond = ir_precond
+    e.window_samples = int(window)
     return e
 
 

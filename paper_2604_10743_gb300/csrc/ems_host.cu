@@ -17,6 +17,34 @@ ems_status fail(ems_ctx *c, ems_status s, const std::string &msg) {
     return s;
 }
 
+// Point the per-sample state arrays at samples [s0, s0 + ns); the per-node
+// coefficient arrays, currents and IR work vectors (window-sized) keep their
+// base: index 0 of a kernel's sample dimension is sample s0.
+void map_window(ems_ctx *c, int s0, int ns) {
+    Dev &d = c->d;
+    d = c->d_all;
+    const size_t nt = (size_t)c->n_trees, ns_ = (size_t)c->n_seg, nv = nt * (size_t)c->maxv;
+    auto off = [&](auto *&ptr, size_t stride) {
+        if (ptr) ptr += (size_t)s0 * stride;
+    };
+    off(d.R, ns_); off(d.j, ns_); off(d.R_prev, ns_); off(d.kfac, ns_); off(d.sfac, ns_);
+    off(d.u, (size_t)c->n_nodes);
+    off(d.drop, 1); off(d.ir_iters, 1); off(d.gttf, 1); off(d.gdrops, (size_t)c->prm.n_outer + 1);
+    d.sig = (char *)d.sig + (size_t)s0 * (size_t)c->P * elem_bytes(c);
+    off(d.v_count, nt); off(d.dirty, nt); off(d.mortal, nt); off(d.ssmax, nt);
+    off(d.kr_mode, nt); off(d.kdone, nt); off(d.sched, nt); off(d.fdt, nt);
+    off(d.v_node, nv); off(d.v_seg, nv); off(d.v_vol, nv); off(d.v_tnuc, nv);
+    off(d.feat, nt * EMS_MLP_FEATURES); off(d.pred, nt * EMS_MLP_OUTPUTS);
+    c->S = ns;
+    c->win_s0 = s0;
+}
+
+void map_all(ems_ctx *c) {
+    c->d = c->d_all;
+    c->S = c->S_all;
+    c->win_s0 = 0;
+}
+
 ems_status cuda_check(ems_ctx *c, cudaError_t e, const char *what) {
     cudaGetLastError();   // clear the error slot so later calls do not report it again
     return fail(c, EMS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -80,6 +108,9 @@ ems_status validate(ems_ctx *c, const ems_params *p, const ems_grid_desc *g) {
         return fail(c, EMS_E_INVAL, "method must be EMS_BE, EMS_KRYLOV or EMS_AUTO");
     if (p->method != EMS_BE && (p->krylov_q < 1 || p->krylov_q > 40 || !(p->krylov_eta > 0.0)))
         return fail(c, EMS_E_INVAL, "krylov_q must be 1..40 and krylov_eta > 0");
+    if (p->window_samples < 0) return fail(c, EMS_E_INVAL, "window_samples must be >= 0");
+    if (p->window_samples > 0 && p->window_samples < S && p->method != EMS_BE)
+        return fail(c, EMS_E_INVAL, "the reduced models need every sample's coefficients: window_samples 0");
     return EMS_OK;
 }
 
@@ -378,7 +409,8 @@ struct Plan {
     MGHost mg;
     std::vector<TreePack> pack;
     int64_t P = 0;
-    int S = 1;
+    int S = 1;      // samples whose state the context holds
+    int Sd = 1;     // samples whose per-node coefficients and IR vectors it holds at once
 };
 
 ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Plan &pl) {
@@ -390,6 +422,7 @@ ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Pl
         mg_build((int)pl.ir.node_of_free.size(), pl.ir.ptr, pl.ir.col, pl.ir.ent_ptr, pl.ir.ent_seg,
                  pl.ir.ent_diag, g->seg_R0, 1024, pl.mg);
     pl.S = g->n_samples > 0 ? g->n_samples : 1;
+    pl.Sd = (p->window_samples > 0 && p->window_samples < pl.S) ? p->window_samples : pl.S;
     pl.pack.resize(pl.tr.n_trees);
     int64_t P = 0;
     for (int t = 0; t < pl.tr.n_trees; ++t) {
@@ -407,7 +440,9 @@ ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Pl
 
 size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev &d) {
     Carver cv(base);
-    const int S = pl.S, ns = g->n_seg, nn = g->n_nodes, nf = (int)pl.ir.node_of_free.size();
+    // per-sample state: S samples; per-node coefficients, currents and IR
+    // work vectors: Sd samples (a window, or all of them)
+    const int S = pl.S, Sd = pl.Sd, ns = g->n_seg, nn = g->n_nodes, nf = (int)pl.ir.node_of_free.size();
     const int64_t nnz = (int64_t)pl.ir.col.size(), N = pl.tr.off.back(), P = pl.P;
     const int nt = pl.tr.n_trees;
     const int maxv = c ? c->prm.max_voids_per_tree : EMS_MAX_VOIDS;
@@ -422,15 +457,15 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.rhs_ptr = cv.take<int32_t>(nf + 1); d.rhs_seg = cv.take<int32_t>(pl.ir.rhs_seg.size() + 1);
     d.rhs_padV = cv.take<double>(pl.ir.rhs_padV.size() + 1);
     d.sink_of_free = cv.take<double>(nf);
-    d.csr_val = cv.take<double>((size_t)S * nnz);
-    d.ir_b = cv.take<double>((size_t)S * nf); d.ir_dinv = cv.take<double>((size_t)S * nf);
-    d.ir_x = cv.take<double>((size_t)S * nf); d.ir_r = cv.take<double>((size_t)S * nf);
-    d.ir_p = cv.take<double>((size_t)S * nf); d.ir_Ap = cv.take<double>((size_t)S * nf);
-    d.ir_z = cv.take<double>((size_t)S * nf);
-    d.val32 = cv.take<float>((size_t)S * nnz); d.dinv32 = cv.take<float>((size_t)S * nf);
-    d.r32 = cv.take<float>((size_t)S * nf); d.p32 = cv.take<float>((size_t)S * nf);
-    d.Ap32 = cv.take<float>((size_t)S * nf); d.z32 = cv.take<float>((size_t)S * nf);
-    d.d32 = cv.take<float>((size_t)S * nf);
+    d.csr_val = cv.take<double>((size_t)Sd * nnz);
+    d.ir_b = cv.take<double>((size_t)Sd * nf); d.ir_dinv = cv.take<double>((size_t)Sd * nf);
+    d.ir_x = cv.take<double>((size_t)Sd * nf); d.ir_r = cv.take<double>((size_t)Sd * nf);
+    d.ir_p = cv.take<double>((size_t)Sd * nf); d.ir_Ap = cv.take<double>((size_t)Sd * nf);
+    d.ir_z = cv.take<double>((size_t)Sd * nf);
+    d.val32 = cv.take<float>((size_t)Sd * nnz); d.dinv32 = cv.take<float>((size_t)Sd * nf);
+    d.r32 = cv.take<float>((size_t)Sd * nf); d.p32 = cv.take<float>((size_t)Sd * nf);
+    d.Ap32 = cv.take<float>((size_t)Sd * nf); d.z32 = cv.take<float>((size_t)Sd * nf);
+    d.d32 = cv.take<float>((size_t)Sd * nf);
     d.u = cv.take<double>((size_t)S * nn); d.pad_V_of_node = cv.take<double>(nn);
     d.drop = cv.take<double>(S);
     d.red = cv.take<double>(4096 + 8 * (size_t)S);
@@ -444,15 +479,15 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.face_dx = cv.take<double>(N); d.face_area = cv.take<double>(N);
     d.nx_ = cv.take<double>(N); d.ny_ = cv.take<double>(N);
     d.Tn = cv.take<double>(N); d.Mface = cv.take<double>(N); d.V = cv.take<double>(N);
-    d.kap_a = cv.take<double>((size_t)S * N); d.g = cv.take<double>((size_t)S * N);
-    d.leak = cv.take<double>((size_t)S * N); d.thr = cv.take<double>((size_t)S * N);
-    d.f = cv.take<double>((size_t)S * N); d.sig_ss = cv.take<double>((size_t)S * N);
+    d.kap_a = cv.take<double>((size_t)Sd * N); d.g = cv.take<double>((size_t)Sd * N);
+    d.leak = cv.take<double>((size_t)Sd * N); d.thr = cv.take<double>((size_t)Sd * N);
+    d.f = cv.take<double>((size_t)Sd * N); d.sig_ss = cv.take<double>((size_t)Sd * N);
     d.pbase = cv.take<int64_t>(nt); d.pT = cv.take<int32_t>(nt); d.pM = cv.take<int32_t>(nt);
-    d.sig = cv.take<char>((size_t)S * P * eb); d.alpha = cv.take<char>((size_t)S * P * eb);
-    d.beta = cv.take<char>((size_t)S * P * eb); d.gam = cv.take<char>((size_t)S * P * eb);
-    d.uu = cv.take<char>((size_t)S * P * eb); d.Pf = cv.take<char>((size_t)S * P * eb);
-    d.Pb = cv.take<char>((size_t)S * P * eb); d.pinv = cv.take<double>((size_t)S * P);
-    d.dtg = cv.take<char>((size_t)S * P * eb); d.dtl = cv.take<char>((size_t)S * P * eb);
+    d.sig = cv.take<char>((size_t)S * P * eb); d.alpha = cv.take<char>((size_t)Sd * P * eb);
+    d.beta = cv.take<char>((size_t)Sd * P * eb); d.gam = cv.take<char>((size_t)Sd * P * eb);
+    d.uu = cv.take<char>((size_t)Sd * P * eb); d.Pf = cv.take<char>((size_t)Sd * P * eb);
+    d.Pb = cv.take<char>((size_t)Sd * P * eb); d.pinv = cv.take<double>((size_t)Sd * P);
+    d.dtg = cv.take<char>((size_t)Sd * P * eb); d.dtl = cv.take<char>((size_t)Sd * P * eb);
     d.v_count = cv.take<int32_t>((size_t)S * nt);
     d.v_node = cv.take<int32_t>((size_t)S * nt * maxv); d.v_seg = cv.take<int32_t>((size_t)S * nt * maxv);
     d.v_vol = cv.take<double>((size_t)S * nt * maxv); d.v_tnuc = cv.take<double>((size_t)S * nt * maxv);
@@ -460,7 +495,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.status = cv.take<int32_t>(8); d.counters = cv.take<int32_t>(8);
     d.mortal = cv.take<uint8_t>((size_t)S * nt); d.ssmax = cv.take<double>((size_t)S * nt);
     d.kfac = cv.take<double>((size_t)S * ns); d.sfac = cv.take<double>((size_t)S * ns);
-    d.thr0 = cv.take<double>((size_t)S * N);
+    d.thr0 = cv.take<double>((size_t)Sd * N);
     d.R_prev = cv.take<double>((size_t)S * ns);
     d.raster = cv.take<double>(EMS_MAX_RASTER);
     d.kr_mode = cv.take<int32_t>((size_t)S * nt); d.kdone = cv.take<int32_t>((size_t)S * nt);
@@ -474,7 +509,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.pred = cv.take<float>((size_t)S * nt * EMS_MLP_OUTPUTS);
     d.mg_i = cv.take<int32_t>(pl.mg.ints.size() + 1);
     d.mg_d = cv.take<double>(pl.mg.dbls.size() + 1);
-    d.mg_sc = cv.take<double>((size_t)S * pl.mg.per_sample + 1);
+    d.mg_sc = cv.take<double>((size_t)Sd * pl.mg.per_sample + 1);
     d.sched = cv.take<int32_t>((size_t)S * nt);
     d.fdt = cv.take<double>((size_t)S * nt);
     d.work = cv.take<unsigned long long>(1);
@@ -578,7 +613,9 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     Dev &D = c->d;
     cudaStream_t st = c->stream;
     EMS_CUDA(c, cudaMemsetAsync(c->ws, 0, need - 256, st));
-    c->S = pl.S; c->n_nodes = g->n_nodes; c->n_seg = g->n_seg; c->n_pads = g->n_pads;
+    c->S = pl.S; c->S_all = pl.S; c->W = pl.Sd; c->win_s0 = 0;
+    c->d_all = c->d;
+    c->n_nodes = g->n_nodes; c->n_seg = g->n_seg; c->n_pads = g->n_pads;
     c->n_sinks = g->n_sinks; c->nf = (int)pl.ir.node_of_free.size(); c->nnz = (int64_t)pl.ir.col.size();
     c->N = pl.tr.off.back(); c->P = pl.P; c->n_trees = pl.tr.n_trees;
     c->maxv = c->prm.max_voids_per_tree;
@@ -588,13 +625,23 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     EMS_CUDA(c, up(D.seg_a, g->seg_a, ns, st)); EMS_CUDA(c, up(D.seg_b, g->seg_b, ns, st));
     EMS_CUDA(c, up(D.seg_R0, g->seg_R0, ns, st)); EMS_CUDA(c, up(D.seg_W, g->seg_W, ns, st));
     EMS_CUDA(c, up(D.seg_H, g->seg_H, ns, st));
-    for (int s = 0; s < S; ++s) {
-        EMS_CUDA(c, up(D.R + (size_t)s * ns, g->seg_R0, ns, st));
-        EMS_CUDA(c, up(D.R_prev + (size_t)s * ns, g->seg_R0, ns, st));
+    // per-sample copies of one host row: upload sample 0, replicate on the device
+    auto replicate = [&](double *dst, const double *row, size_t n) -> ems_status {
+        EMS_CUDA(c, up(dst, row, n, st));
+        for (int s = 1; s < S; ++s)
+            EMS_CUDA(c, cudaMemcpyAsync(dst + (size_t)s * n, dst, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return EMS_OK;
+    };
+    EMS_TRY(replicate(D.R, g->seg_R0, ns));
+    EMS_TRY(replicate(D.R_prev, g->seg_R0, ns));
+    {
+        std::vector<double> ones((g->kappa_factor && g->sigc_factor) ? 0 : (size_t)ns, 1.0);
+        if (g->kappa_factor) EMS_CUDA(c, up(D.kfac, g->kappa_factor, (size_t)S * ns, st));
+        else EMS_TRY(replicate(D.kfac, ones.data(), ns));
+        if (g->sigc_factor) EMS_CUDA(c, up(D.sfac, g->sigc_factor, (size_t)S * ns, st));
+        else EMS_TRY(replicate(D.sfac, ones.data(), ns));
+        EMS_CUDA(c, cudaStreamSynchronize(st));
     }
-    std::vector<double> ones((size_t)S * ns, 1.0);
-    EMS_CUDA(c, up(D.kfac, g->kappa_factor ? g->kappa_factor : ones.data(), (size_t)S * ns, st));
-    EMS_CUDA(c, up(D.sfac, g->sigc_factor ? g->sigc_factor : ones.data(), (size_t)S * ns, st));
     // IR
     const HostIR &ir = pl.ir;
     EMS_CUDA(c, up(D.ir_free_of_node, ir.free_of_node.data(), ir.free_of_node.size(), st));
@@ -628,12 +675,12 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
         double vm = 0.0;
         for (int i = 0; i < g->n_pads; ++i) vm += g->pad_V[i];
         vm /= g->n_pads;
-        std::vector<double> x0((size_t)S * c->nf, vm), u0((size_t)S * g->n_nodes);
-        for (int s = 0; s < S; ++s)
-            for (int i = 0; i < g->n_nodes; ++i)
-                u0[(size_t)s * g->n_nodes + i] = std::isnan(ir.padV_of_node[i]) ? vm : ir.padV_of_node[i];
-        EMS_CUDA(c, up(D.ir_x, x0.data(), x0.size(), st));
-        EMS_CUDA(c, up(D.u, u0.data(), u0.size(), st));
+        std::vector<double> x0((size_t)c->nf, vm), u0((size_t)g->n_nodes);
+        for (int i = 0; i < g->n_nodes; ++i) u0[i] = std::isnan(ir.padV_of_node[i]) ? vm : ir.padV_of_node[i];
+        // with windows the IR guess is gathered from u before every solve
+        if (!windowed(c)) EMS_TRY(replicate(D.ir_x, x0.data(), x0.size()));
+        EMS_TRY(replicate(D.u, u0.data(), u0.size()));
+        EMS_CUDA(c, cudaStreamSynchronize(st));
     }
     // trees
     HostTrees &tr = pl.tr;
@@ -737,11 +784,13 @@ extern "C" ems_status ems_get_resistance(ems_ctx *c, double *R) {
 extern "C" ems_status ems_get_sigma(ems_ctx *c, double *sigma) {
     if (!c || !sigma) return EMS_E_INVAL;
     if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
-    EMS_TRY(ems::pack_sigma(c, /*to_packed=*/false));   // packed -> canonical f (scratch)
-    EMS_CUDA(c, cudaMemcpyAsync(sigma, c->d.sig_ss, sizeof(double) * c->S * c->N,
-                                cudaMemcpyDeviceToHost, c->stream));
-    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
-    return EMS_OK;
+    return ems::each_window(c, [&](int s0, int ns) -> ems_status {
+        EMS_TRY(ems::pack_sigma(c, /*to_packed=*/false));   // packed -> canonical (scratch)
+        EMS_CUDA(c, cudaMemcpyAsync(sigma + (size_t)s0 * c->N, c->d.sig_ss, sizeof(double) * ns * c->N,
+                                    cudaMemcpyDeviceToHost, c->stream));
+        EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+        return EMS_OK;
+    });
 }
 
 extern "C" ems_status ems_get_voids(ems_ctx *c, int cap, int32_t *sample, int32_t *node, int32_t *seg,
@@ -813,7 +862,19 @@ extern "C" ems_status ems_state_export(ems_ctx *c, void *buf, size_t *bytes) {
     EMS_CUDA(c, dn(p, c->d.v_tnuc, st * mv * 8)); p += st * mv * 8;
     EMS_CUDA(c, dn(p, c->d.R, S * c->n_seg * 8)); p += S * c->n_seg * 8;
     EMS_CUDA(c, dn(p, c->d.u, S * c->n_nodes * 8)); p += S * c->n_nodes * 8;
-    EMS_CUDA(c, dn(p, c->d.ir_x, S * c->nf * 8)); p += S * c->nf * 8;
+    if (!windowed(c)) {
+        EMS_CUDA(c, dn(p, c->d.ir_x, S * c->nf * 8));
+    } else {
+        // windows: the IR guess is the free nodes' voltages
+        char *px = p;
+        EMS_TRY(each_window(c, [&](int s0, int ns) -> ems_status {
+            EMS_TRY(gather_x(c));
+            EMS_CUDA(c, dn(px + (size_t)s0 * c->nf * 8, c->d.ir_x, (size_t)ns * c->nf * 8));
+            EMS_CUDA(c, cudaStreamSynchronize(cs));
+            return EMS_OK;
+        }));
+    }
+    p += S * c->nf * 8;
     EMS_CUDA(c, cudaStreamSynchronize(cs));
     *bytes = need;
     return EMS_OK;
@@ -837,7 +898,8 @@ extern "C" ems_status ems_state_import(ems_ctx *c, const void *buf, size_t bytes
     auto upb = [&](void *dst, const void *src, size_t nb) {
         return cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, cs);
     };
-    EMS_CUDA(c, upb(c->d.sig_ss, p, S * N * 8)); p += S * N * 8;
+    const char *psig = p;
+    p += S * N * 8;
     EMS_CUDA(c, upb(c->d.v_count, p, st * 4)); p += st * 4;
     EMS_CUDA(c, upb(c->d.v_node, p, st * mv * 4)); p += st * mv * 4;
     EMS_CUDA(c, upb(c->d.v_seg, p, st * mv * 4)); p += st * mv * 4;
@@ -845,12 +907,19 @@ extern "C" ems_status ems_state_import(ems_ctx *c, const void *buf, size_t bytes
     EMS_CUDA(c, upb(c->d.v_tnuc, p, st * mv * 8)); p += st * mv * 8;
     EMS_CUDA(c, upb(c->d.R, p, S * c->n_seg * 8)); p += S * c->n_seg * 8;
     EMS_CUDA(c, upb(c->d.u, p, S * c->n_nodes * 8)); p += S * c->n_nodes * 8;
-    EMS_CUDA(c, upb(c->d.ir_x, p, S * c->nf * 8)); p += S * c->nf * 8;
+    if (!windowed(c)) EMS_CUDA(c, upb(c->d.ir_x, p, S * c->nf * 8));   // windows: gathered from u
+    p += S * c->nf * 8;
     c->t = h.t;
     c->have_u = true;
-    EMS_TRY(ems::node_physics(c));          // thresholds with the imported voids, all dirty
-    EMS_TRY(ems::pack_sigma(c, /*to_packed=*/true));
-    EMS_TRY(ems::ir_currents_and_drop(c));
     EMS_CUDA(c, cudaStreamSynchronize(cs));
-    return EMS_OK;
+    // stress through the canonical scratch, one window at a time; thresholds
+    // with the imported voids (every tree marked for a refactor)
+    return each_window(c, [&](int s0, int ns) -> ems_status {
+        EMS_CUDA(c, upb(c->d.sig_ss, psig + (size_t)s0 * N * 8, (size_t)ns * N * 8));
+        EMS_TRY(ems::node_physics(c));
+        EMS_TRY(ems::pack_sigma(c, /*to_packed=*/true));
+        EMS_TRY(ems::ir_currents_and_drop(c));
+        EMS_CUDA(c, cudaStreamSynchronize(cs));
+        return EMS_OK;
+    });
 }

@@ -188,6 +188,13 @@ struct Dev {
 
 struct ems_ctx {
     ems_params prm;
+    // Monte Carlo layout: S_all samples hold their state; the per-node
+    // coefficient arrays and IR work vectors hold W of them (W == S_all: the
+    // full layout).  Calls walk the samples in windows of W: S is the number
+    // mapped now, starting at win_s0, and d points the per-sample state
+    // arrays of d_all at that window.
+    int S_all = 1, W = 1, win_s0 = 0;
+    ems::Dev d_all{};
     cudaStream_t stream = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -248,6 +255,7 @@ void mg_build(int nf, const std::vector<int32_t> &ptr, const std::vector<int32_t
               const std::vector<int32_t> &ent_ptr, const std::vector<int32_t> &ent_seg,
               const std::vector<int8_t> &ent_diag, const double *R0, int min_rows, MGHost &h);
 ems_status ir_currents_and_drop(ems_ctx *c);
+ems_status currents(ems_ctx *c);
 ems_status check_status(ems_ctx *c);
 
 // stress (ems_stress.cu)
@@ -261,10 +269,35 @@ ems_status void_update(ems_ctx *c, int *n_changed);
 ems_status screen(ems_ctx *c);
 ems_status pack_sigma(ems_ctx *c, bool to_packed);
 ems_status init_sigma(ems_ctx *c);
+ems_status sample_physics(ems_ctx *c);     // kappa, conductances, leak, thresholds of the mapped samples
+
+// Monte Carlo windows (ems_host.cu)
+void map_window(ems_ctx *c, int s0, int ns);   // map samples [s0, s0 + ns) (ns <= W)
+void map_all(ems_ctx *c);                      // every sample; per-node arrays are window-sized
+ems_status gather_x(ems_ctx *c);               // IR initial guess of the mapped samples from u
+ems_status window_derive(ems_ctx *c);          // per-node coefficients of the mapped window
 
 // Krylov (ems_krylov.cu)
 ems_status krylov_advance(ems_ctx *c, double dt, int n_steps, int method, int *n_new);
 
+}  // namespace ems
+
+namespace ems {
+inline bool windowed(const ems_ctx *c) { return c->W < c->S_all; }
+
+// Run fn(s0, ns) once per window of samples with that window mapped (one
+// call over every sample with the full layout), then map every sample again.
+template <class F>
+ems_status each_window(ems_ctx *c, F &&fn) {
+    if (!windowed(c)) return fn(0, c->S_all);
+    ems_status st = EMS_OK;
+    for (int s0 = 0; s0 < c->S_all && st == EMS_OK; s0 += c->W) {
+        map_window(c, s0, c->S_all - s0 < c->W ? c->S_all - s0 : c->W);
+        st = fn(s0, c->S);
+    }
+    map_all(c);
+    return st;
+}
 }  // namespace ems
 
 #define EMS_CUDA(c, call)                                   \

@@ -368,6 +368,14 @@ __global__ void k_scatter_u(int nf, int n_nodes, const int32_t *node_of_free, co
         u[(size_t)s * n_nodes + node_of_free[i]] = x[(size_t)s * nf + i];
 }
 
+// IR initial guess from the node voltages (Monte Carlo windows: the work
+// vectors are rebuilt for every window, the voltages persist)
+__global__ void k_gather_x(int nf, int n_nodes, const int32_t *node_of_free, const double *u, double *x) {
+    const int s = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x)
+        x[(size_t)s * nf + i] = u[(size_t)s * n_nodes + node_of_free[i]];
+}
+
 // j = (u_a - u_b) / (R W H) per segment
 __global__ void k_currents(int n_seg, int n_nodes, const int32_t *sa, const int32_t *sb, const double *R,
                            const double *W, const double *H, const double *u, double *j) {
@@ -463,6 +471,31 @@ ems_status ir_assemble_and_solve(ems_ctx *c, bool warm) {
     return EMS_OK;
 }
 
+ems_status gather_x(ems_ctx *c) {
+    if (c->nf == 0) return EMS_OK;
+    dim3 g((c->nf + 255) / 256 < 1024 ? (c->nf + 255) / 256 : 1024, c->S);
+    k_gather_x<<<g, 256, 0, c->stream>>>(c->nf, c->n_nodes, c->d.ir_node_of_free, c->d.u, c->d.ir_x);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+ems_status currents(ems_ctx *c) {
+    Dev &d = c->d;
+    dim3 g((c->n_seg + 255) / 256 < 2048 ? (c->n_seg + 255) / 256 : 2048, c->S);
+    k_currents<<<g, 256, 0, c->stream>>>(c->n_seg, c->n_nodes, d.seg_a, d.seg_b, d.R, d.seg_W, d.seg_H, d.u, d.j);
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+// per-node coefficients of the mapped window (with the full layout they
+// persist and nothing is rebuilt)
+ems_status window_derive(ems_ctx *c) {
+    if (!windowed(c)) return EMS_OK;
+    return sample_physics(c);
+}
+
 ems_status ir_currents_and_drop(ems_ctx *c) {
     cudaStream_t st = c->stream;
     Dev &d = c->d;
@@ -495,8 +528,11 @@ ems_status check_status(ems_ctx *c) {
 extern "C" ems_status ems_ir_solve(ems_ctx *c, double *u_out, double *max_drop_frac) {
     if (!c) return EMS_E_INVAL;
     if (!c->loaded) return ems::fail(c, EMS_E_STATE, "no grid loaded");
-    EMS_TRY(ems::ir_assemble_and_solve(c, true));
-    EMS_TRY(ems::ir_currents_and_drop(c));
+    EMS_TRY(ems::each_window(c, [&](int, int) -> ems_status {
+        if (ems::windowed(c)) EMS_TRY(ems::gather_x(c));
+        EMS_TRY(ems::ir_assemble_and_solve(c, true));
+        return ems::ir_currents_and_drop(c);
+    }));
     if (u_out)
         EMS_CUDA(c, cudaMemcpyAsync(u_out, c->d.u, sizeof(double) * c->S * c->n_nodes,
                                     cudaMemcpyDeviceToHost, c->stream));

@@ -23,6 +23,7 @@
 // per (tree, sample) with leaf-to-root elimination.
 #include <cfloat>
 #include <cmath>
+#include <vector>
 
 #include "ems_device.cuh"
 #include "ems_internal.cuh"
@@ -1246,6 +1247,16 @@ ems_status node_physics(ems_ctx *c) {
                                                     c->rx1, c->ry1, p.T0, d.Tn);
     ++c->launches;
     EMS_CUDA(c, cudaGetLastError());
+    return sample_physics(c);
+}
+
+// kappa a, conductances, TM term, volumes, leak and thresholds of the mapped
+// samples from the node temperatures and the per-segment factors; voids
+// raise their node's threshold to +inf and mark the tree for a refactor
+ems_status sample_physics(ems_ctx *c) {
+    Dev &d = c->d;
+    const ems_params &p = c->prm;
+    cudaStream_t st = c->stream;
     PhysArgs a;
     a.N = c->N; a.n_seg = c->n_seg; a.gpar = d.par; a.face_seg = d.face_seg; a.owner_seg = d.owner_seg;
     a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx; a.Tn = d.Tn; a.dx = d.face_dx; a.area = d.face_area;
@@ -1383,7 +1394,16 @@ extern "C" ems_status ems_set_thermal_map(ems_ctx *c, const double *T, int nx, i
     } else {
         c->rnx = 0; c->rny = 0;
     }
-    EMS_TRY(node_physics(c));
+    if (windowed(c)) {
+        // the per-node coefficients are rebuilt for every window before use;
+        // here the temperatures, and the first window's coefficients
+        map_window(c, 0, c->W);
+        ems_status s = node_physics(c);
+        map_all(c);
+        EMS_TRY(s);
+    } else {
+        EMS_TRY(node_physics(c));
+    }
     EMS_CUDA(c, cudaStreamSynchronize(c->stream));
     return EMS_OK;
 }
@@ -1397,11 +1417,22 @@ extern "C" ems_status ems_stress_advance(ems_ctx *c, double dt, int n_steps, int
         return fail(c, EMS_E_INVAL, "unknown method");
     if (method != EMS_BE && c->rmax == 0)
         return fail(c, EMS_E_STATE, "Krylov method needs a context created with method EMS_KRYLOV or EMS_AUTO");
-    EMS_TRY(forcing(c));
-    int nn = 0;
-    EMS_TRY(advance(c, dt, n_steps, &nn, method));
+    if (windowed(c) && method != EMS_BE)
+        return fail(c, EMS_E_STATE, "the reduced models need every sample's coefficients (window_samples 0)");
+    const double t0 = c->t;
+    std::vector<int> nn((size_t)(c->S_all + c->W - 1) / c->W, 0);
+    EMS_TRY(each_window(c, [&](int s0, int) -> ems_status {
+        c->t = t0;
+        EMS_TRY(window_derive(c));
+        EMS_TRY(forcing(c));
+        return advance(c, dt, n_steps, &nn[(size_t)s0 / c->W], method);
+    }));
     EMS_TRY(check_status(c));
-    if (n_new_voids) *n_new_voids = nn;
+    if (n_new_voids) {
+        int tot = 0;
+        for (int v : nn) tot += v;
+        *n_new_voids = tot;
+    }
     return EMS_OK;
 }
 
@@ -1419,13 +1450,18 @@ extern "C" ems_status ems_immortality_check(ems_ctx *c, uint8_t *mortal, double 
     if (!c) return EMS_E_INVAL;
     if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
     if (!c->have_u) return fail(c, EMS_E_STATE, "screen before the first IR solve");
-    EMS_TRY(screen(c));
+    EMS_TRY(each_window(c, [&](int s0, int ns) -> ems_status {
+        EMS_TRY(window_derive(c));
+        EMS_TRY(screen(c));
+        if (sigma_ss)
+            EMS_CUDA(c, cudaMemcpyAsync(sigma_ss + (size_t)s0 * c->N, c->d.sig_ss, sizeof(double) * ns * c->N,
+                                        cudaMemcpyDeviceToHost, c->stream));
+        if (windowed(c)) EMS_CUDA(c, cudaStreamSynchronize(c->stream));   // the window's scratch is reused
+        return EMS_OK;
+    }));
     const size_t ts = (size_t)c->n_trees * c->S;
     if (mortal) EMS_CUDA(c, cudaMemcpyAsync(mortal, c->d.mortal, ts, cudaMemcpyDeviceToHost, c->stream));
     if (sigma_ss_max)
         EMS_CUDA(c, cudaMemcpyAsync(sigma_ss_max, c->d.ssmax, ts * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (sigma_ss)
-        EMS_CUDA(c, cudaMemcpyAsync(sigma_ss, c->d.sig_ss, sizeof(double) * c->S * c->N, cudaMemcpyDeviceToHost,
-                                    c->stream));
     return check_status(c);
 }

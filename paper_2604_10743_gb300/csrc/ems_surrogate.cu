@@ -201,9 +201,10 @@ cudaStream_t mlp_stream(const ems_mlp *m);
 }  // namespace ems
 
 namespace {
-ems_status features(ems_ctx *c) {
+ems_status features_window(ems_ctx *c) {
     Dev &d = c->d;
     const ems_params &p = c->prm;
+    EMS_TRY(window_derive(c));
     EMS_TRY(screen(c));
     FeatArgs a;
     a.n_trees = c->n_trees; a.S = c->S; a.n_seg = c->n_seg; a.N = c->N;
@@ -217,6 +218,11 @@ ems_status features(ems_ctx *c) {
     ++c->launches;
     EMS_CUDA(c, cudaGetLastError());
     return EMS_OK;
+}
+
+// features of every sample (window by window when the context uses windows)
+ems_status features(ems_ctx *c) {
+    return each_window(c, [&](int, int) { return features_window(c); });
 }
 }  // namespace
 

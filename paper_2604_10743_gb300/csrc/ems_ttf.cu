@@ -78,8 +78,8 @@ using namespace ems;
 
 namespace {
 
+// mortal-tree counts per sample from the screen's flags (already computed)
 ems_status screen_counts(ems_ctx *c, ems_ttf_result *out) {
-    EMS_TRY(screen(c));
     const int S = c->S;
     std::vector<uint8_t> mortal((size_t)S * c->n_trees);
     EMS_CUDA(c, cudaMemcpyAsync(mortal.data(), c->d.mortal, mortal.size(), cudaMemcpyDeviceToHost, c->stream));
@@ -126,17 +126,58 @@ ems_status finish(ems_ctx *c, ems_ttf_result *out, const std::vector<double> &tt
     return EMS_OK;
 }
 
-// all aging steps as one captured graph (BE, or reduced models plus BE)
+// One aging step of every sample, recorded on c->stream (the capture
+// stream): per window of samples, the window's coefficients, forcing, stress
+// advance, void update and IR re-solve, then the crossing test; ev holds 4
+// events per window (stress start / end, IR start / end).
+ems_status record_step(ems_ctx *c, double dto, double dti, bool kr, cudaEvent_t *ev) {
+    const ems_params &p = c->prm;
+    const int stride = p.n_outer + 1;
+    int w = 0;
+    EMS_TRY(each_window(c, [&](int, int ns) -> ems_status {
+        cudaEvent_t *e = ev + 4 * (size_t)(w++);
+        Dev &d = c->d;
+        EMS_CUDA(c, cudaEventRecordWithFlags(e[0], c->stream, cudaEventRecordExternal));
+        EMS_TRY(window_derive(c));
+        EMS_TRY(forcing(c));
+        EMS_TRY(kr ? krylov_stress(c, dti, p.n_inner) : launch_be(c, dti, p.n_inner));
+        EMS_CUDA(c, cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
+        EMS_TRY(void_update(c, nullptr));
+        EMS_CUDA(c, cudaEventRecordWithFlags(e[2], c->stream, cudaEventRecordExternal));
+        if (windowed(c)) EMS_TRY(gather_x(c));
+        EMS_TRY(ir_assemble_and_solve(c, true));
+        EMS_TRY(ir_currents_and_drop(c));
+        EMS_CUDA(c, cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal));
+        const unsigned gb = (unsigned)((ns + 255) / 256);
+        k_ttf_step<<<gb, 256, 0, c->stream>>>(ns, stride, p.ir_fail_frac, dto, d.drop, d.gttf, d.gdrops, d.giters,
+                                              d.ir_iters, d.gtime, d.gstep);
+        ++c->launches;
+        return EMS_OK;
+    }));
+    k_ttf_tick<<<1, 1, 0, c->stream>>>(c->S_all, dto, c->d.ir_iters, c->d.giters, c->d.gtime, c->d.gstep);
+    ++c->launches;
+    return EMS_OK;
+}
+
+// All aging steps as captured CUDA graphs (BE, or reduced models plus BE).
+// Full layout: one graph holds every aging step.  Monte Carlo windows: one
+// graph holds one aging step over all windows and is launched n_out times.
 ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
     const ems_params &p = c->prm;
     const double dto = p.horizon / p.n_outer, dti = dto / p.n_inner;
-    const int S = c->S, stride = p.n_outer + 1;
+    const int S = c->S_all, stride = p.n_outer + 1;
     cudaStream_t st = c->stream;
-    Dev &d = c->d;
     const unsigned gb = (unsigned)((S + 255) / 256);
+    const bool win = windowed(c);
+    const int n_win = win ? (S + c->W - 1) / c->W : 1;
+    const int steps_per_graph = win ? 1 : n_out;
     EMS_CUDA(c, cudaEventRecord(c->ev0, st));
-    EMS_TRY(ir_assemble_and_solve(c, true));
-    EMS_TRY(ir_currents_and_drop(c));
+    EMS_TRY(each_window(c, [&](int, int) -> ems_status {
+        if (windowed(c)) EMS_TRY(gather_x(c));
+        EMS_TRY(ir_assemble_and_solve(c, true));
+        return ir_currents_and_drop(c);
+    }));
+    Dev &d = c->d;
     k_ttf_init<<<gb, 256, 0, st>>>(S, stride, p.ir_fail_frac, d.drop, d.gttf, d.gdrops, d.giters, d.ir_iters, c->t,
                                    d.gtime, d.gstep);
     ++c->launches;
@@ -153,12 +194,13 @@ ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
         EMS_CUDA(c, cudaStreamSynchronize(st));
         c->factored_dt = dti;
     }
-    if (!c->ttf_graph || c->graph_nout != n_out || c->graph_dt != dti) {
+    const int graph_key = win ? -1 : n_out;
+    if (!c->ttf_graph || c->graph_nout != graph_key || c->graph_dt != dti) {
         if (c->ttf_graph) { cudaGraphExecDestroy(c->ttf_graph); c->ttf_graph = nullptr; }
         cudaGraph_t g = nullptr;
         const int64_t l0 = c->launches;
         for (auto e : c->gev) cudaEventDestroy(e);
-        c->gev.assign(4 * (size_t)n_out, nullptr);
+        c->gev.assign(4 * (size_t)steps_per_graph * n_win, nullptr);
         for (auto &e : c->gev) EMS_CUDA(c, cudaEventCreate(&e));
         // capture on a library stream (the caller's may be the legacy default
         // stream, which cannot be captured); the graph launches on the caller's
@@ -169,23 +211,10 @@ ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
         if (eb != cudaSuccess) { c->stream = user; cudaGetLastError(); return cuda_check(c, eb, "cudaStreamBeginCapture"); }
         c->graph_capturing = true;
         ems_status sx = EMS_OK;
-        for (int k = 0; k < n_out && sx == EMS_OK; ++k) {
-            cudaEvent_t *ev = &c->gev[4 * (size_t)k];
-            if (cudaEventRecordWithFlags(ev[0], c->stream, cudaEventRecordExternal) != cudaSuccess) { sx = EMS_E_CUDA; break; }
-            if ((sx = forcing(c)) != EMS_OK) break;
-            if ((sx = kr ? krylov_stress(c, dti, p.n_inner) : launch_be(c, dti, p.n_inner)) != EMS_OK) break;
-            if (cudaEventRecordWithFlags(ev[1], c->stream, cudaEventRecordExternal) != cudaSuccess) { sx = EMS_E_CUDA; break; }
-            if ((sx = void_update(c, nullptr)) != EMS_OK) break;
-            if (cudaEventRecordWithFlags(ev[2], c->stream, cudaEventRecordExternal) != cudaSuccess) { sx = EMS_E_CUDA; break; }
-            if ((sx = ir_assemble_and_solve(c, true)) != EMS_OK) break;
-            if ((sx = ir_currents_and_drop(c)) != EMS_OK) break;
-            if (cudaEventRecordWithFlags(ev[3], c->stream, cudaEventRecordExternal) != cudaSuccess) { sx = EMS_E_CUDA; break; }
-            k_ttf_step<<<gb, 256, 0, c->stream>>>(S, stride, p.ir_fail_frac, dto, d.drop, d.gttf, d.gdrops, d.giters,
-                                           d.ir_iters, d.gtime, d.gstep);
-            k_ttf_tick<<<1, 1, 0, c->stream>>>(S, dto, d.ir_iters, d.giters, d.gtime, d.gstep);
-            c->launches += 2;
-        }
+        for (int k = 0; k < steps_per_graph && sx == EMS_OK; ++k)
+            sx = record_step(c, dto, dti, kr, &c->gev[4 * (size_t)k * n_win]);
         c->graph_capturing = false;
+        map_all(c);
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
         c->stream = user;
         if (sx != EMS_OK || e != cudaSuccess) cudaGetLastError();
@@ -194,13 +223,30 @@ ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
         e = cudaGraphInstantiate(&c->ttf_graph, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) { c->ttf_graph = nullptr; return cuda_check(c, e, "cudaGraphInstantiate"); }
-        c->graph_nout = n_out;
+        c->graph_nout = graph_key;
         c->graph_dt = dti;
         c->graph_launches = c->launches - l0;
         c->launches = l0;                             // counted when launched
     }
-    EMS_CUDA(c, cudaGraphLaunch(c->ttf_graph, st));
-    c->launches += c->graph_launches;
+    float ms_stress = 0.0f, ms_ir = 0.0f;
+    auto add_times = [&]() -> ems_status {
+        for (size_t q = 0; q < c->gev.size(); q += 4) {
+            float a = 0.0f, b = 0.0f;
+            EMS_CUDA(c, cudaEventElapsedTime(&a, c->gev[q], c->gev[q + 1]));
+            EMS_CUDA(c, cudaEventElapsedTime(&b, c->gev[q + 2], c->gev[q + 3]));
+            ms_stress += a;
+            ms_ir += b;
+        }
+        return EMS_OK;
+    };
+    for (int k = 0; k < n_out; k += steps_per_graph) {
+        EMS_CUDA(c, cudaGraphLaunch(c->ttf_graph, st));
+        c->launches += c->graph_launches;
+        if (win) {                                    // the step graph's events are re-recorded next launch
+            EMS_CUDA(c, cudaStreamSynchronize(st));
+            EMS_TRY(add_times());
+        }
+    }
     EMS_CUDA(c, cudaEventRecord(c->ev1, st));
     std::vector<double> ttf(S), all((size_t)S * stride), drop(S);
     double it_total = 0.0;
@@ -208,15 +254,7 @@ ems_status ttf_graph(ems_ctx *c, int n_out, ems_ttf_result *out) {
     EMS_CUDA(c, cudaMemcpyAsync(all.data(), d.gdrops, 8 * all.size(), cudaMemcpyDeviceToHost, st));
     EMS_CUDA(c, cudaMemcpyAsync(&it_total, d.giters, 8, cudaMemcpyDeviceToHost, st));
     EMS_TRY(check_status(c));
-    float ms = 0.0f, ms_stress = 0.0f, ms_ir = 0.0f;
-    EMS_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    for (int k = 0; k < n_out; ++k) {
-        float a = 0.0f, b = 0.0f;
-        EMS_CUDA(c, cudaEventElapsedTime(&a, c->gev[4 * (size_t)k], c->gev[4 * (size_t)k + 1]));
-        EMS_CUDA(c, cudaEventElapsedTime(&b, c->gev[4 * (size_t)k + 2], c->gev[4 * (size_t)k + 3]));
-        ms_stress += a;
-        ms_ir += b;
-    }
+    if (!win) EMS_TRY(add_times());
     c->t += dto * n_out;
     std::vector<double> trimmed((size_t)S * (n_out + 1));
     for (int s = 0; s < S; ++s) {
@@ -237,15 +275,20 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
     if (out) out->graph_launch = 0.0;
     EMS_CUDA(c, cudaMemsetAsync(c->d.work, 0, sizeof(unsigned long long), c->stream));
     if (opts && opts->screen) {
-        EMS_TRY(ir_assemble_and_solve(c, true));
-        EMS_TRY(ir_currents_and_drop(c));
+        EMS_TRY(each_window(c, [&](int, int) -> ems_status {
+            if (windowed(c)) EMS_TRY(gather_x(c));
+            EMS_TRY(ir_assemble_and_solve(c, true));
+            EMS_TRY(ir_currents_and_drop(c));
+            EMS_TRY(window_derive(c));
+            return screen(c);
+        }));
         EMS_TRY(screen_counts(c, out));
     }
     if (!(opts && opts->no_graph) && n_out <= p.n_outer) return ttf_graph(c, n_out, out);
 
     const double dto = p.horizon / p.n_outer, dti = dto / p.n_inner;
     const double thr = p.ir_fail_frac;
-    const int S = c->S;
+    const int S = c->S_all;
     cudaStream_t st = c->stream;
     std::vector<double> drop(S), prev(S), ttf(S, INFINITY);
     std::vector<double> all((size_t)S * (n_out + 1));
@@ -267,8 +310,11 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
     } guard{e2, e3};
 
     EMS_CUDA(c, cudaEventRecord(c->ev0, st));
-    EMS_TRY(ir_assemble_and_solve(c, true));
-    EMS_TRY(ir_currents_and_drop(c));
+    EMS_TRY(each_window(c, [&](int, int) -> ems_status {
+        if (windowed(c)) EMS_TRY(gather_x(c));
+        EMS_TRY(ir_assemble_and_solve(c, true));
+        return ir_currents_and_drop(c);
+    }));
     EMS_CUDA(c, cudaEventRecord(c->ev1, st));
     EMS_CUDA(c, cudaMemcpyAsync(drop.data(), c->d.drop, 8 * S, cudaMemcpyDeviceToHost, st));
     EMS_TRY(check_status(c));
@@ -283,21 +329,29 @@ extern "C" ems_status ems_ttf(ems_ctx *c, const ems_ttf_opts *opts, ems_ttf_resu
     for (int k = 0; k < n_out; ++k) {
         const double t_prev = c->t;
         prev = drop;
-        EMS_CUDA(c, cudaEventRecord(c->ev0, st));
-        EMS_TRY(forcing(c));
-        EMS_TRY(advance(c, dti, p.n_inner, nullptr, p.method));
-        EMS_CUDA(c, cudaEventRecord(c->ev1, st));
-        EMS_TRY(void_update(c, nullptr));
-        EMS_CUDA(c, cudaEventRecord(e2, st));
-        EMS_TRY(ir_assemble_and_solve(c, true));
-        EMS_TRY(ir_currents_and_drop(c));
-        EMS_CUDA(c, cudaEventRecord(e3, st));
+        EMS_TRY(each_window(c, [&](int, int) -> ems_status {
+            c->t = t_prev;
+            EMS_CUDA(c, cudaEventRecord(c->ev0, st));
+            EMS_TRY(window_derive(c));
+            EMS_TRY(forcing(c));
+            EMS_TRY(advance(c, dti, p.n_inner, nullptr, p.method));
+            EMS_CUDA(c, cudaEventRecord(c->ev1, st));
+            EMS_TRY(void_update(c, nullptr));
+            EMS_CUDA(c, cudaEventRecord(e2, st));
+            if (windowed(c)) EMS_TRY(gather_x(c));
+            EMS_TRY(ir_assemble_and_solve(c, true));
+            EMS_TRY(ir_currents_and_drop(c));
+            EMS_CUDA(c, cudaEventRecord(e3, st));
+            EMS_CUDA(c, cudaStreamSynchronize(st));
+            EMS_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            ms_stress += ms;
+            EMS_CUDA(c, cudaEventElapsedTime(&ms, e2, e3));
+            ms_ir += ms;
+            return EMS_OK;
+        }));
+        c->t = t_prev + dto;
         EMS_CUDA(c, cudaMemcpyAsync(drop.data(), c->d.drop, 8 * S, cudaMemcpyDeviceToHost, st));
         EMS_TRY(check_status(c));
-        EMS_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-        ms_stress += ms;
-        EMS_CUDA(c, cudaEventElapsedTime(&ms, e2, e3));
-        ms_ir += ms;
         EMS_TRY(add_iters());
         node_steps += (double)c->N * S * p.n_inner;
         for (int s = 0; s < S; ++s) {

@@ -14,13 +14,13 @@ from . import _abi as A
 class Engine:
     def __init__(self, params, grid, precision=A.EMS_F64, method=A.EMS_BE, ir_rtol=1e-13,
                  ir_max_iter=20000, max_voids=16, workspace="torch", stream=None, thermal=True,
-                 ir_precond=A.EMS_PC_AUTO):
+                 ir_precond=A.EMS_PC_AUTO, window=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Engine needs a CUDA device")
         self.L = A.lib()
         self.p = dict(params)
-        self.prm = A.make_params(params, precision, method, ir_rtol, ir_max_iter, max_voids, ir_precond)
+        self.prm = A.make_params(params, precision, method, ir_rtol, ir_max_iter, max_voids, ir_precond, window)
         self.gd = A.GridDesc(grid)
         self.S = self.gd.n_samples
         nbytes = self.L.ems_workspace_bytes(ctypes.byref(self.prm), ctypes.byref(self.gd.desc))

@@ -108,3 +108,25 @@ def test_surrogate_calls_reject_bad_arguments_without_a_device(L):
     assert L.ems_surrogate_targets(None, 10.0, 0, None) == 1
     assert L.ems_surrogate_schedule(None, None, 0.1, 16, 0.8, None, None) == 1
     assert L.ems_surrogate_clear(None) == 1
+
+
+def test_window_layout_sizes(L):
+    """Monte Carlo windows: the per-sample part of the workspace shrinks to
+    the state (stress, resistances, voltages, factors, voids) and the
+    per-node coefficients are held for W samples only; the reduced models
+    need the full layout."""
+    g = es.mc_grid(n_samples=64)
+    full = _ws(L, g)
+    w8 = _ws(L, g, window=8)
+    w64 = _ws(L, g, window=64)
+    assert 0 < w8 < full and w64 == full and _ws(L, g, window=0) == full
+    assert _ws(L, g, window=-1) == 0
+    from paper_2604_10743_gb300 import _abi as A
+    assert _ws(L, g, window=8, method=A.EMS_KRYLOV) == 0
+    assert _ws(L, g, window=64, method=A.EMS_KRYLOV) > 0
+    # growth per extra sample with windows: state only (well under the
+    # full layout's per-sample coefficient arrays)
+    g2 = es.mc_grid(n_samples=128)
+    per_full = (_ws(L, g2) - full) / 64
+    per_win = (_ws(L, g2, window=8) - w8) / 64
+    assert per_win < 0.25 * per_full
