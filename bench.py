@@ -439,7 +439,7 @@ def schedule_leg(p, stream, n_train=24, n_valid=3, test_seed=3000, N=64, S=32):
         xs.append(x); ts.append(t)
     X, T = torch.cat(xs), torch.cat(ts)
     m = sg.Mlp(n_hidden=4, seed=0)
-    m.set_norm(*sg.fit_norm(X, T))
+    m.fit_norm(X, T)
     losses = m.train(X, T, batch=1024, epochs=30, lr=1e-3, seed=1)
     bound, _ = sg.validate_bound(m, [grid(2000 + k) for k in range(n_valid)], p, coarsen=16, guard=0.8,
                                  candidates=(-0.3, 0.0, 0.3, 0.6, 1.0))

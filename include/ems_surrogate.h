@@ -63,6 +63,17 @@ ems_status ems_mlp_set_norm(ems_mlp *mlp, const float *x_mean, const float *x_st
                             const float *t_std);
 
 /*
+ * Standardisation fitted to a record set on the device and installed in the
+ * network: per column of x (24 features) and t (2 targets) the mean and the
+ * standard deviation (square root of the mean squared deviation, FP64 sums
+ * in a fixed order; a column whose deviation is under 1e-6 gets 1).
+ *   x, t    device [rows][24], [rows][2] raw features and targets
+ *   stats   optional host [52] doubles: x mean[24], x std[24], t mean[2], t std[2]
+ * Synchronises the network's stream.  EMS_E_INVAL for rows < 1 or null data.
+ */
+ems_status ems_mlp_fit_norm(ems_mlp *mlp, const float *x, const float *t, int64_t rows, double *stats);
+
+/*
  * Forward + backward without an update, for gradient checks.
  *   x       device [rows][24] raw features; t device [rows][2] raw targets
  *   grads   host [ems_mlp_param_count]: dL/dparam in the flat layout, with L

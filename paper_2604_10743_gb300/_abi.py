@@ -69,7 +69,7 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc",
            # include/ems_surrogate.h
            "ems_mlp_create", "ems_mlp_destroy", "ems_mlp_last_error", "ems_mlp_param_count",
-           "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_gradients",
+           "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_fit_norm", "ems_mlp_gradients",
            "ems_mlp_train_step", "ems_mlp_train", "ems_mlp_predict", "ems_gemm_bf16",
            "ems_surrogate_features", "ems_surrogate_targets", "ems_surrogate_schedule", "ems_surrogate_clear"]
 
@@ -134,6 +134,7 @@ def lib(path=None):
             ("ems_mlp_set_params", S, [vp, fp]),
             ("ems_mlp_get_params", S, [vp, fp]),
             ("ems_mlp_set_norm", S, [vp, fp, fp, fp, fp]),
+            ("ems_mlp_fit_norm", S, [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_double)]),
             ("ems_mlp_gradients", S, [vp, vp, vp, S, fp, fp]),
             ("ems_mlp_train_step", S, [vp, vp, vp, S, f32, fp]),
             ("ems_mlp_train", S, [vp, vp, vp, i64, S, S, f32, u64, fp]),

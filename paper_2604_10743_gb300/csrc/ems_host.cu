@@ -302,12 +302,12 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
 void chain_shape(int64_t n, int prec, int *T, int *M) {
     const int64_t target = prec == EMS_F32 ? 448 : 192;
     // FP32 chains the register-resident kernel holds: 16 nodes per thread
-    // (<= 384 threads) for long chains, 8 (<= 640 threads) for short ones
+    // (<= 320 threads) for long chains, 8 (<= 576 threads) for short ones
     if (prec == EMS_F32) {
         int want = n > 2048 ? 16 : 8;
         if (const char *e = getenv("EMS_CHAIN_M")) want = atoi(e);
         for (int m : {want, 16, 8}) {
-            const int64_t lim = m == 16 ? 384 : m == 8 ? 640 : m == 4 ? 1024 : 0;
+            const int64_t lim = m == 16 ? 320 : m == 8 ? 576 : m == 4 ? 896 : 0;
             const int64_t t = ((n + m - 1) / m + 31) / 32 * 32;
             if (t <= lim) { *T = (int)t; *M = m; return; }
         }
@@ -488,6 +488,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.uu = cv.take<char>((size_t)Sd * P * eb); d.Pf = cv.take<char>((size_t)Sd * P * eb);
     d.Pb = cv.take<char>((size_t)Sd * P * eb); d.pinv = cv.take<double>((size_t)Sd * P);
     d.dtg = cv.take<char>((size_t)Sd * P * eb); d.dtl = cv.take<char>((size_t)Sd * P * eb);
+    d.kc = cv.take<char>((size_t)Sd * P * eb);
     d.v_count = cv.take<int32_t>((size_t)S * nt);
     d.v_node = cv.take<int32_t>((size_t)S * nt * maxv); d.v_seg = cv.take<int32_t>((size_t)S * nt * maxv);
     d.v_vol = cv.take<double>((size_t)S * nt * maxv); d.v_tnuc = cv.take<double>((size_t)S * nt * maxv);

@@ -149,6 +149,7 @@ struct Dev {
     // packed state and factors: element type is float or double (precision)
     void *sig, *alpha, *beta, *gam, *uu, *Pf, *Pb, *pinv;   // [S][P]
     void *dtg, *dtl;                   // [S][P] FP32 increment form: dt g per face, dt leak per node
+    void *kc;                          // [S][P] FP32 streaming chain kernel: compensation of the state sums
     // voids per (sample, tree)
     int32_t *v_count;                  // [S][n_trees]
     int32_t *v_node, *v_seg;           // [S][n_trees][MAXV]

@@ -958,6 +958,65 @@ extern "C" ems_status ems_mlp_set_norm(ems_mlp *m, const float *xm, const float 
     return EMS_OK;
 }
 
+namespace {
+// Column statistics of a record set for the standardisation: one CTA per
+// column (24 feature columns, then 2 target columns), FP64 sums in a fixed
+// order (strided per thread, then the block tree), mean first, then the
+// centred second moment; std = sqrt(mean square deviation), 1 where it is
+// under 1e-6 (a constant column).  Output: x mean, x std, t mean, t std.
+__global__ void __launch_bounds__(256) k_col_stats(const float *x, const float *t, int64_t rows, float *norm,
+                                                   double *stats) {
+    __shared__ double sh[256];
+    const int col = blockIdx.x;
+    const float *src = col < NF ? x : t;
+    const int ld = col < NF ? NF : NO, cc = col < NF ? col : col - NF;
+    auto bsum = [&](double v) {
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        const double r = sh[0];
+        __syncthreads();
+        return r;
+    };
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) a += (double)src[i * ld + cc];
+    const double mean = bsum(a) / (double)rows;
+    double q = 0.0;
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+        const double d = (double)src[i * ld + cc] - mean;
+        q += d * d;
+    }
+    double sd = sqrt(bsum(q) / (double)rows);
+    if (!(sd > 1e-6)) sd = 1.0;
+    if (threadIdx.x == 0) {
+        const int mo = col < NF ? cc : 2 * NF + cc, so = col < NF ? NF + cc : 2 * NF + NO + cc;
+        norm[mo] = (float)mean;
+        norm[so] = (float)sd;
+        stats[mo] = mean;
+        stats[so] = sd;
+    }
+}
+}  // namespace
+
+extern "C" ems_status ems_mlp_fit_norm(ems_mlp *m, const float *x, const float *t, int64_t rows, double *stats) {
+    if (!m || !x || !t || rows < 1) return EMS_E_INVAL;
+    double *dst = nullptr;
+    MLP_CUDA(m, cudaMallocAsync((void **)&dst, sizeof(double) * (2 * NF + 2 * NO), m->st));
+    k_col_stats<<<NF + NO, 256, 0, m->st>>>(x, t, rows, m->norm, dst);
+    cudaError_t e = cudaGetLastError();
+    double h[2 * NF + 2 * NO];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, dst, sizeof h, cudaMemcpyDeviceToHost, m->st);
+    cudaFreeAsync(dst, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    if (e != cudaSuccess) return mcuda(m, e, "ems_mlp_fit_norm");
+    if (stats)
+        for (int k = 0; k < 2 * NF + 2 * NO; ++k) stats[k] = h[k];
+    return EMS_OK;
+}
+
 extern "C" ems_status ems_mlp_gradients(ems_mlp *m, const float *x, const float *t, int rows, float *grads,
                                         float *loss) {
     if (!m || !x || !t || !grads || rows < 1 || rows > 65536) return EMS_E_INVAL;

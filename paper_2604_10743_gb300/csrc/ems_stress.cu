@@ -165,6 +165,7 @@ struct ChainArgs {
     const double *V, *g, *leak, *f;
     double *thr;
     R *sig, *alpha, *beta, *gam, *uu, *Pf, *Pb, *dtg, *dtl;
+    R *kc;                            // increment form, streaming kernel: compensation of the state sums
     double *pinv;
     int32_t *v_count, *v_node, *v_seg;
     double *v_vol, *v_tnuc;
@@ -388,7 +389,10 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, SMC ? 1 : ChainM
     float thr_f = __double2float_rd(thrmin);
     R sg[M];
 #pragma unroll
-    for (int k = 0; k < M; ++k) sg[k] = a.sig[ps + (int64_t)k * T + c];
+    for (int k = 0; k < M; ++k) {
+        sg[k] = a.sig[ps + (int64_t)k * T + c];
+        if (DELTA) a.kc[ps + (int64_t)k * T + c] = R(0);    // compensations start at 0 every launch
+    }
 
     // Step schedule, block-uniform and kept in shared memory (read only on
     // rare branches): s_rs fine steps per step of length s_dt; the current
@@ -525,20 +529,34 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, SMC ? 1 : ChainM
             }
             const R cf = scan_fwd<R>(z, pF[(int64_t)(M - 1) * T], sA, sB, sC);
             R x = R(0);
+            // this chunk's increments before the right carry replace the
+            // forward values (registers with SMC, else shared memory)
 #pragma unroll
             for (int k = M - 1; k >= 0; --k) {
                 if constexpr (SMC) {
                     const R gk1 = k + 1 < M ? pG[(int64_t)(k + 1) * T] : g_next;
                     x = fmx(pP[(int64_t)k * T] * gk1, x, fmx(pF[(int64_t)k * T], cf, zr[k]));
+                    zr[k] = x;
                 } else {
                     const float2 e = zu[k * T + c];
                     x = fmx((R)e.y, x, fmx(pF[(int64_t)k * T], cf, (R)e.x));
+                    zu[k * T + c].x = (float)x;
                 }
-                sg[k] += x;
             }
             const R cr = scan_bwd<R>(x, pBk[0], sA, sB, sC);
+            // compensated (Kahan) state update, the compensation kept in a
+            // global array (no register room for it at these chunk lengths)
 #pragma unroll
-            for (int k = 0; k < M; ++k) sg[k] = fmx(pBk[(int64_t)k * T], cr, sg[k]);
+            for (int k = 0; k < M; ++k) {
+                R &ck = a.kc[ps + (int64_t)k * T + c];
+                R xk;
+                if constexpr (SMC) xk = zr[k];
+                else xk = (R)zu[k * T + c].x;
+                const R y = fmx(pBk[(int64_t)k * T], cr, xk) - ck;
+                const R t = sg[k] + y;
+                ck = (t - sg[k]) - y;
+                sg[k] = t;
+            }
         }
 
         // void growth by the Robin leak: the owner thread of a void node stores
@@ -658,9 +676,9 @@ __global__ void __launch_bounds__(ChainMaxThreads<R, M>::value, SMC ? 1 : ChainM
 // The arithmetic of a step is the same as k_chain's increment form.
 // ---------------------------------------------------------------------------
 template <int M> struct RegMaxThreads;
-template <> struct RegMaxThreads<4> { static constexpr int value = 1024; };
-template <> struct RegMaxThreads<8> { static constexpr int value = 640; };
-template <> struct RegMaxThreads<16> { static constexpr int value = 384; };
+template <> struct RegMaxThreads<4> { static constexpr int value = 896; };
+template <> struct RegMaxThreads<8> { static constexpr int value = 576; };
+template <> struct RegMaxThreads<16> { static constexpr int value = 320; };
 
 template <int M>
 __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainArgs<float> a) {
@@ -688,9 +706,12 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
     double tm = INFINITY;
     for (int i = c; i < n; i += T) tm = fmin(tm, a.thr[cs + i]);
     double thrmin = block_min(tm, sv);
-    R sg[M];
+    // state and its compensation: every increment is added with Kahan's
+    // compensated summation, so increments far below an ulp of the stress
+    // (late, slow evolution) accumulate instead of being rounded away
+    R sg[M], cc[M];
 #pragma unroll
-    for (int k = 0; k < M; ++k) sg[k] = a.sig[ps + (int64_t)k * T + c];
+    for (int k = 0; k < M; ++k) { sg[k] = a.sig[ps + (int64_t)k * T + c]; cc[k] = R(0); }
 
     int rs = sm > 1 ? sm : 1;
     if ((a.n_steps - kd) % rs) rs = 1;
@@ -800,11 +821,16 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
         for (int k = M - 1; k >= 0; --k) {
             const R gk1 = k + 1 < M ? cg[k + 1] : g_next;
             x = fmx(cp[k] * gk1, x, fmx(cpf[k], cf, zr[k]));
-            sg[k] += x;
+            zr[k] = x;
         }
         const R cr = scan_bwd<R>(x, cpb[0], sA, sB, sC);
 #pragma unroll
-        for (int k = 0; k < M; ++k) sg[k] = fmx(cpb[k], cr, sg[k]);
+        for (int k = 0; k < M; ++k) {
+            const R y = fmx(cpb[k], cr, zr[k]) - cc[k];      // the step's increment, compensated
+            const R t = sg[k] + y;
+            cc[k] = (t - sg[k]) - y;
+            sg[k] = t;
+        }
 
         // void growth by the Robin leak
         if (vmask) {
@@ -1153,7 +1179,7 @@ ChainArgs<R> chain_args(ems_ctx *c, double dt, int n_steps) {
     a.V = d.V; a.g = d.g; a.leak = d.leak; a.f = d.f; a.thr = d.thr;
     a.sig = (R *)d.sig; a.alpha = (R *)d.alpha; a.beta = (R *)d.beta; a.gam = (R *)d.gam;
     a.uu = (R *)d.uu; a.Pf = (R *)d.Pf; a.Pb = (R *)d.Pb; a.pinv = (double *)d.pinv;
-    a.dtg = (R *)d.dtg; a.dtl = (R *)d.dtl;
+    a.dtg = (R *)d.dtg; a.dtl = (R *)d.dtl; a.kc = (R *)d.kc;
     a.v_count = d.v_count; a.v_node = d.v_node; a.v_seg = d.v_seg; a.v_vol = d.v_vol; a.v_tnuc = d.v_tnuc;
     a.dirty = d.dirty; a.j = d.j; a.n_seg = c->n_seg; a.face_seg = d.face_seg; a.inc_ptr = d.inc_ptr;
     a.inc_seg = d.inc_seg; a.gpar = d.par; a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx;
@@ -1192,7 +1218,8 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
             dim3 grid((unsigned)b.trees.size(), c->S);
             cudaError_t e = cudaSuccess;
             if constexpr (kDelta) {
-                if ((b.M == 4 && b.T <= 1024) || (b.M == 8 && b.T <= 640) || (b.M == 16 && b.T <= 384)) {
+                if ((b.M == 4 && b.T <= RegMaxThreads<4>::value) || (b.M == 8 && b.T <= RegMaxThreads<8>::value) ||
+                    (b.M == 16 && b.T <= RegMaxThreads<16>::value)) {
                     if (b.M == 4) k_chain_reg<4><<<grid, b.T, 0, c->stream>>>(a);
                     else if (b.M == 8) k_chain_reg<8><<<grid, b.T, 0, c->stream>>>(a);
                     else k_chain_reg<16><<<grid, b.T, 0, c->stream>>>(a);

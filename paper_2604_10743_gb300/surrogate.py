@@ -6,7 +6,7 @@ primitive.  The pipeline functions string C-ABI calls together:
   generate_records   per (tree, sample): features at t = 0 and the first
                      nucleation time / node of the plain solver run with the
                      t = 0 currents, stepped to t_cap
-  fit_norm           standardisation statistics of a record set
+  Mlp.fit_norm       standardisation statistics of a record set (device)
   validate_bound     the skip bound, validated end to end: the most
                      aggressive candidate whose scheduled TTF runs of held-out
                      grids reproduce the plain solver's TTF and final IR drop
@@ -84,6 +84,16 @@ class Mlp:
         a = [np.ascontiguousarray(v, np.float32) for v in (x_mean, x_std, t_mean, t_std)]
         self.norm = a
         self._check(self.L.ems_mlp_set_norm(self.h, *[_fptr(v) for v in a]))
+
+    def fit_norm(self, x, t):
+        """Fit the standardisation to a record set on the device and install
+        it (ems_mlp_fit_norm); returns (x_mean, x_std, t_mean, t_std)."""
+        st = np.empty(2 * N_FEATURES + 2 * N_OUTPUTS)
+        self._check(self.L.ems_mlp_fit_norm(self.h, _vp(x), _vp(t), int(x.shape[0]),
+                                            st.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        nf = N_FEATURES
+        self.norm = [st[:nf], st[nf:2 * nf], st[2 * nf:2 * nf + N_OUTPUTS], st[2 * nf + N_OUTPUTS:]]
+        return tuple(self.norm)
 
     def gradients(self, x, t):
         g = np.empty(self.n_params, np.float32)
@@ -173,13 +183,6 @@ def generate_records(grid, params, t_cap_factor=10.0, precision=A.EMS_F32, ext_o
     return x, t
 
 
-def fit_norm(x, t):
-    """Per-column mean and standard deviation of features and targets (host)."""
-    xh = x.cpu().numpy().astype(np.float64)
-    th = t.cpu().numpy().astype(np.float64)
-    xs = xh.std(0)
-    ts = th.std(0)
-    return (xh.mean(0), np.where(xs > 1e-6, xs, 1.0), th.mean(0), np.where(ts > 1e-6, ts, 1.0))
 
 
 def scale_to_drop(grid, params, target, precision=A.EMS_F32):

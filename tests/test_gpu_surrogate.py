@@ -203,3 +203,27 @@ def test_training_reduces_loss(sg):
     _, l1 = m.gradients(xd, td)
     assert np.all(np.isfinite(losses))
     assert l1 < 0.1 * l0, (l0, l1, losses)
+
+
+def test_fit_norm_matches_column_statistics(sg):
+    """ems_mlp_fit_norm: column means and standard deviations (FP64 sums on
+    the device) against numpy's, a constant column gets std 1, and the
+    installed standardisation is the one the network then uses."""
+    rng = np.random.default_rng(3)
+    x = rng.normal(2.0, 3.0, size=(50_001, 24)).astype(np.float32)
+    x[:, 5] = 7.25                                       # constant column
+    t = np.stack([rng.normal(8.0, 1.5, 50_001), rng.uniform(0, 1, 50_001)], 1).astype(np.float32)
+    m = sg.Mlp(n_hidden=2, seed=0)
+    xm, xs, tm, ts = m.fit_norm(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    xd, td = x.astype(np.float64), t.astype(np.float64)
+    assert np.allclose(xm, xd.mean(0), rtol=1e-12, atol=1e-12)
+    ref_s = xd.std(0); ref_s[5] = 1.0
+    assert np.allclose(xs, ref_s, rtol=1e-10, atol=0)
+    assert np.allclose(tm, td.mean(0), rtol=1e-12) and np.allclose(ts, td.std(0), rtol=1e-10)
+    # the same statistics through the host call give the same predictions
+    xt = torch.from_numpy(x[:4096]).cuda()
+    y1 = m.predict(xt).cpu().numpy()
+    m.set_norm(xm, xs, tm, ts)
+    y2 = m.predict(xt).cpu().numpy()
+    assert np.array_equal(y1, y2)
+    m.close()

@@ -74,7 +74,7 @@ def test_schedule_matches_plain_solver_with_fewer_steps(mods):
         xs.append(x); ts.append(t)
     X, T = torch.cat(xs), torch.cat(ts)
     m = sg.Mlp(n_hidden=4, seed=0)
-    m.set_norm(*sg.fit_norm(X, T))
+    m.fit_norm(X, T)
     losses = m.train(X, T, batch=1024, epochs=30, lr=1e-3, seed=1)
     assert losses[-1] < 0.5 * losses[0]
     bound, log = sg.validate_bound(m, [_grid(es, sg, p, 2000 + k) for k in range(3)], p, coarsen=16, guard=0.8,
