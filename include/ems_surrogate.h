@@ -159,6 +159,27 @@ ems_status ems_surrogate_schedule(ems_ctx *ctx, ems_mlp *mlp, double bound, int 
                                   int *n_coarse, float *pred);
 ems_status ems_surrogate_clear(ems_ctx *ctx);
 
+/*
+ * The skip bound, validated end to end against the plain solver, which stays
+ * the judge of the schedule's error.  Every context in ctxs (held-out grids,
+ * loaded, any Monte Carlo sample count) is run from its current state by
+ * ems_ttf twice per candidate comparison: once plain (no schedule; run once
+ * per context) and once under ems_surrogate_schedule(ctx, mlp, candidate,
+ * coarsen, guard).  A candidate passes when, over every context and sample,
+ * the sets of samples with a finite TTF agree and the largest relative
+ * difference of TTF (where finite) and of the final IR drop is <= tol.
+ * Candidates are tried in the order given (most aggressive first); *bound
+ * receives the first passing candidate + margin, or +inf if none passes.
+ * Every context is left in the state it had on entry, with no schedule.
+ *   log  optional host [n_cand][3]: candidate, fraction of (tree, sample)
+ *        pairs scheduled coarse, largest relative error (+inf for a differing
+ *        set of failed samples); rows after the passing one are not written
+ * EMS_E_INVAL for null or empty inputs, coarsen < 2 or guard outside (0, 1].
+ */
+ems_status ems_surrogate_validate(ems_ctx *const *ctxs, int n_ctx, ems_mlp *mlp, const double *candidates,
+                                  int n_cand, int coarsen, double guard, double tol, double margin,
+                                  double *bound, double *log);
+
 #ifdef __cplusplus
 }
 #endif

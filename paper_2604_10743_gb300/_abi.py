@@ -71,7 +71,8 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_mlp_create", "ems_mlp_destroy", "ems_mlp_last_error", "ems_mlp_param_count",
            "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_fit_norm", "ems_mlp_gradients",
            "ems_mlp_train_step", "ems_mlp_train", "ems_mlp_predict", "ems_gemm_bf16",
-           "ems_surrogate_features", "ems_surrogate_targets", "ems_surrogate_schedule", "ems_surrogate_clear"]
+           "ems_surrogate_features", "ems_surrogate_targets", "ems_surrogate_schedule", "ems_surrogate_clear",
+           "ems_surrogate_validate"]
 
 
 def lib(path=None):
@@ -143,7 +144,10 @@ def lib(path=None):
             ("ems_surrogate_features", S, [vp, vp]),
             ("ems_surrogate_targets", S, [vp, ctypes.c_double, S, vp]),
             ("ems_surrogate_schedule", S, [vp, vp, ctypes.c_double, S, ctypes.c_double, c_int32_p, vp]),
-            ("ems_surrogate_clear", S, [vp])):
+            ("ems_surrogate_clear", S, [vp]),
+            ("ems_surrogate_validate", S, [ctypes.POINTER(vp), S, vp, ctypes.POINTER(ctypes.c_double), S, S,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)])):
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args

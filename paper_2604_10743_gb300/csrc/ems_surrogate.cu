@@ -304,3 +304,87 @@ extern "C" ems_status ems_surrogate_clear(ems_ctx *c) {
     EMS_CUDA(c, cudaMemsetAsync(c->d.sched, 0, sizeof(int32_t) * c->S * c->n_trees, c->stream));
     return EMS_OK;
 }
+
+namespace {
+// one TTF run's per-sample outputs
+struct RunOut {
+    std::vector<double> ttf, final_drop;
+};
+
+ems_status ttf_run(ems_ctx *c, RunOut &o) {
+    o.ttf.assign(c->S_all, 0.0);
+    o.final_drop.assign(c->S_all, 0.0);
+    ems_ttf_result r{};
+    r.ttf = o.ttf.data();
+    r.final_drop = o.final_drop.data();
+    ems_ttf_opts opts{};
+    return ems_ttf(c, &opts, &r);
+}
+
+// largest relative difference of TTF (where the reference's is finite) and
+// final IR drop; +inf when the sets of finite TTFs differ
+double result_error(const RunOut &ref, const RunOut &run) {
+    double e = 0.0;
+    for (size_t s = 0; s < ref.ttf.size(); ++s) {
+        const bool fr = std::isfinite(ref.ttf[s]), fx = std::isfinite(run.ttf[s]);
+        if (fr != fx) return INFINITY;
+        e = std::max(e, std::fabs(run.final_drop[s] - ref.final_drop[s]) / ref.final_drop[s]);
+        if (fr) e = std::max(e, std::fabs(run.ttf[s] - ref.ttf[s]) / std::max(ref.ttf[s], 1e-30));
+    }
+    return e;
+}
+}  // namespace
+
+extern "C" ems_status ems_surrogate_validate(ems_ctx *const *ctxs, int n_ctx, ems_mlp *m, const double *cand,
+                                             int n_cand, int coarsen, double guard, double tol, double margin,
+                                             double *bound, double *log) {
+    if (!ctxs || n_ctx < 1 || !m || !cand || n_cand < 1 || coarsen < 2 || !(guard > 0.0 && guard <= 1.0) ||
+        !(tol >= 0.0) || !std::isfinite(margin) || !bound)
+        return EMS_E_INVAL;
+    for (int k = 0; k < n_ctx; ++k) {
+        if (!ctxs[k]) return EMS_E_INVAL;
+        if (!ctxs[k]->loaded) return fail(ctxs[k], EMS_E_STATE, "no grid loaded");
+    }
+    *bound = INFINITY;
+    // entry states (restored before every run and at the end) and the plain runs
+    std::vector<std::vector<char>> state(n_ctx);
+    std::vector<RunOut> plain(n_ctx);
+    for (int k = 0; k < n_ctx; ++k) {
+        ems_ctx *c = ctxs[k];
+        size_t nb = 0;
+        EMS_TRY(ems_state_export(c, nullptr, &nb));
+        state[k].resize(nb);
+        EMS_TRY(ems_state_export(c, state[k].data(), &nb));
+        EMS_TRY(ems_surrogate_clear(c));
+        EMS_TRY(ttf_run(c, plain[k]));
+        EMS_TRY(ems_state_import(c, state[k].data(), nb));
+    }
+    ems_status st = EMS_OK;
+    for (int q = 0; q < n_cand && st == EMS_OK; ++q) {
+        double worst = 0.0, coarse = 0.0, pairs = 0.0;
+        for (int k = 0; k < n_ctx && st == EMS_OK; ++k) {
+            ems_ctx *c = ctxs[k];
+            std::vector<int> nc(c->S_all, 0);
+            RunOut run;
+            if ((st = ems_ir_solve(c, nullptr, nullptr)) != EMS_OK) break;
+            if ((st = ems_surrogate_schedule(c, m, cand[q], coarsen, guard, nc.data(), nullptr)) != EMS_OK) break;
+            if ((st = ttf_run(c, run)) != EMS_OK) break;
+            for (int v : nc) coarse += v;
+            pairs += (double)c->S_all * c->n_trees;
+            worst = std::max(worst, result_error(plain[k], run));
+            if ((st = ems_surrogate_clear(c)) != EMS_OK) break;
+            st = ems_state_import(c, state[k].data(), state[k].size());
+        }
+        if (st != EMS_OK) break;
+        if (log) {
+            log[3 * q] = cand[q];
+            log[3 * q + 1] = coarse / std::max(pairs, 1.0);
+            log[3 * q + 2] = worst;
+        }
+        if (worst <= tol) {
+            *bound = cand[q] + margin;
+            break;
+        }
+    }
+    return st;
+}

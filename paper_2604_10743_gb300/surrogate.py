@@ -7,17 +7,15 @@ primitive.  The pipeline functions string C-ABI calls together:
                      nucleation time / node of the plain solver run with the
                      t = 0 currents, stepped to t_cap
   Mlp.fit_norm       standardisation statistics of a record set (device)
-  validate_bound     the skip bound, validated end to end: the most
-                     aggressive candidate whose scheduled TTF runs of held-out
-                     grids reproduce the plain solver's TTF and final IR drop
-                     within the tolerance, plus a margin
+  validate_bound     the skip bound, validated end to end on held-out grids
+                     (ems_surrogate_validate): the most aggressive candidate
+                     whose scheduled TTF runs reproduce the plain solver's TTF
+                     and final IR drop within the tolerance, plus a margin
   Engine.schedule    (engine.py) skip flags for one context
 
 Every computation runs in libems.so; torch holds the device tensors.
 """
 import ctypes
-import math
-
 import numpy as np
 
 from . import _abi as A
@@ -199,52 +197,26 @@ def scale_to_drop(grid, params, target, precision=A.EMS_F32):
     return g
 
 
-def result_error(ref, run):
-    """Largest relative difference of TTF (where the reference's is finite)
-    and final IR drop between two ems_ttf results; inf when the sets of
-    finite TTFs differ."""
-    fr, fx = np.isfinite(ref["ttf"]), np.isfinite(run["ttf"])
-    if np.any(fr != fx):
-        return math.inf
-    e = float(np.max(np.abs(run["final_drop"] - ref["final_drop"]) / ref["final_drop"]))
-    if fr.any():
-        t = ref["ttf"][fr]
-        e = max(e, float(np.max(np.abs(run["ttf"][fr] - t) / np.maximum(t, 1e-30))))
-    return e
-
-
 def validate_bound(mlp, grids, params, coarsen=16, guard=0.8, candidates=(-1.0, -0.6, -0.3, 0.0, 0.3, 0.6, 1.0, 1.5),
-                   tol=5e-4, margin=0.1, precision=A.EMS_F32, plains=None):
-    """Schedule bound validated end to end against the plain solver: for
-    each candidate (most aggressive first), full coupled TTF runs of the
-    held-out grids under the surrogate step schedule (`coarsen`-times coarser
-    steps where predicted log10 t_nuc - bound > log10 horizon) must reproduce
-    the plain runs' TTF and final IR drop within `tol`.  Returns (first
-    passing candidate + margin, or inf when none passes; per-candidate log).
-    `plains` may pass the plain runs' results when already computed."""
-    log = []
-    if plains is None:
-        plains = []
-        for g in grids:
-            eng = Engine(params, g, precision=precision, max_voids=32)
-            try:
-                plains.append(eng.ttf())
-            finally:
-                eng.close()
-    for b in candidates:
-        worst, skipped, pairs = 0.0, 0, 0
-        for g, rp in zip(grids, plains):
-            eng = Engine(params, g, precision=precision, max_voids=32)
-            try:
-                eng.ir_solve()
-                n, _ = eng.schedule(mlp, b, coarsen, guard)
-                r = eng.ttf()
-                skipped += int(n.sum())
-                pairs += eng.S * eng.n_trees
-            finally:
-                eng.close()
-            worst = max(worst, result_error(rp, r))
-        log.append(dict(bound=b, coarse_frac=skipped / max(pairs, 1), max_rel_err=worst))
-        if worst <= tol:
-            return b + margin, log
-    return math.inf, log
+                   tol=5e-4, margin=0.1, precision=A.EMS_F32):
+    """Schedule bound validated end to end against the plain solver
+    (ems_surrogate_validate on one context per held-out grid).  Returns
+    (first passing candidate + margin, or inf when none passes;
+    per-candidate log of dicts bound / coarse_frac / max_rel_err)."""
+    engs = [Engine(params, g, precision=precision, max_voids=32) for g in grids]
+    try:
+        ctxs = (ctypes.c_void_p * len(engs))(*[e.ctx.value for e in engs])
+        cand = np.ascontiguousarray(candidates, np.float64)
+        log = np.full((cand.size, 3), np.nan)
+        bound = ctypes.c_double()
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = engs[0].L.ems_surrogate_validate(ctxs, len(engs), mlp.h, cand.ctypes.data_as(dp), int(cand.size),
+                                              int(coarsen), float(guard), float(tol), float(margin),
+                                              ctypes.byref(bound), log.ctypes.data_as(dp))
+        engs[0]._check(st)
+    finally:
+        for e in engs:
+            e.close()
+    rows = [dict(bound=float(r[0]), coarse_frac=float(r[1]), max_rel_err=float(r[2]))
+            for r in log if not np.isnan(r[0])]
+    return bound.value, rows

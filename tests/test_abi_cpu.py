@@ -108,6 +108,16 @@ def test_surrogate_calls_reject_bad_arguments_without_a_device(L):
     assert L.ems_surrogate_targets(None, 10.0, 0, None) == 1
     assert L.ems_surrogate_schedule(None, None, 0.1, 16, 0.8, None, None) == 1
     assert L.ems_surrogate_clear(None) == 1
+    b = ctypes.c_double()
+    cand = (ctypes.c_double * 2)(0.0, 0.5)
+    assert L.ems_surrogate_validate(None, 1, None, cand, 2, 16, 0.8, 5e-4, 0.1, ctypes.byref(b), None) == 1
+    ctxs = (ctypes.c_void_p * 1)(None)
+    assert L.ems_surrogate_validate(ctxs, 1, ctypes.c_void_p(8), cand, 2, 1, 0.8, 5e-4, 0.1,
+                                    ctypes.byref(b), None) == 1                    # coarsen < 2
+    assert L.ems_surrogate_validate(ctxs, 1, ctypes.c_void_p(8), cand, 2, 16, 1.5, 5e-4, 0.1,
+                                    ctypes.byref(b), None) == 1                    # guard > 1
+    assert L.ems_surrogate_validate(ctxs, 1, ctypes.c_void_p(8), cand, 2, 16, 0.8, 5e-4, 0.1,
+                                    ctypes.byref(b), None) == 1                    # null context
 
 
 def test_window_layout_sizes(L):

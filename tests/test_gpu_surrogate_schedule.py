@@ -60,6 +60,20 @@ def test_features_match_oracle_quantities(mods):
         assert x[t, 5] == pytest.approx(math.log10(min(tl[o:e].min(), 1e13)), abs=1e-5)
 
 
+def _result_error(ref, run):
+    """Largest relative difference of TTF (where the reference's is finite)
+    and final IR drop between two TTF results; inf when the sets of failed
+    samples differ."""
+    fr, fx = np.isfinite(ref["ttf"]), np.isfinite(run["ttf"])
+    if np.any(fr != fx):
+        return math.inf
+    e = float(np.max(np.abs(run["final_drop"] - ref["final_drop"]) / ref["final_drop"]))
+    if fr.any():
+        t = ref["ttf"][fr]
+        e = max(e, float(np.max(np.abs(run["ttf"][fr] - t) / np.maximum(t, 1e-30))))
+    return e
+
+
 def _grid(es, sg, p, seed, N=64, S=32):
     g = es.grid.surrogate_grid(seed=seed, N=N, n_samples=S)
     return sg.scale_to_drop(g, p, np.random.default_rng(seed + 7).uniform(0.07, 0.095))
@@ -90,6 +104,6 @@ def test_schedule_matches_plain_solver_with_fewer_steps(mods):
     r2 = e2.ttf()
     e2.close()
     assert n_coarse.sum() > 0
-    assert sg.result_error(r1, r2) <= 5e-4
+    assert _result_error(r1, r2) <= 5e-4
     assert r1["node_steps_executed"] == pytest.approx(r1["node_steps"])
     assert r2["node_steps_executed"] <= 0.9 * r1["node_steps_executed"]
