@@ -399,7 +399,7 @@ def crossing_time(t_prev, d_prev, d_now, dt, thr):
 
 
 def run_ttf(grid, p, sample=None, screen_first=False, record=False, n_threads=0,
-            n_outer=None, stepper=None, keep_state=False):
+            n_outer=None, stepper=None, keep_state=False, Tn=None):
     """Coupled EM/TM/IR aging loop (Sec. IV-A) for one sample.
 
     Each outer step: G and f from the current j -> n_inner BE steps with
@@ -407,12 +407,14 @@ def run_ttf(grid, p, sample=None, screen_first=False, record=False, n_threads=0,
     TTF is the linear-interpolated first crossing of ir_fail_frac (0 if the
     initial drop already exceeds it, inf if never crossed).  `stepper`
     replaces the BE advance (Krylov path): stepper(tr, p, phys, f, st, t0,
-    dt, n) -> new void count.
+    dt, n) -> new void count.  Tn replaces the node temperatures sampled
+    from the map (e.g. a Joule-heating profile).
     """
     tr = build_trees(grid) if "trees" not in grid else grid["trees"]
     kf = None if sample is None or grid.get("kappa_factor") is None else grid["kappa_factor"][sample]
     sf = None if sample is None or grid.get("sigc_factor") is None else grid["sigc_factor"][sample]
-    Tn = node_temperature(tr, grid.get("thermal"), p["T0"])
+    if Tn is None:
+        Tn = node_temperature(tr, grid.get("thermal"), p["T0"])
     phys = tree_physics(tr, p, Tn, kf, sf)
     n_out = p["n_outer"] if n_outer is None else n_outer
     dto = p["horizon"] / p["n_outer"]

@@ -91,9 +91,15 @@ def shift_time(tr, phys, t, eta):
     return eta * L * L / (math.pi ** 2 * kbar)
 
 
-def krylov_basis(C, A, f, sigma0, s0, q, eps_rel=1e-10):
+def krylov_basis(C, A, f, sigma0, s0, q, eps_rel=1e-10, ortho="mgs"):
     """Alg. 1.  Returns (V, A_h, C_h, f_h, status) with status 'ok',
-    'empty' (nothing to reduce) or 'rank' (rank-deficient later block)."""
+    'empty' (nothing to reduce) or 'rank' (rank-deficient later block).
+    ortho: "mgs" orthogonalises each new block against the earlier blocks
+    block by block (twice) and then within itself by a QR; "cgs2" takes the
+    block's columns one at a time, each orthogonalised against every earlier
+    column by classical Gram-Schmidt applied twice.  The two span the same
+    space in exact arithmetic; comparing them measures how far rounding
+    alone moves the reduced model."""
     K = (s0 * C - A).tocsc()
     lu = spla.splu(K)
 
@@ -120,6 +126,23 @@ def krylov_basis(C, A, f, sigma0, s0, q, eps_rel=1e-10):
     for j in range(1, q):
         W = Mop(blocks[-1])
         epsj = eps_rel * np.linalg.norm(W)
+        if ortho == "cgs2":
+            prev = np.column_stack(blocks)
+            qs, norms = [], []
+            for k in range(W.shape[1]):
+                w = W[:, k].copy()
+                for _ in range(2):
+                    B = np.column_stack([prev] + qs) if qs else prev
+                    w = w - B @ (B.T @ w)
+                nw = np.linalg.norm(w)
+                norms.append(nw)
+                qs.append(w / nw if nw > 0 else w)
+            if math.sqrt(sum(v * v for v in norms)) < epsj:
+                break
+            if min(norms) < epsj:
+                return None, None, None, None, "rank"
+            blocks.append(np.column_stack(qs))
+            continue
         for _ in range(2):                      # block modified Gram-Schmidt, applied twice
             for Vi in blocks:                   # (the second pass restores orthogonality
                 H = Vi.T @ W                    # lost to rounding; it leaves the span as is)
@@ -162,9 +185,10 @@ def augment(V, lu, C, sigma0, f, eps_rel=1e-10):
 class KrylovStepper:
     """Drop-in replacement for flow.advance inside flow.run_ttf."""
 
-    def __init__(self, q=10, eta=1.0, n_threads=0, cache=True, policy="augment"):
+    def __init__(self, q=10, eta=1.0, n_threads=0, cache=True, policy="augment", ortho="mgs"):
         if policy not in ("augment", "forcing", "stale"):
             raise ValueError("policy must be 'augment', 'forcing' or 'stale'")
+        self.ortho = ortho
         self.q = q
         self.eta = eta
         self.n_threads = n_threads
@@ -202,7 +226,7 @@ class KrylovStepper:
                         V = augment(V, lu, C, sig, ft)
                     Ah, Ch, fh, status = V.T @ (A @ V), V.T @ (C @ V), V.T @ ft, "ok"
                 else:
-                    V, Ah, Ch, fh, status = krylov_basis(C, A, ft, sig, s0, self.q)
+                    V, Ah, Ch, fh, status = krylov_basis(C, A, ft, sig, s0, self.q, ortho=self.ortho)
                     self.n_built += 1
                     if status == "ok" and self.cache is not None:
                         self.cache[key] = (V, spla.splu((s0 * C - A).tocsc()))
