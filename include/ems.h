@@ -75,7 +75,7 @@ typedef struct {
     double krylov_eta;     /* shift-time factor eta (Eq. rak_shift_time) */
     double ir_rtol;        /* PCG relative residual target (||r|| <= rtol ||b||) */
     int    ir_max_iter;    /* PCG iteration cap (EMS_E_NOCONV beyond it) */
-    int    max_voids_per_tree;  /* void slots per (tree, sample) */
+    int    max_voids_per_tree;  /* void slots per (tree, sample), 1..256 */
     int    ir_precond;     /* EMS_PC_AUTO: smoothed-aggregation multigrid V-cycle for systems of
                               >= 1,024 unknowns (hierarchy built once from the initial
                               resistances), Jacobi below; EMS_PC_JACOBI: Jacobi always */

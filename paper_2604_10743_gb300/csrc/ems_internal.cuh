@@ -17,7 +17,7 @@
 
 #include "../../include/ems.h"
 
-#define EMS_MAX_VOIDS 32      // compile-time cap on void slots per (tree, sample)
+#define EMS_MAX_VOIDS 256     // compile-time cap on void slots per (tree, sample)
 #define EMS_MAX_RASTER (1024 * 1024)  // thermal raster values held in the workspace
 
 namespace ems {
