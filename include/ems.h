@@ -165,6 +165,34 @@ ems_status ems_set_thermal_map(ems_ctx *ctx, const double *T, int nx, int ny,
                                double x0, double y0, double x1, double y1);
 
 /*
+ * Joule-heating temperature profile along every branch (Sec. III-A: the
+ * stationary thermal equation k T'' + j^2 rho - k (T - T0) / Gamma^2 = 0 with
+ * the thermal characteristic length Gamma^2 = t_cu t_ILD k_cu / k_ILD, t_cu
+ * the segment's thickness H).  Per segment with end temperatures T1 (end a)
+ * and T2 (end b), on x in [-L/2, L/2]:
+ *   T(x) = T0 + Tm + (Tbar - T0 - Tm) cosh(x/Gamma) / cosh(L/(2 Gamma))
+ *             - Tn sinh(x/Gamma) / sinh(L/(2 Gamma)),
+ *   Tm = j^2 rho_Cu Gamma^2 / k_cu, Tbar = (T1 + T2)/2, Tn = (T1 - T2)/2
+ * (the printed solution's cos / sin terms solve the equation with the
+ * opposite sign of the loss term; this is the form that satisfies it).
+ * End temperatures: an IR node that joins segments of different layers (a
+ * via) or is a pad takes the thermal map's value (params.T0 without a map);
+ * every other IR node is solved from zero net heat flow into its segments
+ * (one thread per tree, leaf-to-root elimination).  Uses the current
+ * densities of sample 0 (all samples share them until voids form) and the
+ * map set by ems_set_thermal_map; the profile replaces the node
+ * temperatures, kappa and the thermomigration term follow, and it stays
+ * until the next ems_set_thermal_map.
+ *   k_cu, k_ild   thermal conductivities of the wire and the dielectric (W/(m K))
+ *   t_ild         dielectric thickness (m)
+ * EMS_E_STATE before the first IR solve; EMS_E_INVAL for non-positive inputs.
+ */
+ems_status ems_joule_profile(ems_ctx *ctx, double k_cu, double k_ild, double t_ild);
+
+/* Node temperatures in use (host [n_stress_nodes], canonical order, K). */
+ems_status ems_get_node_temperature(ems_ctx *ctx, double *T);
+
+/*
  * IR-drop solve (Sec. III-C, Eq. ir_drop_mna) for every sample with the
  * current resistances: preconditioned CG in FP64 on the conductance matrix of
  * the non-pad nodes (params.ir_precond: a smoothed-aggregation multigrid

@@ -197,7 +197,7 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
     total += tr.n_trees;
     tr.par.reserve(total); tr.face_seg.reserve(total); tr.face_dx.reserve(total);
     tr.face_area.reserve(total); tr.face_sign.reserve(total); tr.x.reserve(total);
-    tr.y.reserve(total); tr.owner_seg.reserve(total);
+    tr.y.reserve(total); tr.owner_seg.reserve(total); tr.ir_id.reserve(total); tr.ir_par.reserve(total);
     tr.inc_ptr.assign(1, 0);
     tr.is_chain.assign(tr.n_trees, 1);
 
@@ -225,7 +225,8 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
         const int64_t base = (int64_t)tr.par.size();
         int32_t cnt = 0;
         auto emit = [&](int32_t parent, int32_t seg, double dx, double area, int8_t sign, double xx,
-                        double yy, int32_t own, int32_t grp) -> int32_t {
+                        double yy, int32_t own, int32_t grp, int32_t irn, int32_t irp) -> int32_t {
+            tr.ir_id.push_back(irn); tr.ir_par.push_back(irp);
             tr.par.push_back(parent); tr.face_seg.push_back(seg); tr.face_dx.push_back(dx);
             tr.face_area.push_back(area); tr.face_sign.push_back(sign);
             tr.x.push_back(xx); tr.y.push_back(yy); tr.owner_seg.push_back(own);
@@ -238,7 +239,7 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
             return cnt++;
         };
         int32_t rg = group_of(layer, root);
-        emit(-1, -1, 0.0, 0.0, 0, g->node_x[root], g->node_y[root], rec[gstart[rg]].seg, rg);
+        emit(-1, -1, 0.0, 0.0, 0, g->node_x[root], g->node_y[root], rec[gstart[rg]].seg, rg, root, -1);
         // depth-first preorder: ("node", ir, local, came) or ("seg", pir, plocal, seg, cir)
         struct Item { int kind; int32_t u, lu, s, w; };
         std::vector<Item> stack;
@@ -266,11 +267,11 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
                     double f = (double)k / cells;
                     prev = emit(prev, s, dx, area, sign,
                                 g->node_x[u] + f * (g->node_x[w] - g->node_x[u]),
-                                g->node_y[u] + f * (g->node_y[w] - g->node_y[u]), s, -1);
+                                g->node_y[u] + f * (g->node_y[w] - g->node_y[u]), s, -1, -1, -1);
                 }
                 int32_t wg = group_of(layer, w);
                 int32_t lw = emit(prev, s, dx, area, sign, g->node_x[w], g->node_y[w],
-                                  rec[gstart[wg]].seg, wg);
+                                  rec[gstart[wg]].seg, wg, w, it.lu);
                 stack.push_back({0, w, lw, s, -1});
             }
         }
@@ -514,6 +515,9 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.sched = cv.take<int32_t>((size_t)S * nt);
     d.fdt = cv.take<double>((size_t)S * nt);
     d.work = cv.take<unsigned long long>(1);
+    d.ir_id = cv.take<int32_t>(N); d.ir_par = cv.take<int32_t>(N);
+    d.node_x = cv.take<double>(nn); d.node_y = cv.take<double>(nn); d.seg_L = cv.take<double>(ns);
+    d.ir_fixed = cv.take<int8_t>(nn); d.T_ir = cv.take<double>(nn);
     const int rmax = (c && c->prm.method != EMS_BE) ? 2 * c->prm.krylov_q + 2 : 0;
     if (rmax > 0) {
         d.kr_V = cv.take<unsigned char>((size_t)S * rmax * P * eb);
@@ -708,6 +712,23 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     EMS_CUDA(c, up(D.face_area, tr.face_area.data(), N, st));
     EMS_CUDA(c, up(D.nx_, tr.x.data(), N, st));
     EMS_CUDA(c, up(D.ny_, tr.y.data(), N, st));
+    EMS_CUDA(c, up(D.ir_id, tr.ir_id.data(), N, st));
+    EMS_CUDA(c, up(D.ir_par, tr.ir_par.data(), N, st));
+    EMS_CUDA(c, up(D.node_x, g->node_x, (size_t)g->n_nodes, st));
+    EMS_CUDA(c, up(D.node_y, g->node_y, (size_t)g->n_nodes, st));
+    EMS_CUDA(c, up(D.seg_L, g->seg_L, (size_t)ns, st));
+    {   // IR nodes whose temperature is given: vias between layers and pads
+        std::vector<int32_t> lay0((size_t)g->n_nodes, -1);
+        std::vector<int8_t> fixed((size_t)g->n_nodes, 0);
+        for (int q = 0; q < ns; ++q)
+            for (int32_t nd : {g->seg_a[q], g->seg_b[q]}) {
+                if (lay0[nd] < 0) lay0[nd] = g->seg_layer[q];
+                else if (lay0[nd] != g->seg_layer[q]) fixed[nd] = 1;
+            }
+        for (int q = 0; q < g->n_pads; ++q) fixed[g->pad_node[q]] = 1;
+        EMS_CUDA(c, up(D.ir_fixed, fixed.data(), fixed.size(), st));
+        EMS_CUDA(c, cudaStreamSynchronize(st));
+    }
     {   // inc_ptr is per node: global CSR over all nodes
         EMS_CUDA(c, up(D.inc_ptr, tr.inc_ptr.data(), tr.inc_ptr.size(), st));
     }
@@ -743,6 +764,7 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     c->t = 0.0;
     c->factored_dt = -1.0;
     c->have_u = false;
+    c->joule = false;
     c->loaded = true;
     // uniform temperature, node physics, initial stress
     EMS_TRY(ems_set_thermal_map(c, nullptr, 0, 0, 0, 0, 0, 0));

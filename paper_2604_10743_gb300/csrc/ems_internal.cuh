@@ -89,6 +89,8 @@ struct HostTrees {
     std::vector<int32_t> child_ptr, child_idx;  // tree-local children, CSR over nodes
     std::vector<uint8_t> is_chain;     // per tree
     std::vector<int32_t> tree_of_seg;  // per segment
+    std::vector<int32_t> ir_id;        // per stress node: its IR node, -1 inside a segment
+    std::vector<int32_t> ir_par;       // per IR stress node: tree-local index of the parent IR stress node (-1 root)
 };
 
 // Packing of one tree
@@ -183,6 +185,11 @@ struct Dev {
     int32_t *sched;                    // [S][n_trees] step schedule: <= 1 fine, r > 1 r-times coarser, < 0 frozen
     double *fdt;                       // [S][n_trees] step the packed factors were built for
     unsigned long long *work;          // [1] node-steps the stress kernels executed
+    // Joule-heating profile (ems_joule.cu)
+    int32_t *ir_id, *ir_par;           // [N] per stress node
+    double *node_x, *node_y, *seg_L;   // IR node coordinates [n_nodes], segment lengths [n_seg]
+    int8_t *ir_fixed;                  // [n_nodes] 1: temperature given (via between layers, or a pad)
+    double *T_ir;                      // [n_nodes] IR node temperatures of the last profile
 };
 
 }  // namespace ems
@@ -237,6 +244,7 @@ struct ems_ctx {
     double kr_eta = 1.0;
     int kr_kc = 64;            // steps per on-chip chunk of the reduced trajectory
     double sched_guard = 0.8;  // coarse trees turn fine once sigma >= guard * lowest sigma_crit
+    bool joule = false;        // node temperatures hold a Joule-heating profile (not the raster)
     // thermal raster currently set (nx = 0: uniform T0)
     int rnx = 0, rny = 0;
     double rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;

@@ -1270,10 +1270,12 @@ ems_status node_physics(ems_ctx *c) {
     Dev &d = c->d;
     const ems_params &p = c->prm;
     cudaStream_t st = c->stream;
-    k_temperature<<<grid_1d(c->N, 1), 256, 0, st>>>(c->N, d.nx_, d.ny_, d.raster, c->rnx, c->rny, c->rx0, c->ry0,
-                                                    c->rx1, c->ry1, p.T0, d.Tn);
-    ++c->launches;
-    EMS_CUDA(c, cudaGetLastError());
+    if (!c->joule) {           // a Joule-heating profile, once set, stays until a new map
+        k_temperature<<<grid_1d(c->N, 1), 256, 0, st>>>(c->N, d.nx_, d.ny_, d.raster, c->rnx, c->rny, c->rx0,
+                                                        c->ry0, c->rx1, c->ry1, p.T0, d.Tn);
+        ++c->launches;
+        EMS_CUDA(c, cudaGetLastError());
+    }
     return sample_physics(c);
 }
 
@@ -1421,6 +1423,7 @@ extern "C" ems_status ems_set_thermal_map(ems_ctx *c, const double *T, int nx, i
     } else {
         c->rnx = 0; c->rny = 0;
     }
+    c->joule = false;
     if (windowed(c)) {
         // the per-node coefficients are rebuilt for every window before use;
         // here the temperatures, and the first window's coefficients

@@ -77,6 +77,15 @@ class Engine:
         self._check(self.L.ems_set_thermal_map(self.ctx, T.ctypes.data_as(A.c_double_p), nx, ny,
                                                th["x0"], th["y0"], th["x1"], th["y1"]))
 
+    def joule_profile(self, k_cu=400.0, k_ild=1.4, t_ild=0.2e-6):
+        """Joule-heating temperature profile along every branch (ems_joule_profile)."""
+        self._check(self.L.ems_joule_profile(self.ctx, float(k_cu), float(k_ild), float(t_ild)))
+
+    def node_temperature(self):
+        T = np.empty(self.n_stress)
+        self._check(self.L.ems_get_node_temperature(self.ctx, T.ctypes.data_as(A.c_double_p)))
+        return T
+
     def ir_solve(self):
         u = np.empty((self.S, self.n_nodes)); d = np.empty(self.S)
         self._check(self.L.ems_ir_solve(self.ctx, u.ctypes.data_as(A.c_double_p), d.ctypes.data_as(A.c_double_p)))
