@@ -307,6 +307,16 @@ ems_status ems_get_resistance(ems_ctx *ctx, double *R /* [S][n_seg] */);
 ems_status ems_get_voids(ems_ctx *ctx, int cap, int32_t *sample, int32_t *node,
                          int32_t *seg, double *volume, double *t_nuc, int *n);
 
+/*
+ * Iteration limit of the device-side waits of this context (the grid
+ * barriers of the cooperative IR solvers): after `polls` polls a wait gives
+ * up, every block of the kernel returns, and the call reports
+ * EMS_E_TIMEOUT; the context stays usable.  polls >= 1; 0 restores the
+ * default, 2^24 polls (about a second).  A guard against a lost participant,
+ * not a tuning knob: a limit too small for the work makes solves time out.
+ */
+ems_status ems_set_wait_limit(ems_ctx *ctx, long long polls);
+
 /* PCG iterations of the last IR solve, per sample (host [S]). */
 ems_status ems_ir_iterations(ems_ctx *ctx, int32_t *iters);
 

@@ -618,6 +618,11 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     Dev &D = c->d;
     cudaStream_t st = c->stream;
     EMS_CUDA(c, cudaMemsetAsync(c->ws, 0, need - 256, st));
+    {   // polls a grid-barrier wait makes before giving up (words 2-3 of the barrier block)
+        const long long lim = kDefaultWaitLimit;
+        EMS_CUDA(c, cudaMemcpyAsync(D.gbar + 2, &lim, sizeof lim, cudaMemcpyHostToDevice, st));
+        EMS_CUDA(c, cudaStreamSynchronize(st));
+    }
     c->S = pl.S; c->S_all = pl.S; c->W = pl.Sd; c->win_s0 = 0;
     c->d_all = c->d;
     c->n_nodes = g->n_nodes; c->n_seg = g->n_seg; c->n_pads = g->n_pads;
@@ -770,6 +775,15 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     EMS_TRY(ems_set_thermal_map(c, nullptr, 0, 0, 0, 0, 0, 0));
     EMS_TRY(ems::init_sigma(c));
     EMS_CUDA(c, cudaStreamSynchronize(st));
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_set_wait_limit(ems_ctx *c, long long polls) {
+    if (!c || polls < 0) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    const long long lim = polls == 0 ? kDefaultWaitLimit : polls;
+    EMS_CUDA(c, cudaMemcpyAsync(c->d_all.gbar + 2, &lim, sizeof lim, cudaMemcpyHostToDevice, c->stream));
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
     return EMS_OK;
 }
 

@@ -19,6 +19,8 @@
 
 #define EMS_MAX_VOIDS 256     // compile-time cap on void slots per (tree, sample)
 #define EMS_MAX_RASTER (1024 * 1024)  // thermal raster values held in the workspace
+// polls a grid-barrier wait makes before it gives up (about a second)
+constexpr long long kDefaultWaitLimit = 1LL << 24;
 
 namespace ems {
 

@@ -287,7 +287,6 @@ namespace {
 
 constexpr int kStatusNoConv = 0;
 constexpr int kStatusTimeout = 1;
-constexpr long kSpinLimit = 1L << 24;
 
 struct MGArgs {
     int nf, S;
@@ -328,6 +327,7 @@ __device__ bool gsync(unsigned int *bar, int32_t *status) {
     if (threadIdx.x == 0) {
         ok = 1;
         volatile unsigned int *vgen = bar + 1;
+        const long long limit = *((volatile long long *)(bar + 2));   // polls before giving up
         const unsigned int gen = *vgen;
         __threadfence();
         const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
@@ -338,7 +338,7 @@ __device__ bool gsync(unsigned int *bar, int32_t *status) {
         } else {
             long spins = 0;
             while (*vgen == gen) {
-                if (++spins > kSpinLimit || *((volatile int32_t *)&status[kStatusTimeout])) {
+                if (++spins > limit || *((volatile int32_t *)&status[kStatusTimeout])) {
                     atomicOr(&status[kStatusTimeout], 1);
                     ok = 0;
                     break;

@@ -159,6 +159,9 @@ class Engine:
                                          ctypes.byref(n)))
         return dict(sample=smp, node=node, seg=seg, volume=vol, t_nuc=tn)
 
+    def set_wait_limit(self, polls):
+        self._check(self.L.ems_set_wait_limit(self.ctx, int(polls)))
+
     def ir_iterations(self):
         it = np.empty(self.S, np.int32)
         self._check(self.L.ems_ir_iterations(self.ctx, it.ctypes.data_as(A.c_int32_p)))

@@ -385,11 +385,10 @@ def test_krylov_tiny_matches_oracle_and_be():
     r = eng.ttf()
     ks = K.KrylovStepper(q=20)
     ref = F.run_ttf(g, p, keep_state=True, stepper=ks)
-    # two FP64 implementations of the same recursion (Gram-Schmidt order,
-    # increment-form reduced stepping) agree to round-off amplified by the
-    # conditioning of the bases, an order below the reduced model's own
-    # error against BE
-    assert _relerr(eng.sigma()[0], ref["state"].sigma) < 1e-5
+    # the same reduced model in two FP64 implementations (classical
+    # Gram-Schmidt twice per column here, block Gram-Schmidt + QR in the
+    # oracle): measured 1e-12 apart, within the FP64 bar
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
     gpu, ora, _ = _void_sets(eng, ref)
     assert gpu == ora
     assert abs(r["final_drop"][0] - ref["final_drop"]) <= 1e-6 * ref["final_drop"]
@@ -410,7 +409,7 @@ def test_krylov_f32_tiny_matches_oracle():
     eng = _engine(p, g, method=EMS_KRYLOV, precision=EMS_F32)
     r = eng.ttf()
     ref = F.run_ttf(g, p, keep_state=True, stepper=K.KrylovStepper(q=20))
-    assert _relerr(eng.sigma()[0], ref["state"].sigma) < 1e-3
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
     gpu, ora, _ = _void_sets(eng, ref)
     assert [v for v, _ in gpu] == [v for v, _ in ora]
     assert abs(r["ttf"][0] - ref["ttf"]) <= TTF_TOL * ref["ttf"]
@@ -466,7 +465,7 @@ def test_krylov_mc_samples_mixed_with_be():
     sig = eng.sigma()
     for s in range(3):
         ref = F.run_ttf(g, p, sample=s, keep_state=True, stepper=K.KrylovStepper(q=20))
-        assert _relerr(sig[s], ref["state"].sigma) < 1e-5, s
+        assert _relerr(sig[s], ref["state"].sigma) < TOL64, s
         gpu, ora, _ = _void_sets(eng, ref, sample=s)
         assert gpu == ora, s
         assert abs(r["final_drop"][s] - ref["final_drop"]) <= 1e-6 * ref["final_drop"], s
@@ -544,4 +543,22 @@ def test_monte_carlo_1024_samples():
     # every sample's TTF and final drop compared; void sets on all but the
     # trees with a near-tied node choice
     assert n_finite >= 5 and n_trees >= 10 * 16 - 5
+    eng.close()
+
+
+def test_grid_barrier_wait_runs_out_and_context_recovers():
+    """A grid-barrier wait of the cooperative multigrid PCG limited to one
+    poll gives up: every block returns, the solve reports EMS_E_TIMEOUT; with
+    the default limit restored the same context solves correctly."""
+    from paper_2604_10743_gb300 import EmsError
+    g = es.mid_grid(N=128, with_map=False)          # 16,320 unknowns, one sample: the cooperative grid solver
+    eng = _engine(es.default_params(), g)
+    eng.set_wait_limit(1)
+    with pytest.raises(EmsError) as e:
+        eng.ir_solve()
+    assert e.value.status == 6
+    eng.set_wait_limit(0)
+    u, d = eng.ir_solve()
+    uo = F.ir_solve(g, g["seg_R0"])
+    assert np.abs(u[0] - uo).max() < 1e-11
     eng.close()
