@@ -300,8 +300,18 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
 // team larger than the chunk length allows moves to a longer chunk; chains
 // too long for any chunk fall back to the single-thread tree path.
 // EMS_CHAIN_M (environment) pins M for tuning.
-void chain_shape(int64_t n, int prec, int *T, int *M) {
+void chain_shape(int64_t n, int prec, int method, int *T, int *M, int *CL) {
     const int64_t target = prec == EMS_F32 ? 448 : 192;
+    *CL = 1;
+    // FP32 backward-Euler chains longer than one register-resident CTA holds:
+    // a cluster of 2, 4 or 8 CTAs of <= 320 threads, 16 nodes per thread
+    if (prec == EMS_F32 && method == EMS_BE && n > 320 * 16 && !getenv("EMS_NO_CLUSTER")) {
+        const int64_t th = (n + 15) / 16;
+        for (int cl : {2, 4, 8}) {
+            const int64_t t = ((th + cl - 1) / cl + 31) / 32 * 32;
+            if (t <= 320) { *T = (int)(t * cl); *M = 16; *CL = cl; return; }
+        }
+    }
     // FP32 chains the register-resident kernel holds: 16 nodes per thread
     // (<= 320 threads) for long chains, 8 (<= 576 threads) for short ones
     if (prec == EMS_F32) {
@@ -428,10 +438,10 @@ ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Pl
     int64_t P = 0;
     for (int t = 0; t < pl.tr.n_trees; ++t) {
         int64_t n = pl.tr.off[t + 1] - pl.tr.off[t];
-        int T = 0, M = 0;
-        if (pl.tr.is_chain[t]) chain_shape(n, p->precision, &T, &M);
+        int T = 0, M = 0, CL = 1;
+        if (pl.tr.is_chain[t]) chain_shape(n, p->precision, p->method, &T, &M, &CL);
         TreePack tp;
-        if (T > 0) { tp.T = T; tp.M = M; tp.pbase = P; P += (int64_t)T * M; }
+        if (T > 0) { tp.T = T; tp.M = M; tp.CL = CL; tp.pbase = P; P += (int64_t)T * M; }
         else { tp.T = 1; tp.M = (int)n; tp.pbase = P; P += (n + 31) / 32 * 32; }
         pl.pack[t] = tp;
     }
@@ -751,11 +761,13 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
         bool ch = pl.pack[t].T > 1;
         Bucket *bk = nullptr;
         for (auto &b : c->buckets)
-            if (b.chain == ch && (!ch || (b.T == pl.pack[t].T && b.M == pl.pack[t].M))) bk = &b;
+            if (b.chain == ch && (!ch || (b.T == pl.pack[t].T && b.M == pl.pack[t].M && b.CL == pl.pack[t].CL)))
+                bk = &b;
         if (!bk) {
             c->buckets.push_back(Bucket{});
             bk = &c->buckets.back();
             bk->chain = ch; bk->T = ch ? pl.pack[t].T : 1; bk->M = ch ? pl.pack[t].M : 0;
+            bk->CL = ch ? pl.pack[t].CL : 1;
         }
         bk->trees.push_back(t);
     }

@@ -99,10 +99,12 @@ struct HostTrees {
 struct TreePack {
     int T, M;          // threads per tree and chunk length (T = 1 for branched)
     int64_t pbase;     // packed base (within one sample)
+    int CL = 1;        // CTAs per tree (a thread-block cluster when > 1; T counts all of them)
 };
 
 struct Bucket {        // trees launched together: same precision kernel, T and M
     int T, M;
+    int CL = 1;        // CTAs per tree: T / CL threads each
     bool chain;
     std::vector<int32_t> trees;
     int32_t *d_trees = nullptr;

@@ -25,6 +25,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "ems_device.cuh"
 #include "ems_internal.cuh"
 
@@ -944,6 +946,470 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident FP32 chain kernel over a thread-block cluster.  A chain
+// longer than one CTA holds (5,120 nodes at 16 per thread) is split over CL
+// CTAs of one cluster: team thread g = rank * T + c owns nodes [16 g, 16 g +
+// 16) in the same chunk layout as the one-CTA kernel (team size CL T).  The
+// arithmetic of a step is k_chain_reg's; what crosses CTAs goes through
+// distributed shared memory after a cluster barrier: the chunk scans' CTA
+// aggregates (forward, then backward), the boundary stresses for the next
+// step's halo and the nucleation / guard flags, the cluster-wide argmax and
+// threshold minimum of a nucleation, and the factorisation's 2 x 2 product
+// scan.  Every CTA keeps an identical copy of the tree's void list; a void's
+// volume is accumulated and stored by the CTA that owns its node.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+struct ClSlots {                      // per-CTA words read by the other CTAs of the cluster
+    float fA, fB, bA, bB;             // forward / backward aggregates of this CTA's chunks
+    float first, last;                // stresses at this CTA's first and last node (halo)
+    int flags;                        // bit 0: a node reached its threshold, bit 1: a node is near the guard
+    double best;                      // argmax of sigma - sigma_crit over this CTA (nucleation)
+    int arg;
+    double tmin;                      // lowest threshold over this CTA
+    double fm[4];                     // factorisation: this CTA's product of 2 x 2 chunk matrices
+};
+
+// cluster-wide composition of affine maps x -> A + B x in rank order (fwd:
+// ranks < r left to right) or reverse (bwd: ranks > r right to left), applied to 0
+__device__ __forceinline__ float cl_carry_fwd(cg::cluster_group &cl, ClSlots *sl, int rank) {
+    float z = 0.0f;
+    for (int q = 0; q < rank; ++q) {
+        const ClSlots *o = cl.map_shared_rank(sl, q);
+        z = fmaf(o->fB, z, o->fA);
+    }
+    return z;
+}
+__device__ __forceinline__ float cl_carry_bwd(cg::cluster_group &cl, ClSlots *sl, int rank, int CL) {
+    float x = 0.0f;
+    for (int q = CL - 1; q > rank; --q) {
+        const ClSlots *o = cl.map_shared_rank(sl, q);
+        x = fmaf(o->bB, x, o->bA);
+    }
+    return x;
+}
+
+// exclusive scan of the chunk maps within the CTA (one barrier), with the
+// CTA's carry-in composed in: returns the carry entering this thread's chunk
+// and (thread 0 of the CTA, once all threads passed the barrier) the CTA's
+// aggregate map in *aggA, *aggB.  dir 0: left to right, 1: right to left.
+template <int DIR>
+__device__ __forceinline__ void cta_scan(float A, float B, float *sA, float *sB, float &exA, float &exB,
+                                         float &aggA, float &aggB) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // inclusive warp scan
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float Ao = DIR == 0 ? __shfl_up_sync(full, A, d) : __shfl_down_sync(full, A, d);
+        const float Bo = DIR == 0 ? __shfl_up_sync(full, B, d) : __shfl_down_sync(full, B, d);
+        if (DIR == 0 ? lane >= d : lane + d < 32) { A = fmaf(B, Ao, A); B = B * Bo; }
+    }
+    const int edge = DIR == 0 ? 31 : 0;
+    if (lane == edge) { sA[DIR * 32 + w] = A; sB[DIR * 32 + w] = B; }
+    __syncthreads();
+    // composite of the earlier warps (fwd: warps < w; bwd: warps > w), as a map
+    const int k = DIR == 0 ? lane : nw - 1 - lane;
+    const bool take = DIR == 0 ? k < w : k > w;
+    float a = take && k >= 0 && k < nw ? sA[DIR * 32 + k] : 0.0f, b = take && k >= 0 && k < nw ? sB[DIR * 32 + k] : 1.0f;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float ao = __shfl_up_sync(full, a, d), bo = __shfl_up_sync(full, b, d);
+        if (lane >= d) { a = fmaf(b, ao, a); b = b * bo; }
+    }
+    const float cwA = __shfl_sync(full, a, 31), cwB = __shfl_sync(full, b, 31);
+    // this thread's exclusive map within the CTA: (earlier lanes) o (earlier warps)
+    const float iA = fmaf(B, cwA, A), iB = B * cwB;            // inclusive
+    const float pA = DIR == 0 ? __shfl_up_sync(full, iA, 1) : __shfl_down_sync(full, iA, 1);
+    const float pB = DIR == 0 ? __shfl_up_sync(full, iB, 1) : __shfl_down_sync(full, iB, 1);
+    const int first = DIR == 0 ? 0 : 31;
+    exA = lane == first ? cwA : pA;
+    exB = lane == first ? cwB : pB;
+    // the CTA aggregate (every warp's map composed), thread 0
+    aggA = 0.0f; aggB = 1.0f;
+    if (threadIdx.x == 0) {
+        if (DIR == 0)
+            for (int q = 0; q < nw; ++q) { aggA = fmaf(sB[q], aggA, sA[q]); aggB = sB[q] * aggB; }
+        else
+            for (int q = nw - 1; q >= 0; --q) { aggA = fmaf(sB[32 + q], aggA, sA[32 + q]); aggB = sB[32 + q] * aggB; }
+    }
+}
+
+// Cluster version of chain_factor (increment form, R = float): every CTA
+// calls it; g = team thread, TT = team size.  Two cluster barriers.
+template <int M>
+__device__ __noinline__ void chain_factor_cl(const ChainArgs<float> &a, double dt, int n, int TT, int g, int64_t cb,
+                                             int64_t cs, int64_t ps, ClSlots *sl, int rank) {
+    using R = float;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double sfm[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    auto node = [&](int i, double &d, double &em, double &ep, bool &is_void) {
+        const double gl = i > 0 ? a.g[cs + i] : 0.0, gr = i + 1 < n ? a.g[cs + i + 1] : 0.0;
+        is_void = isinf(a.thr[cs + i]);
+        d = __fma_rn(dt, __dadd_rn(gl, gr), a.V[cb + i]);
+        if (is_void) d = __fma_rn(dt, a.leak[cs + i], d);
+        em = -__dmul_rn(dt, gl);
+        ep = -__dmul_rn(dt, gr);
+    };
+    M2 P{1.0, 0.0, 0.0, 1.0};
+    for (int k = 0; k < M; ++k) {
+        const int i = g * M + k;
+        if (i >= n) break;
+        double d, em, ep;
+        bool v;
+        node(i, d, em, ep, v);
+        P = m2mul(M2{d, -__dmul_rn(em, em), 1.0, 0.0}, P);
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const M2 o = m2shfl_up(P, d);
+        if (lane >= d) P = m2mul(P, o);
+    }
+    if (lane == 31) { sfm[0][w] = P.a; sfm[1][w] = P.b; sfm[2][w] = P.c; sfm[3][w] = P.d; }
+    __syncthreads();
+    M2 Cw{1.0, 0.0, 0.0, 1.0};
+    for (int k = 0; k < w; ++k) Cw = m2mul(M2{sfm[0][k], sfm[1][k], sfm[2][k], sfm[3][k]}, Cw);
+    if (threadIdx.x == 0) {
+        M2 Ag{1.0, 0.0, 0.0, 1.0};
+        for (int k = 0; k < nw; ++k) Ag = m2mul(M2{sfm[0][k], sfm[1][k], sfm[2][k], sfm[3][k]}, Ag);
+        sl->fm[0] = Ag.a; sl->fm[1] = Ag.b; sl->fm[2] = Ag.c; sl->fm[3] = Ag.d;
+    }
+    cl.sync();
+    // product of the earlier CTAs' aggregates (later on the left)
+    M2 Qc{1.0, 0.0, 0.0, 1.0};
+    for (int q = 0; q < rank; ++q) {
+        const ClSlots *o = cl.map_shared_rank(sl, q);
+        Qc = m2mul(M2{o->fm[0], o->fm[1], o->fm[2], o->fm[3]}, Qc);
+    }
+    const M2 CwT = m2mul(Cw, Qc);
+    const M2 incl = m2mul(P, CwT);
+    const M2 prev = m2shfl_up(incl, 1);
+    const M2 Q = lane == 0 ? CwT : prev;
+    double pprev = g == 0 ? 0.0 : __ddiv_rn(Q.c, Q.a);
+    for (int k = 0; k < M; ++k) {
+        const int i = g * M + k;
+        if (i >= n) break;
+        double d, em, ep;
+        bool is_void;
+        node(i, d, em, ep, is_void);
+        const double p = __drcp_rn(__fma_rn(-__dmul_rn(em, em), pprev, d));
+        const int64_t pk = ps + (int64_t)k * TT + g;
+        a.pinv[pk] = p;
+        a.alpha[pk] = (R)p;
+        a.dtg[pk] = (R)(-em);
+        a.dtl[pk] = is_void ? (R)(dt * a.leak[cs + i]) : R(0);
+        a.gam[pk] = (R)(p * em);
+        a.uu[pk] = (R)(p * ep);
+        pprev = p;
+    }
+    cl.sync();                          // dt g of the next chunk may belong to another CTA
+    R acc = R(1);
+    for (int k = 0; k < M; ++k) {
+        const int64_t pk = ps + (int64_t)k * TT + g;
+        const int i = g * M + k;
+        a.beta[pk] = i < n ? (R)(dt * a.f[cs + i]) : R(0);
+        acc *= a.alpha[pk] * a.dtg[pk];
+        a.Pf[pk] = acc;
+    }
+    acc = R(1);
+    for (int k = M - 1; k >= 0; --k) {
+        const int64_t pk = ps + (int64_t)k * TT + g;
+        const R gn = k + 1 < M ? a.dtg[pk + TT] : (g + 1 < TT ? a.dtg[ps + g + 1] : R(0));
+        acc *= a.alpha[pk] * gn;
+        a.Pb[pk] = acc;
+    }
+}
+
+template <int CL>
+__global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
+    constexpr int M = 16;
+    using R = float;
+    __shared__ R sA[64], sB[64], sL[32], sR[32];
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ int s_nv;
+    __shared__ int s_node[EMS_MAX_VOIDS];
+    __shared__ double s_vol[EMS_MAX_VOIDS], s_coef[EMS_MAX_VOIDS];
+    __shared__ double s_dt, s_tbase, s_gthr;
+    __shared__ int s_rs, s_sbase, s_refac;
+    __shared__ ClSlots sl;
+    cg::cluster_group cl = cg::this_cluster();
+
+    const int rank = (int)cl.block_rank();
+    const int t = a.trees[blockIdx.x / CL], s = blockIdx.y;
+    const int T = blockDim.x, c = threadIdx.x, TT = T * CL, g = rank * T + c;
+    const int lane = c & 31, w = c >> 5, nw = T >> 5;
+    const int64_t cb = a.toff[t];
+    const int n = (int)(a.toff[t + 1] - cb);
+    const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
+    const int64_t st = (int64_t)s * a.n_trees + t;
+    const int sm = a.sched[st];
+    if (a.kr_mode[st] || sm < 0) return;        // uniform over the cluster: every CTA returns
+    const int kd = a.kdone[st];
+    auto owner = [&](int v) { return (v / M) / T; };   // rank holding node v
+
+    // cluster-wide lowest threshold
+    auto thr_min = [&]() -> double {
+        double tm = INFINITY;
+        for (int i = g; i < n; i += TT) tm = fmin(tm, a.thr[cs + i]);
+        tm = block_min(tm, sv);
+        if (c == 0) sl.tmin = tm;
+        cl.sync();
+        double r = INFINITY;
+        for (int q = 0; q < CL; ++q) r = fmin(r, cl.map_shared_rank(&sl, q)->tmin);
+        cl.sync();                               // tmin may be rewritten next time
+        return r;
+    };
+    double thrmin = thr_min();
+    R sg[M], cc[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) { sg[k] = a.sig[ps + (int64_t)k * TT + g]; cc[k] = R(0); }
+
+    int rs = sm > 1 ? sm : 1;
+    if ((a.n_steps - kd) % rs) rs = 1;
+    if (rs > 1) {
+        const int nr = __syncthreads_or(near_guard<R, M>(sg, a.guard * thrmin));
+        if (c == 0) sl.flags = nr ? 2 : 0;
+        cl.sync();
+        int any = 0;
+        for (int q = 0; q < CL; ++q) any |= cl.map_shared_rank(&sl, q)->flags;
+        cl.sync();
+        if (any & 2) {
+            rs = 1;
+            if (g == 0) a.sched[st] = 0;
+        }
+    }
+    int n_steps = (a.n_steps - kd) / rs;
+    if (c == 0) {
+        const double dt = a.dt * rs;
+        s_dt = dt;
+        s_rs = rs;
+        s_gthr = a.guard * thrmin;
+        s_sbase = 0;
+        s_tbase = (a.t0p ? *a.t0p : a.t0) + kd * a.dt;
+        const int nv = a.v_count[st];
+        s_nv = nv;
+        for (int q = 0; q < nv; ++q) {
+            const int v = a.v_node[st * a.maxv + q];
+            s_node[q] = v;
+            s_vol[q] = a.v_vol[st * a.maxv + q];
+            s_coef[q] = dt * a.Binv * a.leak[cs + v];
+        }
+        s_refac = (a.refactor_all || a.dirty[st] || a.fdt[st] != dt) ? 1 : 0;
+    }
+    cl.sync();                                   // every CTA has read dirty / fdt
+    if (g == 0) { a.dirty[st] = 0; a.fdt[st] = s_dt; }
+    if (s_refac) {
+        chain_factor_cl<M>(a, s_dt, n, TT, g, cb, cs, ps, &sl, rank);
+    } else {
+        const double dt = s_dt;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int i = g * M + k;
+            a.beta[ps + (int64_t)k * TT + g] = i < n ? (R)(dt * a.f[cs + i]) : R(0);
+        }
+    }
+
+    R cp[M], cg_[M], cbt[M], cpf[M], cpb[M], cth[M], g_next;
+    unsigned vmask = 0u;
+    auto load = [&]() {
+        cl.sync();                               // coefficients of every CTA written
+        vmask = 0u;
+        for (int q = 0; q < s_nv; ++q)
+            if (s_node[q] / M == g) vmask |= 1u << (s_node[q] % M);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int64_t pk = ps + (int64_t)k * TT + g;
+            const int i = g * M + k;
+            cp[k] = a.alpha[pk];
+            cg_[k] = a.dtg[pk];
+            cbt[k] = a.beta[pk];
+            cpf[k] = a.Pf[pk];
+            cpb[k] = a.Pb[pk];
+            cth[k] = ((vmask >> k) & 1u) ? a.dtl[pk] : (i < n ? __double2float_rd(a.thr[cs + i]) : INFINITY);
+        }
+        g_next = g + 1 < TT ? a.dtg[ps + g + 1] : R(0);
+    };
+    load();
+
+    const unsigned full = 0xffffffffu;
+    // boundary stresses: warps in shared memory, the CTA's ends in its slots
+    auto publish = [&]() {
+        if (lane == 31) sL[w] = sg[M - 1];
+        if (lane == 0) sR[w] = sg[0];
+        if (c == 0) sl.first = sg[0];
+        if (c == T - 1) sl.last = sg[M - 1];
+    };
+    publish();
+    cl.sync();
+    for (int step = 0; step < n_steps; ++step) {
+        R left = __shfl_up_sync(full, sg[M - 1], 1);
+        R right = __shfl_down_sync(full, sg[0], 1);
+        if (lane == 0 && w > 0) left = sL[w - 1];
+        if (lane == 31 && w + 1 < nw) right = sR[w + 1];
+        if (c == 0) left = rank > 0 ? cl.map_shared_rank(&sl, rank - 1)->last : R(0);
+        if (c == T - 1) right = rank + 1 < CL ? cl.map_shared_rank(&sl, rank + 1)->first : R(0);
+        R gk = cg_[0];
+        R qprev = gk * (left - sg[0]);
+        R z = R(0);
+        R zr[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const R nxt = k + 1 < M ? sg[k + 1] : right;
+            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
+            const R qn = gk1 * (sg[k] - nxt);
+            R r = qprev - qn + cbt[k];
+            if ((vmask >> k) & 1u) r -= cth[k] * sg[k];
+            z = cp[k] * fmx(gk, z, r);
+            zr[k] = z;
+            qprev = qn;
+            gk = gk1;
+        }
+        // forward carries: within the CTA, then across the cluster
+        float exA, exB, agA, agB;
+        cta_scan<0>(z, cpf[M - 1], sA, sB, exA, exB, agA, agB);
+        if (c == 0) { sl.fA = agA; sl.fB = agB; }
+        cl.sync();
+        const float cf = fmaf(exB, cl_carry_fwd(cl, &sl, rank), exA);
+        R x = R(0);
+#pragma unroll
+        for (int k = M - 1; k >= 0; --k) {
+            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
+            x = fmx(cp[k] * gk1, x, fmx(cpf[k], cf, zr[k]));
+            zr[k] = x;
+        }
+        float bxA, bxB, bgA, bgB;
+        cta_scan<1>(x, cpb[0], sA, sB, bxA, bxB, bgA, bgB);
+        if (c == 0) { sl.bA = bgA; sl.bB = bgB; }
+        cl.sync();
+        const float cr = fmaf(bxB, cl_carry_bwd(cl, &sl, rank, CL), bxA);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const R y = fmx(cpb[k], cr, zr[k]) - cc[k];
+            const R tt = sg[k] + y;
+            cc[k] = (tt - sg[k]) - y;
+            sg[k] = tt;
+        }
+        // void growth by the Robin leak (owner thread only)
+        if (vmask) {
+            for (int q = 0; q < s_nv; ++q) {
+                const int v = s_node[q];
+                if (v / M == g) {
+                    R val = R(0);
+#pragma unroll
+                    for (int k = 0; k < M; ++k)
+                        if (v % M == k) val = sg[k];
+                    s_vol[q] += s_coef[q] * (double)val;
+                }
+            }
+        }
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < M; ++k) hit |= !((vmask >> k) & 1u) && sg[k] >= cth[k];
+        const bool nr = s_rs > 1 && near_guard<R, M>(sg, s_gthr);
+        publish();
+        const int f = __syncthreads_or(hit) | (__syncthreads_or(nr) << 1);
+        if (c == 0) sl.flags = f;
+        cl.sync();
+        int any = 0;
+        for (int q = 0; q < CL; ++q) any |= cl.map_shared_rank(&sl, q)->flags;
+        int refac_from = -1;
+        if (any & 1) {
+            double best = -INFINITY;
+            int arg = 0x7fffffff;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int i = g * M + k;
+                if (i < n) {
+                    const double m = (double)sg[k] - a.thr[cs + i];
+                    if (m > best) { best = m; arg = i; }
+                }
+            }
+            block_argmax(best, arg, sv, si);
+            cl.sync();                           // the flags were read; slots may change
+            if (c == 0) { sl.best = best; sl.arg = arg; }
+#pragma unroll
+            for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * TT + g] = sg[k];
+            cl.sync();
+            best = -INFINITY; arg = 0x7fffffff;
+            for (int q = 0; q < CL; ++q) {
+                const ClSlots *o = cl.map_shared_rank(&sl, q);
+                if (o->best > best || (o->best == best && o->arg < arg)) { best = o->best; arg = o->arg; }
+            }
+            if (best >= 0.0) {
+                const int v = arg;
+                if (c == 0) {
+                    const int nv = s_nv;
+                    if (rank == owner(v)) {
+                        const double dt = s_dt;
+                        auto S_ = [&](int i) { return (double)a.sig[ps + (int64_t)(i % M) * TT + i / M]; };
+                        const double gl = v > 0 ? a.g[cs + v] : 0.0, gr = v + 1 < n ? a.g[cs + v + 1] : 0.0;
+                        double acc = (a.V[cb + v] + dt * (gl + gr)) * S_(v);
+                        if (v > 0) acc -= dt * gl * S_(v - 1);
+                        if (v + 1 < n) acc -= dt * gr * S_(v + 1);
+                        const double s0 = (acc - dt * a.f[cs + v]) / a.V[cb + v];
+                        const double m0 = s0 - a.thr[cs + v];
+                        const double frac = m0 < 0.0 ? -m0 / (best - m0) : 0.0;
+                        if (nv < a.maxv) {
+                            const int64_t e = st * a.maxv + nv;
+                            a.v_node[e] = v;
+                            a.v_seg[e] = void_segment<R>(a, s, cb + v);
+                            a.v_tnuc[e] = s_tbase + ((double)(step - s_sbase) + frac) * dt;
+                            a.v_vol[e] = 0.0;
+                            a.v_count[st] = nv + 1;
+                            atomicAdd(&a.counters[0], 1);
+                        } else {
+                            atomicOr(&a.status[kStatusOverflow], 1);
+                        }
+                        a.thr[cs + v] = INFINITY;
+                    }
+                    if (nv < a.maxv) {                  // every CTA's copy of the void list
+                        s_node[nv] = v; s_vol[nv] = 0.0; s_coef[nv] = s_dt * a.Binv * a.leak[cs + v];
+                        s_nv = nv + 1;
+                    }
+                }
+                refac_from = arg;
+            }
+        }
+        bool promoted = false;
+        if (any & 2) {
+            n_steps = step + 1 + (n_steps - step - 1) * s_rs;
+            promoted = true;
+            __syncthreads();
+            if (c == 0) {
+                s_tbase += (double)(step + 1 - s_sbase) * s_dt;
+                s_sbase = step + 1;
+                s_dt = a.dt;
+                s_rs = 1;
+                for (int q = 0; q < s_nv; ++q) s_coef[q] = a.dt * a.Binv * a.leak[cs + s_node[q]];
+                if (rank == 0) { a.sched[st] = 0; a.fdt[st] = a.dt; }
+            }
+            refac_from = 0;
+        }
+        if (refac_from >= 0) {
+            cl.sync();                           // the new threshold is written; every CTA is here
+            const double dtf = promoted ? a.dt : s_dt;
+            chain_factor_cl<M>(a, dtf, n, TT, g, cb, cs, ps, &sl, rank);
+            thrmin = thr_min();
+            if (c == 0) s_gthr = a.guard * thrmin;
+            load();
+        }
+        cl.sync();                               // slots read by every CTA before they change
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * TT + g] = sg[k];
+    __syncthreads();
+    if (c == 0) {
+        for (int q = 0; q < s_nv; ++q)
+            if (owner(s_node[q]) == rank) a.v_vol[st * a.maxv + q] = s_vol[q];
+        if (rank == 0) atomicAdd(a.work, (unsigned long long)n * (unsigned long long)n_steps);
+    }
+    cl.sync();                                   // no CTA leaves while another may read its slots
+}
+
+// ---------------------------------------------------------------------------
 // Branched trees: one thread per (tree, sample), leaf-to-root elimination.
 // Packed layout == canonical order.  pinv holds 1/d', gam holds l = e/d',
 // uu holds e, beta is the right-hand-side scratch.
@@ -1214,6 +1680,28 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
         ChainArgs<R> a = chain_args<R>(c, dt, n_steps);
         a.trees = b.d_trees;
         a.n_bucket = (int)b.trees.size();
+        if (b.chain && b.CL > 1) {
+            // one thread-block cluster of CL CTAs per (tree, sample)
+            if constexpr (kDelta) {
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = b.CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3((unsigned)(b.trees.size() * b.CL), c->S);
+                cfg.blockDim = dim3(b.T / b.CL);
+                cfg.stream = c->stream;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                cudaError_t e = b.CL == 2 ? cudaLaunchKernelEx(&cfg, k_chain_cl<2>, a)
+                              : b.CL == 4 ? cudaLaunchKernelEx(&cfg, k_chain_cl<4>, a)
+                                          : cudaLaunchKernelEx(&cfg, k_chain_cl<8>, a);
+                EMS_CUDA(c, e);
+                ++c->launches;
+                continue;
+            } else {
+                return fail(c, EMS_E_STATE, "cluster chain layout needs the FP32 path");
+            }
+        }
         if (b.chain) {
             dim3 grid((unsigned)b.trees.size(), c->S);
             cudaError_t e = cudaSuccess;

@@ -562,3 +562,34 @@ def test_grid_barrier_wait_runs_out_and_context_recovers():
     uo = F.ir_solve(g, g["seg_R0"])
     assert np.abs(u[0] - uo).max() < 1e-11
     eng.close()
+
+
+@pytest.mark.parametrize("cells,cl", [(1462, 2), (2924, 4), (5000, 8)])
+def test_cluster_chain_kernel_against_oracle(cells, cl):
+    """FP32 stripes longer than one CTA holds run on a thread-block cluster
+    of 2, 4 or 8 CTAs (10,235 / 20,469 / 35,001 nodes); a low critical stress
+    makes voids nucleate in every CTA of a cluster, so the cluster-wide
+    argmax, the shared void list and the refactor across CTAs all run."""
+    from paper_2604_10743_gb300 import EMS_F32
+    g = es.stripe_mesh(8, 20e-6)
+    g["seg_cells"][:] = cells
+    t = es.tiny_grid()
+    g["pad_node"], g["pad_V"], g["sink_node"], g["sink_I"] = t["pad_node"], t["pad_V"], t["sink_node"], t["sink_I"]
+    g["thermal"] = es.hotspot_raster(np.random.default_rng(cells), 140e-6, 2, 360.0, 20.0, 40.0, 0.2, nx=33, ny=33)
+    p = es.default_params(n_outer=3, n_inner=64, sigma_crit=250e6)
+    eng = _engine(p, g, precision=EMS_F32, max_voids=64)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True, n_threads=8)
+    assert ref["n_voids"] >= 16
+    # voids spread over the CTAs of the clusters
+    n = 7 * cells + 1
+    T = ((n + 15) // 16 + cl - 1) // cl
+    T = (T + 31) // 32 * 32
+    ranks = {int(((v - ref["trees"]["off"][np.searchsorted(ref["trees"]["off"], v, side="right") - 1]) // 16) // T)
+             for v in ref["void_nodes"]}
+    assert len(ranks) >= 2
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+    nt, nv = _f32_voids(eng, ref)
+    assert nt >= 1
+    _metric_close(r, ref)
+    eng.close()
