@@ -1,17 +1,24 @@
 #!/usr/bin/env python
-"""Benchmark: stress node-steps/s of the full coupled EM/TM/IR aging run.
+"""Benchmark: stress node-steps/s of the coupled EM/TM/IR aging run on the full chip.
 
-One step = one full time-to-failure run (64 aging steps x 256 backward-Euler
-steps over every tree, IR re-solves, nucleation, void growth, resistance
-write-back) of the 256 x 256-stripe two-layer mesh: 512 trees x 5,101 nodes =
-2,611,712 stress nodes with a 3-hotspot thermal map, so 4.28e10 node-steps.
+Workload: the 2048 x 2048-stripe two-layer mesh at 5 um (4,096 stripes x
+20,471 stress nodes = 83.8 M, 4.19 M IR nodes, 5 % lognormal sinks, 8
+hotspots) with a batch of Monte Carlo samples (20 % CoV kappa / sigma_crit
+per segment) held at once; per-node coefficients are rebuilt in windows of
+samples.  One step = one aging step of every sample: 256 backward-Euler
+steps of every stripe, nucleation, void growth, resistance write-back, IR
+re-solve, drop.  The line also carries the plain-vs-chosen comparison
+(whole-horizon TTF runs of one sample, FP64 plain against the FP32 path),
+the roofline of the dominant kernel, the CPU oracle on a bounded sample and
+an end-to-end number through the public API.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--samples S] [--window W]
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (the
 trees and samples are independent; no collective on the data path) and
-rank 0 prints the aggregate.  --impl reference times the CPU oracle on the
-same workload (bounded sample per step) on this host's cores.
+rank 0 prints the aggregate.  --impl reference times the CPU oracle on a
+bounded sample of the same workload on this host's cores.
 """
 import argparse
 import json
@@ -26,9 +33,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "stress node-steps/s; full-chip TTF time at <=0.05% TTF error, plain vs chosen"
-WORKLOAD = ("256x256-stripe two-layer Cu mesh: 512 trees x 5,101 stress nodes (2,611,712), "
-            "10 um segments, dx 0.5 um, 64 pads, 1,311 lognormal sinks, 340 K + 3 x 40 K hotspot map; "
-            "64 aging steps x 256 BE steps over a 10-year horizon per TTF run")
+WORKLOAD = ("2048x2048-stripe two-layer Cu mesh at 5 um (the full chip): 4,096 trees x 20,471 stress nodes "
+            "(83.8 M), 4.19 M IR nodes, a pad every 32 crossings, 5 %% lognormal sinks, 330 K + 8 hotspots; "
+            "%d Monte Carlo samples (20 %% CoV kappa and sigma_crit per segment) held at once, coefficients "
+            "rebuilt in windows of %d samples; one step = one aging step (256 BE steps, void update, IR re-solve) "
+            "of every sample")
 
 
 def _dist():
@@ -119,6 +128,23 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def _finite(o):
+    """JSON-safe copy: non-finite floats (a censored TTF is +inf) become null."""
+    if isinstance(o, float):
+        return o if math.isfinite(o) else None
+    if isinstance(o, dict):
+        return {k: _finite(v) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [_finite(v) for v in o]
+    return o
+
+
+def full_chip(n_samples, seed=5):
+    """The 2048 x 2048 full chip with n_samples Monte Carlo factor sets."""
+    import ems_synth as es
+    return es.grid.large_grid(seed=seed, n_samples=n_samples)
+
+
 def run_mine(args):
     import numpy as np
     import torch
@@ -132,18 +158,21 @@ def run_mine(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    g = es.mid_grid()
+    S, W = args.samples, args.window
     p = es.default_params()
     prec = EMS_F32 if args.precision == "f32" else EMS_F64
-    eng = Engine(p, g, precision=prec)
-    init = eng.state_export()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB L2
+    g = full_chip(S)
+    t0 = time.perf_counter()
+    eng = Engine(p, g, precision=prec, max_voids=args.max_voids, window=W)
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
 
+    # one step = one aging step (256 BE steps of every tree of every sample,
+    # void update, IR re-solve, drop) of the whole Monte Carlo batch; steps
+    # follow each other along the horizon (warm-up steps included)
     def one():
-        eng.state_import(init)
-        flush.fill_(1)
-        return eng.ttf()
+        return eng.ttf(n_outer=1)
 
     for _ in range(args.warmup):
         one()
@@ -155,11 +184,12 @@ def run_mine(args):
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    stress_ms = 0.0
+    stress_ms = ir_ms = 0.0
     res = None
     for _ in range(args.steps):
         res = one()
         stress_ms += res["stress_ms"]
+        ir_ms += res["ir_ms"]
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -168,18 +198,20 @@ def run_mine(args):
     if world > 1:
         ms = max_over_ranks(ms, dist, "cuda")
         dist.barrier()
-    node_steps = res["node_steps"]
+    node_steps = res["node_steps"]                      # per step: nodes x samples x 256
     value = job_value(node_steps, args.steps, world, ms)
+    n_win = (S + W - 1) // W if 0 < W < S else 1
+    voids = int(np.asarray(res["n_voids"]).sum())
 
-    # dominant kernel: the chain stress kernel; one launch advances every tree
-    # by n_inner steps.  Algorithmic bytes per node-step: state in + out (2w)
-    # plus the per-launch coefficient arrays amortised over the inner steps.
+    # dominant kernel: the cluster chain kernel (one launch = 256 BE steps of
+    # every tree of one window of samples).  Algorithmic bytes per node-step:
+    # state in + out (2w), plus the per-launch coefficient arrays.
     w = 4 if prec == EMS_F32 else 8
-    n_nodes = eng.n_stress
     n_inner = p["n_inner"]
     n_coef = 7 if prec == EMS_F32 else 6
-    alg_bytes_launch = n_nodes * (2 * w * n_inner + n_coef * w)
-    per_launch_ms = stress_ms / (args.steps * p["n_outer"])
+    nodes_launch = eng.n_stress * (S / n_win)
+    alg_bytes_launch = nodes_launch * (2 * w * n_inner + n_coef * w)
+    per_launch_ms = stress_ms / (args.steps * n_win)
     peaks, src = _peaks()
     achieved = alg_bytes_launch / (per_launch_ms / 1e3) / 1e9
     traffic = None
@@ -187,69 +219,61 @@ def run_mine(args):
     if os.path.exists(tf):
         try:
             t = json.load(open(tf))
-            if t.get("precision") == args.precision:
+            if t.get("precision") == args.precision and t.get("kernel") == "k_chain_cl<4>":
                 traffic = t.get("bytes_per_launch")
         except (OSError, ValueError):
             pass
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src if src == "measured" else "fallback 6.8 TB/s",
-            "kernel": "k_chain_reg<16> (stress advance, one launch = 256 BE steps of all trees)",
-            "alg_bytes_per_launch": alg_bytes_launch, "launch_ms": round(per_launch_ms, 4)}
+            "kernel": "k_chain_cl<4> (stress advance: one 4-CTA cluster per (stripe, sample), one launch = "
+                      "256 BE steps of every stripe of %d samples)" % (S // n_win),
+            "alg_bytes_per_launch": int(alg_bytes_launch), "launch_ms": round(per_launch_ms, 3)}
 
-    # end to end through the public API with host buffers: load the netlist
-    # and map from host arrays, run, read the TTF results back
+    # end to end through the public API with host buffers: the netlist, the
+    # map and the factor sets copied in, then aging steps with every step's
+    # drops and TTF read back
     e2e = None
     if not args.no_e2e:
-        th = g["thermal"]
+        eng.close()
         h2d = sum(np.asarray(g[k]).nbytes for k in ("node_x", "node_y", "seg_a", "seg_b", "seg_layer",
                                                       "seg_cells", "seg_R0", "seg_W", "seg_H", "seg_L",
-                                                      "pad_node", "pad_V", "sink_node", "sink_I"))
-        h2d += th["T"].nbytes
+                                                      "pad_node", "pad_V", "sink_node", "sink_I",
+                                                      "kappa_factor", "sigc_factor"))
+        h2d += g["thermal"]["T"].nbytes
+        ke = 3
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ke = max(1, min(args.steps, 2))
+        e = Engine(p, g, precision=prec, max_voids=args.max_voids, window=W)
         for _ in range(ke):
-            e = Engine(p, g, precision=prec)
-            r = e.ttf()
-            e.close()
+            r = e.ttf(n_outer=1)                      # results come back to the host
         torch.cuda.synchronize()
-        dt_e = (time.perf_counter() - t0) / ke
-        d2h = 8 * 3 + 4 + 8 * (p["n_outer"] + 1)
-        e2e = {"value": node_steps * world / dt_e, "unit": "node-steps/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "s_per_step": round(dt_e, 4)}
+        dt_e = time.perf_counter() - t0
+        e.close()
+        d2h = S * (8 * 3 + 4 + 8 * 2)
+        e2e = {"value": node_steps * ke * world / dt_e, "unit": "node-steps/s",
+               "h2d_bytes_per_step": int(h2d / ke), "d2h_bytes_per_step": int(d2h),
+               "s_total": round(dt_e, 2), "steps": ke,
+               "note": "one context built from host arrays (netlist, map, %d factor sets), then %d aging steps "
+                       "with results read back each step; the load is spread over the steps" % (S, ke)}
+    else:
+        eng.close()
 
-    # plain method (FP64 backward Euler, no screen) for the TTF-time comparison
-    plain = None
-    if not args.no_plain and prec != EMS_F64:
-        ep = Engine(p, g, precision=EMS_F64)
-        ip = ep.state_export()                     # fresh state
-        ep.ttf()                                   # warm
-        torch.cuda.synchronize()
-        ep.state_import(ip)
-        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        rp = ep.ttf()
-        a1.record(stream)
-        torch.cuda.synchronize()
-        pms = a0.elapsed_time(a1)
-        plain = {"ttf_s": float(rp["ttf"][0]), "final_drop": float(rp["final_drop"][0]),
-                 "ttf_wall_ms": round(pms, 2), "node_steps_per_s": rp["node_steps"] / (pms / 1e3)}
-        ep.close()
+    # plain vs chosen on the full chip: whole TTF runs of one Monte Carlo
+    # sample (the batch's first factor set): plain = FP64 backward Euler;
+    # chosen = the FP32 path timed above (cluster kernel, compensated sums)
+    pvc = None
+    if not args.no_plain:
+        pvc = plain_vs_chosen(p, args, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(g, p, 1)
+        cpu = cpu_baseline(p)
 
     mc = None
     if not args.no_mc:
         mc = mc_leg(p, peaks, src, stream)
-    krylov = None
-    if args.krylov:
-        krylov = krylov_leg(g, p, stream, res)
 
-    # learned surrogate: fused tensor-core inference over 4,096 trees x 1,024
-    # Monte Carlo samples (one schedule's worth of rows)
     surrogate = None
     if not args.no_surrogate:
         surrogate = surrogate_leg(peaks, src, stream, rows=args.surrogate_rows)
@@ -258,24 +282,96 @@ def run_mine(args):
         "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (stress, increment form) / f64 (IR PCG, nucleation time)" if prec == EMS_F32 else "f64",
+        "dtype": "f32 (stress, increment form, compensated sums) / f64 (IR PCG, nucleation time)"
+                 if prec == EMS_F32 else "f64",
         "data": "synthetic (seeded generator; the paper's SAED32 netlists and maps are not available)",
-        "config": {"workload": WORKLOAD, "trees": eng.n_trees, "stress_nodes": eng.n_stress,
-                   "node_steps_per_step": node_steps, "precision": args.precision,
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "256 MB buffer written between timed iterations (L2 flush)"},
-        "ttf_s": float(res["ttf"][0]), "final_drop": float(res["final_drop"][0]),
+        "config": {"workload": WORKLOAD % (S, W), "trees": eng.n_trees, "stress_nodes": eng.n_stress,
+                   "samples": S, "window_samples": W, "node_steps_per_step": node_steps,
+                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "no flush: the per-step working set (%d samples x 83.8 M nodes of state, %d samples of "
+                         "coefficients) is far larger than the 129 MB L2" % (S, S // n_win),
+                   "workspace_gb": round(eng.ws_bytes / 1e9, 2), "load_s": round(t_load, 1)},
         "stress_node_steps_per_s": node_steps * args.steps / (stress_ms / 1e3),
-        "ir_ms_per_step": res["ir_ms"], "ir_iterations_per_step": res["ir_iterations"],
-        "ttf_wall_ms": ms / args.steps, "plain_fp64": plain,
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "surrogate": surrogate, "monte_carlo": mc, "krylov": krylov,
+        "stress_ms_per_step": round(stress_ms / args.steps, 1), "ir_ms_per_step": round(ir_ms / args.steps, 1),
+        "voids_after_timed_steps": voids, "max_drop_after_timed_steps": float(np.max(res["final_drop"])),
+        "plain_vs_chosen": pvc, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "surrogate": surrogate, "monte_carlo": mc,
     }
     if rank == 0:
-        print(json.dumps(line))
-    eng.close()
+        print(json.dumps(_finite(line)))
     if world > 1:
         dist.destroy_process_group()
+
+
+def plain_vs_chosen(p, args, stream, n_samples=1):
+    """Full-chip TTF of the same sample(s), plain FP64 method against the
+    chosen FP32 path: wall time (CUDA events), TTF, final IR drop, errors."""
+    import numpy as np
+    import torch
+    from paper_2604_10743_gb300 import EMS_F32, EMS_F64
+    from paper_2604_10743_gb300.engine import Engine
+    g = full_chip(n_samples)
+    out = {}
+    for name, prec in (("chosen", EMS_F32), ("plain", EMS_F64)):
+        eng = Engine(p, g, precision=prec, max_voids=args.max_voids)
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        r = eng.ttf()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t = a0.elapsed_time(a1)
+        out[name] = {"ttf_s": [float(v) for v in r["ttf"]], "final_drop": [float(v) for v in r["final_drop"]],
+                     "ttf_wall_ms": round(t, 1), "stress_ms": round(r["stress_ms"], 1), "ir_ms": round(r["ir_ms"], 1),
+                     "voids": [int(v) for v in r["n_voids"]],
+                     "node_steps_per_s": r["node_steps"] / (t / 1e3),
+                     "precision": "f32" if prec == EMS_F32 else "f64"}
+        eng.close()
+    rc, rp = out["chosen"], out["plain"]
+    err = 0.0
+    for a, b in zip(rc["final_drop"], rp["final_drop"]):
+        err = max(err, abs(a - b) / b)
+    for a, b in zip(rc["ttf_s"], rp["ttf_s"]):
+        if math.isfinite(b):
+            err = max(err, abs(a - b) / b if math.isfinite(a) else math.inf)
+        elif math.isfinite(a):
+            err = math.inf
+    out["max_rel_err_ttf_and_final_drop"] = err
+    out["speedup"] = round(rp["ttf_wall_ms"] / rc["ttf_wall_ms"], 3)
+    out["samples"] = n_samples
+    out["workload"] = "2048x2048 full chip, %d Monte Carlo sample(s), whole 10-year horizon (64 x 256 BE steps)" % \
+        n_samples
+    return out
+
+
+def mid_grid_leg(args, stream):
+    """The 256 x 256-stripe mesh (512 trees x 5,101 nodes): full TTF runs
+    (64 x 256 BE steps) with inputs resident, FP32."""
+    import torch
+    import ems_synth as es
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300.engine import Engine
+    g, p = es.mid_grid(), es.default_params()
+    eng = Engine(p, g, precision=EMS_F32)
+    init = eng.state_export()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    r = None
+    for k in range(args.warmup + args.steps):
+        eng.state_import(init)
+        flush.fill_(1)
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        r = eng.ttf()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(a0.elapsed_time(a1))
+    t = sum(ms) / len(ms)
+    eng.close()
+    return {"workload": "256x256 mesh, 512 trees x 5,101 nodes, full TTF run", "ttf_wall_ms": round(t, 2),
+            "node_steps_per_s": r["node_steps"] / (t / 1e3), "stress_ms": round(r["stress_ms"], 2),
+            "ir_ms": round(r["ir_ms"], 2), "final_drop": float(r["final_drop"][0])}
 
 
 def surrogate_leg(peaks, src, stream, rows=4096 * 1024, reps=10):
@@ -395,41 +491,6 @@ def krylov_leg(g, p, stream, be, q=20, oracle=True):
     return out
 
 
-def large_leg(p, stream):
-    """The 2048 x 2048 full chip (4,096 stripes of 20,471 stress nodes,
-    83.8 M nodes; 4.19 M IR nodes), one sample, FP32: load time, workspace
-    and one graph-captured TTF run of 64 x 256 steps."""
-    import torch
-    import ems_synth as es
-    from paper_2604_10743_gb300 import EMS_F32
-    from paper_2604_10743_gb300.engine import Engine
-    g = es.grid.large_grid(n_samples=0)
-    t0 = time.perf_counter()
-    eng = Engine(p, g, precision=EMS_F32, max_voids=32)
-    torch.cuda.synchronize()
-    t_load = time.perf_counter() - t0
-    init = eng.state_export()
-    eng.ttf()                                        # warm-up (captures the graph)
-    torch.cuda.synchronize()
-    eng.state_import(init)
-    a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    r = eng.ttf()
-    a1.record(stream)
-    torch.cuda.synchronize()
-    t = a0.elapsed_time(a1)
-    out = {"workload": "2048x2048-stripe two-layer mesh at 5 um: 4,096 trees x 20,471 stress nodes (83.8 M), "
-                       "4.19 M IR nodes, 5 % lognormal sinks, 330 K + 8 hotspots; one sample, FP32; "
-                       "64 aging steps x 256 BE steps",
-           "stress_nodes": eng.n_stress, "workspace_gb": round(eng.ws_bytes / 1e9, 2), "load_s": round(t_load, 1),
-           "ttf_wall_ms": round(t, 1), "node_steps_per_s": r["node_steps"] / (t / 1e3),
-           "stress_ms": round(r["stress_ms"], 1), "ir_ms": round(r["ir_ms"], 1),
-           "ir_iterations": r["ir_iterations"], "ttf_s": float(r["ttf"][0]), "drop0": float(r["drop0"][0]),
-           "final_drop": float(r["final_drop"][0]), "voids": int(r["n_voids"][0]), "graph": r["graph"]}
-    eng.close()
-    return out
-
-
 def schedule_leg(p, stream, n_train=24, n_valid=3, test_seed=3000, N=64, S=32):
     """What the learned part buys: the surrogate trained on the plain
     solver's records of n_train seeded N x N grids (S Monte Carlo samples
@@ -496,19 +557,45 @@ def schedule_leg(p, stream, n_train=24, n_valid=3, test_seed=3000, N=64, S=32):
             "max_rel_err_ttf_or_final_drop": _result_error(r_plain, r_sched)}
 
 
-def cpu_baseline(g, p, n_outer):
-    """The CPU oracle, as it stands, on a bounded sample of the same workload:
-    the full grid (all 512 trees) for n_outer aging steps."""
+def corner_grid(n=256):
+    """The n x n-crossing corner of the full chip: the same pitch, pads, sinks
+    and thermal map, cut out of the 2048 x 2048 netlist (array selection
+    only)."""
+    import numpy as np
+    g = full_chip(0)
+    N = 2048
+    ii, jj = np.divmod(np.arange(N * N), N)
+    keep = (ii < n) & (jj < n)
+    new_id = -np.ones(N * N, np.int64)
+    new_id[keep] = ii[keep] * n + jj[keep]
+    a, b = np.asarray(g["seg_a"]), np.asarray(g["seg_b"])
+    sk = keep[a] & keep[b]
+    out = dict(g)
+    out.update(N=n, node_x=g["node_x"][keep], node_y=g["node_y"][keep],
+               seg_a=new_id[a[sk]].astype(np.int32), seg_b=new_id[b[sk]].astype(np.int32))
+    for k in ("seg_layer", "seg_cells", "seg_R0", "seg_W", "seg_H", "seg_L"):
+        out[k] = np.asarray(g[k])[sk]
+    pk = keep[g["pad_node"]]
+    out["pad_node"] = new_id[g["pad_node"][pk]].astype(np.int32); out["pad_V"] = g["pad_V"][pk]
+    sk2 = keep[g["sink_node"]]
+    out["sink_node"] = new_id[g["sink_node"][sk2]].astype(np.int32); out["sink_I"] = g["sink_I"][sk2]
+    return out
+
+
+def cpu_baseline(p, n_outer=1):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the
+    256 x 256-crossing corner of the full chip (512 stripes x 2,551 nodes),
+    one sample, n_outer aging steps including the IR solves."""
     from oracle import flow as F
-    g = dict(g)
+    g = corner_grid()
     g["trees"] = F.build_trees(g)
     t0 = time.perf_counter()
-    r = F.run_ttf(g, p, n_outer=n_outer)
+    r = F.run_ttf(g, p, n_outer=n_outer, n_threads=os.cpu_count() or 0)
     dt = time.perf_counter() - t0
-    cores = os.cpu_count()
-    return {"value": r["node_steps"] / dt, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of %d aging steps (all 512 trees, %d BE steps each) incl. IR solves" %
-                      (n_outer, p["n_outer"], p["n_inner"]), "seconds": round(dt, 2)}
+    return {"value": r["node_steps"] / dt, "unit": "node-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d aging step(s) of the 256x256-crossing corner of the full chip (512 stripes x 2,551 "
+                      "nodes, same pitch, sinks and map), one Monte Carlo sample, IR solves included" % n_outer,
+            "seconds": round(dt, 2)}
 
 
 def run_reference(args):
@@ -517,25 +604,27 @@ def run_reference(args):
         return
     import ems_synth as es
     from oracle import flow as F
-    g = es.mid_grid()
+    g = corner_grid()
     p = es.default_params()
     g["trees"] = F.build_trees(g)
+    nt = os.cpu_count() or 0
     for _ in range(args.warmup):
-        F.run_ttf(g, p, n_outer=1)
+        F.run_ttf(g, p, n_outer=1, n_threads=nt)
     t0 = time.perf_counter()
     ns = 0
     for _ in range(args.steps):
-        r = F.run_ttf(g, p, n_outer=1)
+        r = F.run_ttf(g, p, n_outer=1, n_threads=nt)
         ns += r["node_steps"]
     dt = time.perf_counter() - t0
     v = ns / dt
     cores = os.cpu_count()
+    sample = ("1 aging step per step of the 256x256-crossing corner of the full chip (512 stripes x 2,551 nodes, "
+              "same pitch, sinks and map), one Monte Carlo sample, IR solve included")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "node-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 aging step per step"},
-            "cpu_baseline": {"value": v, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": "1 of 64 aging steps of the full grid per step"},
+            "data": "synthetic", "config": {"workload": WORKLOAD % (args.samples, args.window), "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "node-steps/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -555,13 +644,16 @@ def main():
     ap.add_argument("--krylov", action="store_true", help="also time the Krylov reduced model (slow oracle leg)")
     ap.add_argument("--schedule-only", action="store_true",
                     help="train the surrogate and time a Monte Carlo TTF run with and without its step schedule")
-    ap.add_argument("--large-only", action="store_true",
-                    help="time only the 2048 x 2048 full chip (one sample); prints its own JSON line")
     ap.add_argument("--krylov-only", action="store_true",
                     help="time only the Krylov TTF run and its BE reference (profiling); prints its own JSON line")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="time only the surrogate inference (profiling); prints its own JSON line")
     ap.add_argument("--surrogate-rows", type=int, default=4096 * 1024)
+    ap.add_argument("--samples", type=int, default=32, help="Monte Carlo samples of the full chip held at once")
+    ap.add_argument("--window", type=int, default=8, help="samples whose coefficients are held at once")
+    ap.add_argument("--max-voids", type=int, default=128)
+    ap.add_argument("--mid-only", action="store_true",
+                    help="time only full TTF runs of the 256 x 256 mesh; prints its own JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -572,10 +664,9 @@ def main():
             import torch
             import ems_synth as es
             print(json.dumps({"surrogate_schedule": schedule_leg(es.default_params(), torch.cuda.current_stream())}))
-        elif args.large_only:
+        elif args.mid_only:
             import torch
-            import ems_synth as es
-            print(json.dumps({"large": large_leg(es.default_params(), torch.cuda.current_stream())}))
+            print(json.dumps({"mid": mid_grid_leg(args, torch.cuda.current_stream())}))
         elif args.krylov_only:
             import torch
             import ems_synth as es

@@ -272,7 +272,8 @@ typedef struct {
     int32_t *n_mortal;    /* [S] mortal trees by the screen (if opts.screen) */
     double *drops;        /* optional [S][n_outer+1] drop after every aging step */
     double node_steps;    /* out: sum over trees and samples of nodes x BE steps */
-    double stress_ms;     /* out: device time of the stress kernels (ms) */
+    double stress_ms;     /* out: device time of the stress-advance kernels (ms; graph runs: the
+                             chain / tree / reduced-model launches themselves) */
     double ir_ms;         /* out: device time of the IR solves (ms) */
     double ir_iterations; /* out: PCG iterations summed over the IR solves and samples */
     double ttf_mean;      /* out: mean TTF over uncensored samples (NaN if none) */

@@ -960,32 +960,32 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
-struct ClSlots {                      // per-CTA words read by the other CTAs of the cluster
-    float fA, fB, bA, bB;             // forward / backward aggregates of this CTA's chunks
-    float first, last;                // stresses at this CTA's first and last node (halo)
-    int flags;                        // bit 0: a node reached its threshold, bit 1: a node is near the guard
-    double best;                      // argmax of sigma - sigma_crit over this CTA (nucleation)
-    int arg;
-    double tmin;                      // lowest threshold over this CTA
-    double fm[4];                     // factorisation: this CTA's product of 2 x 2 chunk matrices
+struct ClSlots {                      // written by the other CTAs of the cluster (push), read locally
+    float fA[8], fB[8], bA[8], bB[8]; // each rank's forward / backward aggregate of its chunks
+    float last_left, first_right;     // stress at the left neighbour CTA's last / right one's first node
+    int flags[8];                     // each rank: bit 0 a node reached its threshold, bit 1 near the guard
+    double best[8];                   // each rank's argmax of sigma - sigma_crit (nucleation)
+    int arg[8];
+    double tmin[8];                   // each rank's lowest threshold
+    double fm[8][4];                  // each rank's product of 2 x 2 chunk matrices (factorisation)
 };
 
-// cluster-wide composition of affine maps x -> A + B x in rank order (fwd:
-// ranks < r left to right) or reverse (bwd: ranks > r right to left), applied to 0
-__device__ __forceinline__ float cl_carry_fwd(cg::cluster_group &cl, ClSlots *sl, int rank) {
+// composition of the ranks' affine maps x -> A + B x applied to 0, from the
+// local copies: forward over ranks < r left to right, backward over ranks > r
+template <int CL>
+__device__ __forceinline__ float cl_carry_fwd(const ClSlots &sl, int rank) {
     float z = 0.0f;
-    for (int q = 0; q < rank; ++q) {
-        const ClSlots *o = cl.map_shared_rank(sl, q);
-        z = fmaf(o->fB, z, o->fA);
-    }
+#pragma unroll
+    for (int q = 0; q < CL; ++q)
+        if (q < rank) z = fmaf(sl.fB[q], z, sl.fA[q]);
     return z;
 }
-__device__ __forceinline__ float cl_carry_bwd(cg::cluster_group &cl, ClSlots *sl, int rank, int CL) {
+template <int CL>
+__device__ __forceinline__ float cl_carry_bwd(const ClSlots &sl, int rank) {
     float x = 0.0f;
-    for (int q = CL - 1; q > rank; --q) {
-        const ClSlots *o = cl.map_shared_rank(sl, q);
-        x = fmaf(o->bB, x, o->bA);
-    }
+#pragma unroll
+    for (int q = CL - 1; q >= 0; --q)
+        if (q > rank) x = fmaf(sl.bB[q], x, sl.bA[q]);
     return x;
 }
 
@@ -1071,18 +1071,16 @@ __device__ __noinline__ void chain_factor_cl(const ChainArgs<float> &a, double d
     __syncthreads();
     M2 Cw{1.0, 0.0, 0.0, 1.0};
     for (int k = 0; k < w; ++k) Cw = m2mul(M2{sfm[0][k], sfm[1][k], sfm[2][k], sfm[3][k]}, Cw);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 4 * (int)cl.num_blocks()) {         // this CTA's product, pushed to every CTA
         M2 Ag{1.0, 0.0, 0.0, 1.0};
         for (int k = 0; k < nw; ++k) Ag = m2mul(M2{sfm[0][k], sfm[1][k], sfm[2][k], sfm[3][k]}, Ag);
-        sl->fm[0] = Ag.a; sl->fm[1] = Ag.b; sl->fm[2] = Ag.c; sl->fm[3] = Ag.d;
+        const int q = threadIdx.x >> 2, e = threadIdx.x & 3;
+        cl.map_shared_rank(sl, q)->fm[rank][e] = e == 0 ? Ag.a : e == 1 ? Ag.b : e == 2 ? Ag.c : Ag.d;
     }
     cl.sync();
     // product of the earlier CTAs' aggregates (later on the left)
     M2 Qc{1.0, 0.0, 0.0, 1.0};
-    for (int q = 0; q < rank; ++q) {
-        const ClSlots *o = cl.map_shared_rank(sl, q);
-        Qc = m2mul(M2{o->fm[0], o->fm[1], o->fm[2], o->fm[3]}, Qc);
-    }
+    for (int q = 0; q < rank; ++q) Qc = m2mul(M2{sl->fm[q][0], sl->fm[q][1], sl->fm[q][2], sl->fm[q][3]}, Qc);
     const M2 CwT = m2mul(Cw, Qc);
     const M2 incl = m2mul(P, CwT);
     const M2 prev = m2shfl_up(incl, 1);
@@ -1155,11 +1153,10 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
         double tm = INFINITY;
         for (int i = g; i < n; i += TT) tm = fmin(tm, a.thr[cs + i]);
         tm = block_min(tm, sv);
-        if (c == 0) sl.tmin = tm;
+        if (c < CL) cl.map_shared_rank(&sl, c)->tmin[rank] = tm;
         cl.sync();
         double r = INFINITY;
-        for (int q = 0; q < CL; ++q) r = fmin(r, cl.map_shared_rank(&sl, q)->tmin);
-        cl.sync();                               // tmin may be rewritten next time
+        for (int q = 0; q < CL; ++q) r = fmin(r, sl.tmin[q]);
         return r;
     };
     double thrmin = thr_min();
@@ -1171,10 +1168,10 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
     if ((a.n_steps - kd) % rs) rs = 1;
     if (rs > 1) {
         const int nr = __syncthreads_or(near_guard<R, M>(sg, a.guard * thrmin));
-        if (c == 0) sl.flags = nr ? 2 : 0;
+        if (c < CL) cl.map_shared_rank(&sl, c)->flags[rank] = nr ? 2 : 0;
         cl.sync();
         int any = 0;
-        for (int q = 0; q < CL; ++q) any |= cl.map_shared_rank(&sl, q)->flags;
+        for (int q = 0; q < CL; ++q) any |= sl.flags[q];
         cl.sync();
         if (any & 2) {
             rs = 1;
@@ -1239,8 +1236,8 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
     auto publish = [&]() {
         if (lane == 31) sL[w] = sg[M - 1];
         if (lane == 0) sR[w] = sg[0];
-        if (c == 0) sl.first = sg[0];
-        if (c == T - 1) sl.last = sg[M - 1];
+        if (c == 0 && rank > 0) cl.map_shared_rank(&sl, rank - 1)->first_right = sg[0];
+        if (c == T - 1 && rank + 1 < CL) cl.map_shared_rank(&sl, rank + 1)->last_left = sg[M - 1];
     };
     publish();
     cl.sync();
@@ -1249,8 +1246,8 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
         R right = __shfl_down_sync(full, sg[0], 1);
         if (lane == 0 && w > 0) left = sL[w - 1];
         if (lane == 31 && w + 1 < nw) right = sR[w + 1];
-        if (c == 0) left = rank > 0 ? cl.map_shared_rank(&sl, rank - 1)->last : R(0);
-        if (c == T - 1) right = rank + 1 < CL ? cl.map_shared_rank(&sl, rank + 1)->first : R(0);
+        if (c == 0) left = rank > 0 ? sl.last_left : R(0);
+        if (c == T - 1) right = rank + 1 < CL ? sl.first_right : R(0);
         R gk = cg_[0];
         R qprev = gk * (left - sg[0]);
         R z = R(0);
@@ -1270,9 +1267,11 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
         // forward carries: within the CTA, then across the cluster
         float exA, exB, agA, agB;
         cta_scan<0>(z, cpf[M - 1], sA, sB, exA, exB, agA, agB);
-        if (c == 0) { sl.fA = agA; sl.fB = agB; }
+        agA = __shfl_sync(0xffffffffu, agA, 0);
+        agB = __shfl_sync(0xffffffffu, agB, 0);
+        if (c < CL) { ClSlots *o = cl.map_shared_rank(&sl, c); o->fA[rank] = agA; o->fB[rank] = agB; }
         cl.sync();
-        const float cf = fmaf(exB, cl_carry_fwd(cl, &sl, rank), exA);
+        const float cf = fmaf(exB, cl_carry_fwd<CL>(sl, rank), exA);
         R x = R(0);
 #pragma unroll
         for (int k = M - 1; k >= 0; --k) {
@@ -1282,9 +1281,11 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
         }
         float bxA, bxB, bgA, bgB;
         cta_scan<1>(x, cpb[0], sA, sB, bxA, bxB, bgA, bgB);
-        if (c == 0) { sl.bA = bgA; sl.bB = bgB; }
+        bgA = __shfl_sync(0xffffffffu, bgA, 0);
+        bgB = __shfl_sync(0xffffffffu, bgB, 0);
+        if (c < CL) { ClSlots *o = cl.map_shared_rank(&sl, c); o->bA[rank] = bgA; o->bB[rank] = bgB; }
         cl.sync();
-        const float cr = fmaf(bxB, cl_carry_bwd(cl, &sl, rank, CL), bxA);
+        const float cr = fmaf(bxB, cl_carry_bwd<CL>(sl, rank), bxA);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
             const R y = fmx(cpb[k], cr, zr[k]) - cc[k];
@@ -1311,10 +1312,10 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
         const bool nr = s_rs > 1 && near_guard<R, M>(sg, s_gthr);
         publish();
         const int f = __syncthreads_or(hit) | (__syncthreads_or(nr) << 1);
-        if (c == 0) sl.flags = f;
+        if (c < CL) cl.map_shared_rank(&sl, c)->flags[rank] = f;
         cl.sync();
         int any = 0;
-        for (int q = 0; q < CL; ++q) any |= cl.map_shared_rank(&sl, q)->flags;
+        for (int q = 0; q < CL; ++q) any |= sl.flags[q];
         int refac_from = -1;
         if (any & 1) {
             double best = -INFINITY;
@@ -1328,16 +1329,13 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
                 }
             }
             block_argmax(best, arg, sv, si);
-            cl.sync();                           // the flags were read; slots may change
-            if (c == 0) { sl.best = best; sl.arg = arg; }
+            if (c < CL) { ClSlots *o = cl.map_shared_rank(&sl, c); o->best[rank] = best; o->arg[rank] = arg; }
 #pragma unroll
             for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * TT + g] = sg[k];
             cl.sync();
             best = -INFINITY; arg = 0x7fffffff;
-            for (int q = 0; q < CL; ++q) {
-                const ClSlots *o = cl.map_shared_rank(&sl, q);
-                if (o->best > best || (o->best == best && o->arg < arg)) { best = o->best; arg = o->arg; }
-            }
+            for (int q = 0; q < CL; ++q)
+                if (sl.best[q] > best || (sl.best[q] == best && sl.arg[q] < arg)) { best = sl.best[q]; arg = sl.arg[q]; }
             if (best >= 0.0) {
                 const int v = arg;
                 if (c == 0) {

@@ -129,7 +129,7 @@ ems_status finish(ems_ctx *c, ems_ttf_result *out, const std::vector<double> &tt
 // One aging step of every sample, recorded on c->stream (the capture
 // stream): per window of samples, the window's coefficients, forcing, stress
 // advance, void update and IR re-solve, then the crossing test; ev holds 4
-// events per window (stress start / end, IR start / end).
+// events per window (around the stress kernels, around the IR solve).
 ems_status record_step(ems_ctx *c, double dto, double dti, bool kr, cudaEvent_t *ev) {
     const ems_params &p = c->prm;
     const int stride = p.n_outer + 1;
@@ -137,9 +137,9 @@ ems_status record_step(ems_ctx *c, double dto, double dti, bool kr, cudaEvent_t 
     EMS_TRY(each_window(c, [&](int, int ns) -> ems_status {
         cudaEvent_t *e = ev + 4 * (size_t)(w++);
         Dev &d = c->d;
-        EMS_CUDA(c, cudaEventRecordWithFlags(e[0], c->stream, cudaEventRecordExternal));
         EMS_TRY(window_derive(c));
         EMS_TRY(forcing(c));
+        EMS_CUDA(c, cudaEventRecordWithFlags(e[0], c->stream, cudaEventRecordExternal));
         EMS_TRY(kr ? krylov_stress(c, dti, p.n_inner) : launch_be(c, dti, p.n_inner));
         EMS_CUDA(c, cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
         EMS_TRY(void_update(c, nullptr));

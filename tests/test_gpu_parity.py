@@ -589,7 +589,15 @@ def test_cluster_chain_kernel_against_oracle(cells, cl):
              for v in ref["void_nodes"]}
     assert len(ranks) >= 2
     assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
-    nt, nv = _f32_voids(eng, ref)
-    assert nt >= 1
+    # cells of 6.8-24 nm: a nucleation's runner-up is its neighbour, so FP32
+    # may pick the next node; every tree has the oracle's number of voids,
+    # each within two nodes of the oracle's
+    v = eng.voids()
+    off = ref["trees"]["off"]
+    for t in range(len(off) - 1):
+        gv = sorted(x for x in v["node"].tolist() if off[t] <= x < off[t + 1])
+        ov = sorted(x for x in ref["void_nodes"].tolist() if off[t] <= x < off[t + 1])
+        assert len(gv) == len(ov), t
+        assert all(abs(p_ - q_) <= 2 for p_, q_ in zip(gv, ov)), t
     _metric_close(r, ref)
     eng.close()
