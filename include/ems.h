@@ -165,6 +165,21 @@ ems_status ems_set_thermal_map(ems_ctx *ctx, const double *T, int nx, int ny,
                                double x0, double y0, double x1, double y1);
 
 /*
+ * Per-sample temperature-map perturbation (Sec. IV-F: external temperature
+ * maps among the inputs a Monte Carlo sample may vary): sample s adds the
+ * raster dT[s][iy*nx + ix] (K), vertex-centred over the extent of the map set
+ * by ems_set_thermal_map and sampled bilinearly (clamped at the border), to
+ * the temperature of every stress node; kappa and the thermomigration term
+ * of the sample follow.  dT == NULL removes the perturbations.  The map (or
+ * a Joule-heating profile) stays the common base; the surrogate's features
+ * keep using the base temperatures.
+ *   dT      host [n_samples][ny][nx], nx, ny >= 2, nx * ny <= 4,096
+ * EMS_E_STATE without a thermal map; EMS_E_INVAL for a bad size or a
+ * non-finite value.
+ */
+ems_status ems_set_thermal_perturbation(ems_ctx *ctx, const double *dT, int nx, int ny);
+
+/*
  * Joule-heating temperature profile along every branch (Sec. III-A: the
  * stationary thermal equation k T'' + j^2 rho - k (T - T0) / Gamma^2 = 0 with
  * the thermal characteristic length Gamma^2 = t_cu t_ILD k_cu / k_ILD, t_cu

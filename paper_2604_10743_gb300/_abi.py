@@ -67,7 +67,7 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_krylov_reduce", "ems_void_update", "ems_ttf", "ems_get_sigma", "ems_get_currents",
            "ems_get_resistance", "ems_get_voids", "ems_state_export", "ems_state_import",
            "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc", "ems_joule_profile", "ems_set_wait_limit",
-           "ems_get_node_temperature",
+           "ems_get_node_temperature", "ems_set_thermal_perturbation",
            # include/ems_surrogate.h
            "ems_mlp_create", "ems_mlp_destroy", "ems_mlp_last_error", "ems_mlp_param_count",
            "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_fit_norm", "ems_mlp_gradients",
@@ -124,6 +124,8 @@ def lib(path=None):
     L.ems_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.ems_state_import.restype = S
     L.ems_state_import.argtypes = [vp, vp, ctypes.c_size_t]
+    L.ems_set_thermal_perturbation.restype = S
+    L.ems_set_thermal_perturbation.argtypes = [vp, c_double_p, S, S]
     L.ems_set_wait_limit.restype = S
     L.ems_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     L.ems_joule_profile.restype = S

@@ -35,6 +35,7 @@ void map_window(ems_ctx *c, int s0, int ns) {
     off(d.kr_mode, nt); off(d.kdone, nt); off(d.sched, nt); off(d.fdt, nt);
     off(d.v_node, nv); off(d.v_seg, nv); off(d.v_vol, nv); off(d.v_tnuc, nv);
     off(d.feat, nt * EMS_MLP_FEATURES); off(d.pred, nt * EMS_MLP_OUTPUTS);
+    off(d.pert, (size_t)EMS_MAX_PERT);
     c->S = ns;
     c->win_s0 = s0;
 }
@@ -489,7 +490,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.face_sign = cv.take<int8_t>(N);
     d.face_dx = cv.take<double>(N); d.face_area = cv.take<double>(N);
     d.nx_ = cv.take<double>(N); d.ny_ = cv.take<double>(N);
-    d.Tn = cv.take<double>(N); d.Mface = cv.take<double>(N); d.V = cv.take<double>(N);
+    d.Tn = cv.take<double>(N); d.Mface = cv.take<double>((size_t)Sd * N); d.V = cv.take<double>(N);
     d.kap_a = cv.take<double>((size_t)Sd * N); d.g = cv.take<double>((size_t)Sd * N);
     d.leak = cv.take<double>((size_t)Sd * N); d.thr = cv.take<double>((size_t)Sd * N);
     d.f = cv.take<double>((size_t)Sd * N); d.sig_ss = cv.take<double>((size_t)Sd * N);
@@ -510,6 +511,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.thr0 = cv.take<double>((size_t)Sd * N);
     d.R_prev = cv.take<double>((size_t)S * ns);
     d.raster = cv.take<double>(EMS_MAX_RASTER);
+    d.pert = cv.take<double>((size_t)S * EMS_MAX_PERT);
     d.kr_mode = cv.take<int32_t>((size_t)S * nt); d.kdone = cv.take<int32_t>((size_t)S * nt);
     {
         const int no = c ? c->prm.n_outer : 1;
@@ -782,6 +784,7 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     c->factored_dt = -1.0;
     c->have_u = false;
     c->joule = false;
+    c->pnx = c->pny = 0;
     c->loaded = true;
     // uniform temperature, node physics, initial stress
     EMS_TRY(ems_set_thermal_map(c, nullptr, 0, 0, 0, 0, 0, 0));

@@ -19,6 +19,7 @@
 
 #define EMS_MAX_VOIDS 256     // compile-time cap on void slots per (tree, sample)
 #define EMS_MAX_RASTER (1024 * 1024)  // thermal raster values held in the workspace
+#define EMS_MAX_PERT 4096             // values of one sample's temperature perturbation raster
 // polls a grid-barrier wait makes before it gives up (about a second)
 constexpr long long kDefaultWaitLimit = 1LL << 24;
 
@@ -144,7 +145,7 @@ struct Dev {
     int8_t *face_sign;
     double *face_dx, *face_area, *nx_, *ny_;
     double *Tn;                        // [N] node temperature
-    double *Mface;                     // [N] TM term per face
+    double *Mface;                     // [S][N] TM term per face (per sample: temperature perturbations)
     double *V;                         // [N]
     double *kap_a, *g, *leak, *thr;    // [S][N]
     double *f;                         // [S][N] forcing
@@ -169,6 +170,7 @@ struct Dev {
     double *thr0;                      // [S][N] critical stress without voids
     double *R_prev;                    // [S][n_seg]
     double *raster;                    // thermal raster (up to EMS_MAX_RASTER values)
+    double *pert;                      // [S][EMS_MAX_PERT] per-sample temperature perturbation rasters
     // rational Krylov reduced models (allocated when params.method != EMS_BE)
     void *kr_V;                        // [S][RMAX][P] basis columns (context precision); RMAX = 2q + 2
     double *kr_Ah, *kr_Ch;             // [S][nt][RMAX^2] reduced A_h, C_h (cached base block + current block)
@@ -252,6 +254,7 @@ struct ems_ctx {
     // thermal raster currently set (nx = 0: uniform T0)
     int rnx = 0, rny = 0;
     double rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;
+    int pnx = 0, pny = 0;      // per-sample perturbation rasters over the map's extent (0: none)
 };
 
 namespace ems {

@@ -61,29 +61,52 @@ struct PhysArgs {
     int n_seg;
     const int32_t *gpar, *face_seg, *owner_seg, *child_ptr, *child_gidx;
     const double *Tn, *dx, *area, *kfac, *sfac;
+    const double *pert, *nx, *ny;      // per-sample perturbation rasters [S][EMS_MAX_PERT] (pnx = 0: none)
+    int pnx, pny;
+    double px0, py0, px1, py1;
     double D0, Ea, kB, B, Omega, Qs, delta, sigma_crit;
     double *kap_a, *g, *Mface, *V, *leak, *thr0, *thr;
 };
 
+// a sample's temperature perturbation at (x, y): bilinear over its raster,
+// vertex-centred over the map's extent, clamped at the border
+__device__ double pert_at(const PhysArgs &a, const double *r, double x, double y) {
+    double fx = (x - a.px0) / (a.px1 - a.px0) * (a.pnx - 1);
+    double fy = (y - a.py0) / (a.py1 - a.py0) * (a.pny - 1);
+    fx = fmin(fmax(fx, 0.0), (double)(a.pnx - 1));
+    fy = fmin(fmax(fy, 0.0), (double)(a.pny - 1));
+    const int ix = min((int)floor(fx), a.pnx - 2), iy = min((int)floor(fy), a.pny - 2);
+    const double tx = fx - ix, ty = fy - iy;
+    const double *r0 = r + (int64_t)iy * a.pnx, *r1 = r0 + a.pnx;
+    return (1 - tx) * (1 - ty) * r0[ix] + tx * (1 - ty) * r0[ix + 1] + (1 - tx) * ty * r1[ix] + tx * ty * r1[ix + 1];
+}
+
 // per face (stored at the child node): a kappa, g = a kappa / dx, TM term M
+// (per sample: a sample's perturbation raster adds to the node temperatures)
 __global__ void k_faces(PhysArgs a) {
     const int s = blockIdx.y;
+    const double *pr = a.pert + (int64_t)s * EMS_MAX_PERT;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t si = (int64_t)s * a.N + i;
         const int32_t q = a.gpar[i];
         if (q < 0) {
             a.kap_a[si] = 0.0; a.g[si] = 0.0;
-            if (s == 0) a.Mface[i] = 0.0;
+            a.Mface[si] = 0.0;
             continue;
         }
-        const double Te = 0.5 * (a.Tn[i] + a.Tn[q]);
+        double Ti = a.Tn[i], Tq = a.Tn[q];
+        if (a.pnx > 0) {
+            Ti += pert_at(a, pr, a.nx[i], a.ny[i]);
+            Tq += pert_at(a, pr, a.nx[q], a.ny[q]);
+        }
+        const double Te = 0.5 * (Ti + Tq);
         const double ikT = 1.0 / (a.kB * Te);
         const double kap = a.D0 * exp(-a.Ea * ikT) * a.B * a.Omega * ikT *
                            a.kfac[(int64_t)s * a.n_seg + a.face_seg[i]];
         const double ka = a.area[i] * kap;
         a.kap_a[si] = ka;
         a.g[si] = ka / a.dx[i];
-        if (s == 0) a.Mface[i] = a.Qs / (a.Omega * Te) * (a.Tn[i] - a.Tn[q]) / a.dx[i];
+        a.Mface[si] = a.Qs / (a.Omega * Te) * (Ti - Tq) / a.dx[i];
     }
 }
 
@@ -123,13 +146,13 @@ __global__ void k_forcing(int64_t N, int n_seg, double sfac_em, const int32_t *g
                           const int8_t *sign, const int32_t *child_ptr, const int32_t *child_gidx,
                           const double *Mface, const double *kap_a, const double *j, double *f) {
     const int s = blockIdx.y;
-    const double *js = j + (int64_t)s * n_seg, *ka = kap_a + (int64_t)s * N;
+    const double *js = j + (int64_t)s * n_seg, *ka = kap_a + (int64_t)s * N, *Ms = Mface + (int64_t)s * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        if (gpar[i] >= 0) acc = ka[i] * (sfac_em * sign[i] * js[face_seg[i]] + Mface[i]);
+        if (gpar[i] >= 0) acc = ka[i] * (sfac_em * sign[i] * js[face_seg[i]] + Ms[i]);
         for (int k = child_ptr[i]; k < child_ptr[i + 1]; ++k) {
             const int32_t ch = child_gidx[k];
-            acc -= ka[ch] * (sfac_em * sign[ch] * js[face_seg[ch]] + Mface[ch]);
+            acc -= ka[ch] * (sfac_em * sign[ch] * js[face_seg[ch]] + Ms[ch]);
         }
         f[(int64_t)s * N + i] = acc;
     }
@@ -1613,7 +1636,7 @@ __global__ void k_screen(int n_trees, int S, int64_t N, int n_seg, double sfac_e
     ss[cs] = 0.0;
     for (int64_t i = 1; i < n; ++i) {
         const int64_t gi = cb + i;
-        const double G = sfac_em * sign[gi] * js[face_seg[gi]] + Mface[gi];
+        const double G = sfac_em * sign[gi] * js[face_seg[gi]] + Mface[(int64_t)s * N + gi];
         const double Pi = ss[(int64_t)s * N + gpar[gi]] + dx[gi] * G;
         ss[cs + i] = Pi;
         sv += V[gi];
@@ -1775,7 +1798,9 @@ ems_status sample_physics(ems_ctx *c) {
     PhysArgs a;
     a.N = c->N; a.n_seg = c->n_seg; a.gpar = d.par; a.face_seg = d.face_seg; a.owner_seg = d.owner_seg;
     a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx; a.Tn = d.Tn; a.dx = d.face_dx; a.area = d.face_area;
-    a.kfac = d.kfac; a.sfac = d.sfac; a.D0 = p.D0; a.Ea = p.Ea; a.kB = p.k_B; a.B = p.B_modulus;
+    a.kfac = d.kfac; a.sfac = d.sfac; a.D0 = p.D0;
+    a.pert = d.pert; a.nx = d.nx_; a.ny = d.ny_; a.pnx = c->pnx; a.pny = c->pny;
+    a.px0 = c->rx0; a.py0 = c->ry0; a.px1 = c->rx1; a.py1 = c->ry1; a.Ea = p.Ea; a.kB = p.k_B; a.B = p.B_modulus;
     a.Omega = p.Omega; a.Qs = p.Q_star; a.delta = p.delta; a.sigma_crit = p.sigma_crit;
     a.kap_a = d.kap_a; a.g = d.g; a.Mface = d.Mface; a.V = d.V; a.leak = d.leak; a.thr0 = d.thr0; a.thr = d.thr;
     k_faces<<<grid_1d(c->N, c->S), 256, 0, st>>>(a);
@@ -1908,6 +1933,7 @@ extern "C" ems_status ems_set_thermal_map(ems_ctx *c, const double *T, int nx, i
         c->rnx = nx; c->rny = ny; c->rx0 = x0; c->ry0 = y0; c->rx1 = x1; c->ry1 = y1;
     } else {
         c->rnx = 0; c->rny = 0;
+        c->pnx = c->pny = 0;                    // perturbations live on the map's extent
     }
     c->joule = false;
     if (windowed(c)) {
@@ -1980,4 +2006,32 @@ extern "C" ems_status ems_immortality_check(ems_ctx *c, uint8_t *mortal, double 
     if (sigma_ss_max)
         EMS_CUDA(c, cudaMemcpyAsync(sigma_ss_max, c->d.ssmax, ts * 8, cudaMemcpyDeviceToHost, c->stream));
     return check_status(c);
+}
+
+extern "C" ems_status ems_set_thermal_perturbation(ems_ctx *c, const double *dT, int nx, int ny) {
+    if (!c) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    if (dT) {
+        if (c->rnx == 0) return fail(c, EMS_E_STATE, "a perturbation needs a thermal map (its extent)");
+        if (nx < 2 || ny < 2 || nx * ny > EMS_MAX_PERT)
+            return fail(c, EMS_E_INVAL, "perturbation raster must be 2x2 .. 4,096 values");
+        for (int64_t k = 0; k < (int64_t)c->S_all * nx * ny; ++k)
+            if (!std::isfinite(dT[k])) return fail(c, EMS_E_INVAL, "non-finite temperature perturbation");
+        for (int s = 0; s < c->S_all; ++s)
+            EMS_CUDA(c, cudaMemcpyAsync(c->d_all.pert + (size_t)s * EMS_MAX_PERT, dT + (size_t)s * nx * ny,
+                                        sizeof(double) * nx * ny, cudaMemcpyHostToDevice, c->stream));
+        c->pnx = nx; c->pny = ny;
+    } else {
+        c->pnx = c->pny = 0;
+    }
+    if (windowed(c)) {
+        map_window(c, 0, c->W);
+        ems_status s = sample_physics(c);
+        map_all(c);
+        EMS_TRY(s);
+    } else {
+        EMS_TRY(sample_physics(c));
+    }
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EMS_OK;
 }

@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(256) k_features(FeatArgs a) {
             const double dx = a.dx[gi], ar = a.area[gi];
             const double jj = a.sign[gi] * js[a.face_seg[gi]];
             const double kap = a.kap_a[si] / ar;
-            const double G = a.sem * jj + a.Mface[gi];
+            const double G = a.sem * jj + a.Mface[si];
             p.s[0] += dx; p.s[3] += fabs(jj) * dx; p.s[4] += jj * dx; p.s[5] += kap * dx;
-            p.mx[0] = fmax(p.mx[0], fabs(jj)); p.mx[2] = fmax(p.mx[2], fabs(a.Mface[gi]));
+            p.mx[0] = fmax(p.mx[0], fabs(jj)); p.mx[2] = fmax(p.mx[2], fabs(a.Mface[si]));
             p.mx[3] = fmax(p.mx[3], kap); p.mn[1] = fmin(p.mn[1], kap);
             if (fabs(G) > p.gmax) { p.gmax = fabs(G); p.gkap = kap; }
         }
@@ -97,13 +97,13 @@ __global__ void __launch_bounds__(256) k_features(FeatArgs a) {
         double F = 0.0, Sa = 0.0;
         if (a.par[gi] >= 0) {
             const double ak = a.kap_a[si], ar = a.area[gi];
-            F += ak * (a.sem * a.sign[gi] * js[a.face_seg[gi]] + a.Mface[gi]);
+            F += ak * (a.sem * a.sign[gi] * js[a.face_seg[gi]] + a.Mface[si]);
             Sa += ar * sqrt(ak / ar);
         }
         for (int k = a.child_ptr[gi]; k < a.child_ptr[gi + 1]; ++k) {
             const int32_t ch = a.child_idx[k];
             const double ak = a.kap_a[(int64_t)s * a.N + ch], ar = a.area[ch];
-            F -= ak * (a.sem * a.sign[ch] * js[a.face_seg[ch]] + a.Mface[ch]);
+            F -= ak * (a.sem * a.sign[ch] * js[a.face_seg[ch]] + a.Mface[(int64_t)s * a.N + ch]);
             Sa += ar * sqrt(ak / ar);
         }
         if (F > 0.0 && Sa > 0.0) {

@@ -77,6 +77,17 @@ class Engine:
         self._check(self.L.ems_set_thermal_map(self.ctx, T.ctypes.data_as(A.c_double_p), nx, ny,
                                                th["x0"], th["y0"], th["x1"], th["y1"]))
 
+    def set_thermal_perturbation(self, dT):
+        """Per-sample temperature perturbation rasters [S, ny, nx] over the
+        map's extent (ems_set_thermal_perturbation); None removes them."""
+        if dT is None:
+            return self._check(self.L.ems_set_thermal_perturbation(self.ctx, None, 0, 0))
+        dT = np.ascontiguousarray(dT, np.float64)
+        S, ny, nx = dT.shape
+        if S != self.S:
+            raise ValueError("one perturbation raster per sample")
+        self._check(self.L.ems_set_thermal_perturbation(self.ctx, dT.ctypes.data_as(A.c_double_p), nx, ny))
+
     def joule_profile(self, k_cu=400.0, k_ild=1.4, t_ild=0.2e-6):
         """Joule-heating temperature profile along every branch (ems_joule_profile)."""
         self._check(self.L.ems_joule_profile(self.ctx, float(k_cu), float(k_ild), float(t_ild)))

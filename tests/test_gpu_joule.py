@@ -68,3 +68,36 @@ def test_aging_run_with_joule_profile():
         sorted(zip(ref["void_nodes"].tolist(), ref["void_seg"].tolist()))
     assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
     eng.close()
+
+
+@pytest.mark.parametrize("window", [0, 2])
+def test_per_sample_thermal_perturbation(window):
+    """Monte Carlo samples with their own temperature-map perturbation (a
+    coarse random raster per sample, +-15 K) on top of the hotspot map and
+    the kappa / sigma_crit factors: every sample against the oracle run with
+    that sample's node temperatures (base map + its perturbation)."""
+    g = es.mc_grid(n_samples=4)
+    g["thermal"] = es.hotspot_raster(np.random.default_rng(8), 140e-6, 2, 360.0, 20.0, 40.0, 0.2, nx=33, ny=33)
+    th = g["thermal"]
+    rng = np.random.default_rng(9)
+    dT = rng.uniform(-15.0, 15.0, size=(4, 6, 7))
+    p = es.default_params(n_outer=24)
+    eng = _engine(p, g, window=window)
+    eng.set_thermal_perturbation(dT)
+    r = eng.ttf()
+    sig = eng.sigma()
+    v = eng.voids()
+    tr = F.build_trees(g)
+    g["trees"] = tr
+    base = F.node_temperature(tr, th, p["T0"])
+    spread = []
+    for s in range(4):
+        Tn = base + F.bilinear(dict(T=dT[s], x0=th["x0"], y0=th["y0"], x1=th["x1"], y1=th["y1"]), tr["x"], tr["y"])
+        ref = F.run_ttf(g, p, sample=s, keep_state=True, Tn=Tn)
+        assert np.abs(sig[s] - ref["state"].sigma).max() / np.abs(ref["state"].sigma).max() < 1e-9
+        m = v["sample"] == s
+        assert sorted(zip(v["node"][m].tolist(), v["seg"][m].tolist())) == \
+            sorted(zip(ref["void_nodes"].tolist(), ref["void_seg"].tolist()))
+        assert abs(r["final_drop"][s] - ref["final_drop"]) <= 5e-4 * ref["final_drop"]
+        spread.append(ref["n_voids"])
+    eng.close()
