@@ -118,6 +118,41 @@ def _pad_array(N, every):
     return np.array([i * N + j for i in idx for j in idx], np.int32)
 
 
+def via_mesh(seed=6, N=8, pitch=20e-6, R_via=2.0, W_via=0.2e-6, H_via=0.2e-6, I_lo=0.4e-3, I_hi=1.6e-3,
+             cells=None):
+    """Two-layer mesh with explicit via resistors: every crossing (i, j) has a
+    lower-layer node i*N + j (horizontal stripes, layer 0) and an upper-layer
+    node N*N + i*N + j (vertical stripes, layer 1) joined by a via resistor
+    (seg_via = 1, resistance R_via).  Four corner pads on the upper layer, a
+    U(I_lo, I_hi) sink on every lower-layer crossing."""
+    rng = _rng(seed)
+    rho = default_params()["rho_Cu"]
+    g = stripe_mesh(N, pitch)
+    nh = N * (N - 1)
+    a = g["seg_a"].copy(); b = g["seg_b"].copy()
+    a[nh:] += N * N; b[nh:] += N * N                     # vertical stripes on the upper nodes
+    va = np.arange(N * N, dtype=np.int32); vb = va + N * N
+    ns = a.size
+    g["node_x"] = np.concatenate([g["node_x"], g["node_x"]])
+    g["node_y"] = np.concatenate([g["node_y"], g["node_y"]])
+    g["seg_a"] = np.concatenate([a, va]).astype(np.int32)
+    g["seg_b"] = np.concatenate([b, vb]).astype(np.int32)
+    g["seg_layer"] = np.concatenate([g["seg_layer"], np.zeros(N * N, np.int32)]).astype(np.int32)
+    c = g["seg_cells"] if cells is None else np.full(ns, cells, np.int32)
+    g["seg_cells"] = np.concatenate([c, np.ones(N * N, np.int32)]).astype(np.int32)
+    g["seg_W"] = np.concatenate([g["seg_W"], np.full(N * N, W_via)])
+    g["seg_H"] = np.concatenate([g["seg_H"], np.full(N * N, H_via)])
+    g["seg_L"] = np.concatenate([g["seg_L"], np.full(N * N, H_via)])
+    g["seg_R0"] = np.concatenate([rho * g["seg_L"][:ns] / (g["seg_W"][:ns] * g["seg_H"][:ns]), np.full(N * N, R_via)])
+    g["seg_via"] = np.concatenate([np.zeros(ns, np.int8), np.ones(N * N, np.int8)])
+    up = N * N
+    g["pad_node"] = np.array([up, up + N - 1, up + N * (N - 1), up + N * N - 1], np.int32)
+    g["pad_V"] = np.ones(4)
+    g["sink_node"] = np.arange(N * N, dtype=np.int32)
+    g["sink_I"] = rng.uniform(I_lo, I_hi, size=N * N)
+    return g
+
+
 def tiny_grid(seed=1, N=8, pitch=20e-6):
     """8x8 stripes of 7 x 20 um segments, 4 corner pads at 1 V, a sink on
     every crossing drawing U(0.5, 2) mA; uniform temperature (no map)."""

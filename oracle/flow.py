@@ -70,12 +70,17 @@ def build_trees(grid):
     L = np.asarray(grid["seg_L"]); W = np.asarray(grid["seg_W"]); H = np.asarray(grid["seg_H"])
     x = np.asarray(grid["node_x"]); y = np.asarray(grid["node_y"])
     nseg = a.size
-    # adjacency (node, layer) -> sorted list of segments
+    via = np.asarray(grid["seg_via"], bool) if grid.get("seg_via") is not None else np.zeros(nseg, bool)
+    # adjacency (node, layer) -> sorted list of wire segments (via resistors
+    # join layers; they carry current but belong to no stress tree)
     adj = {}
     for s in range(nseg):
+        if via[s]:
+            continue
         adj.setdefault((int(a[s]), int(layer[s])), []).append(s)
         adj.setdefault((int(b[s]), int(layer[s])), []).append(s)
     seen = np.zeros(nseg, bool)
+    seen[via] = True
     trees = []
     for s0 in range(nseg):            # trees ordered by their smallest segment id
         if seen[s0]:
@@ -377,12 +382,39 @@ def assign_void_segments(tr, st, j_seg, new_nodes):
 # Void growth resistance (Sec. III-D.3) and TTF (Eq. ttf_calculation, Sec. V)
 # ---------------------------------------------------------------------------
 
-def void_resistance(grid, p, st):
-    """R_s = R0_s + sum over voids on s of max(0, dR), with
-    dR = (V_v - V_crit)/(W H) [rho_Ta/(h_Ta(2H+W)) - rho_Cu/(H W)] and
-    V_crit = W * W * H (void length W: width is the critical dimension)."""
+R_OPEN = 1.0e9   # Ohm: open-circuit sentinel of a severed via (early failure)
+
+
+def up_vias(grid):
+    """Per IR node: the via resistor to a node of a strictly higher metal
+    layer (lowest segment id when several), -1 if none.  A node's layer is
+    the layer of its wire segments."""
+    n = len(grid["node_x"])
+    a = np.asarray(grid["seg_a"]); b = np.asarray(grid["seg_b"]); layer = np.asarray(grid["seg_layer"])
+    via = np.asarray(grid["seg_via"], bool) if grid.get("seg_via") is not None else np.zeros(a.size, bool)
+    nl = np.full(n, -1)
+    for s in np.nonzero(~via)[0]:
+        nl[a[s]] = layer[s]; nl[b[s]] = layer[s]
+    up = np.full(n, -1)
+    for s in np.nonzero(via)[0]:
+        for u, w in ((a[s], b[s]), (b[s], a[s])):
+            if nl[u] >= 0 and nl[w] > nl[u] and up[u] < 0:
+                up[u] = s
+    return up
+
+
+def void_resistance(grid, p, st, tr=None):
+    """Late failure (Sec. III-D.3): R_s = R0_s + sum over voids on s of
+    max(0, dR), dR = (V_v - V_crit)/(W H) [rho_Ta/(h_Ta(2H+W)) - rho_Cu/(H W)],
+    V_crit = W * W * H (void length W: width is the critical dimension).
+    Early failure (Sec. IV-C, explicit via resistors only): a void at an IR
+    node that connects upward through a via to a strictly higher layer severs
+    that via once its volume exceeds V_crit: the via's resistance becomes the
+    open-circuit sentinel R_OPEN.  Without via resistors only late failure
+    applies."""
     R = np.array(grid["seg_R0"], np.float64, copy=True)
     vn = np.nonzero(st.void)[0]
+    up = up_vias(grid) if grid.get("seg_via") is not None and tr is not None else None
     for v in vn:
         s = st.vseg[v]
         W = grid["seg_W"][s]; H = grid["seg_H"][s]
@@ -391,6 +423,8 @@ def void_resistance(grid, p, st):
         dR = (st.vol[v] - Vc) / (W * H) * coef
         if dR > 0.0:
             R[s] += dR
+        if up is not None and tr["ir"][v] >= 0 and up[tr["ir"][v]] >= 0 and st.vol[v] > Vc:
+            R[up[tr["ir"][v]]] = R_OPEN
     return R
 
 
@@ -447,7 +481,7 @@ def run_ttf(grid, p, sample=None, screen_first=False, record=False, n_threads=0,
         node_steps += tr["n_nodes"] * p["n_inner"]
         new = np.nonzero(st.void & ~before)[0]
         assign_void_segments(tr, st, j, new)
-        R_new = void_resistance(grid, p, st)
+        R_new = void_resistance(grid, p, st, tr)
         if not np.array_equal(R_new, R):
             R = R_new
             u = ir_solve(grid, R)
