@@ -97,7 +97,7 @@ enum { EMS_PC_AUTO = 0, EMS_PC_JACOBI = 1 };       /* IR preconditioner */
 
 /*
  * Extracted power-grid netlist (Sec. III-C: a resistor network with uniform
- * current density per segment).  Segment a -> b is the +x direction of its
+ * current density per segment; via resistors optional, Sec. IV-C).  Segment a -> b is the +x direction of its
  * current density.  Pads are Dirichlet voltage sources; sinks draw current.
  * kappa_factor / sigc_factor, when not NULL, are [n_samples][n_seg] Monte
  * Carlo multipliers (Sec. IV-F) on kappa and sigma_crit of every face / node
@@ -118,6 +118,8 @@ typedef struct {
     const double *sink_I;
     int n_samples;
     const double *kappa_factor, *sigc_factor;
+    const int8_t *seg_via;   /* optional [n_seg]: 1 marks a via resistor (joins two layers; part of
+                                the IR network, of no stress tree); NULL: no explicit vias */
 } ems_grid_desc;
 
 typedef struct ems_ctx ems_ctx;
@@ -266,9 +268,14 @@ ems_status ems_krylov_reduce(ems_ctx *ctx, int q, double eta, int *n_reduced,
                              int *n_fallback);
 
 /*
- * Void growth resistance write-back (Sec. III-D.3, IV-C, late failure):
+ * Void growth resistance write-back (Sec. III-D.3, IV-C).  Late failure:
  * R_s = R0_s + sum over the voids on segment s of
  * max(0, (V_v - W^2 H)/(W H) [rho_Ta/(h_Ta (2H+W)) - rho_Cu/(H W)]).
+ * Early failure (grids with explicit via resistors only): a void at an IR
+ * node that connects through a via to a strictly higher layer (a node's
+ * layer is that of its wire segments) opens the via once its volume exceeds
+ * W^2 H of its segment: the via's resistance becomes the open-circuit
+ * sentinel 1e9 Ohm.
  *   n_segments_changed  optional host: segments (all samples) whose R changed
  */
 ems_status ems_void_update(ems_ctx *ctx, int *n_segments_changed);

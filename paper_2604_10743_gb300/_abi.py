@@ -44,7 +44,8 @@ class EmsGridDesc(ctypes.Structure):
                 ("seg_R0", c_double_p), ("seg_W", c_double_p), ("seg_H", c_double_p), ("seg_L", c_double_p),
                 ("n_pads", ctypes.c_int), ("pad_node", c_int32_p), ("pad_V", c_double_p),
                 ("n_sinks", ctypes.c_int), ("sink_node", c_int32_p), ("sink_I", c_double_p),
-                ("n_samples", ctypes.c_int), ("kappa_factor", c_double_p), ("sigc_factor", c_double_p)]
+                ("n_samples", ctypes.c_int), ("kappa_factor", c_double_p), ("sigc_factor", c_double_p),
+                ("seg_via", ctypes.POINTER(ctypes.c_int8))]
 
 
 class EmsTtfOpts(ctypes.Structure):
@@ -223,5 +224,8 @@ class GridDesc:
         d.n_samples = S
         d.kappa_factor = _ptr(k["kf"], ctypes.c_double)
         d.sigc_factor = _ptr(k["sf"], ctypes.c_double)
+        sv = g.get("seg_via")
+        self.keep["via"] = None if sv is None else np.ascontiguousarray(sv, np.int8)
+        d.seg_via = _ptr(self.keep["via"], ctypes.c_int8)
         self.desc = d
         self.n_samples = max(S, 1)

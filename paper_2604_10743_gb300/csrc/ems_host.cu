@@ -82,6 +82,9 @@ ems_status validate(ems_ctx *c, const ems_params *p, const ems_grid_desc *g) {
             return fail(c, EMS_E_INVAL, "segment end out of range");
         if (g->seg_cells[s] < 1) return fail(c, EMS_E_INVAL, "segment with < 1 FD cell");
     }
+    if (g->seg_via)
+        for (int s = 0; s < g->n_seg; ++s)
+            if (g->seg_via[s] != 0 && g->seg_via[s] != 1) return fail(c, EMS_E_INVAL, "seg_via must be 0 or 1");
     if (!finite_pos(g->seg_R0, g->n_seg) || !finite_pos(g->seg_W, g->n_seg) ||
         !finite_pos(g->seg_H, g->n_seg) || !finite_pos(g->seg_L, g->n_seg))
         return fail(c, EMS_E_INVAL, "non-positive or non-finite segment R, W, H or L");
@@ -150,12 +153,16 @@ int find(std::vector<int> &p, int x) {
 // ---------------------------------------------------------------------------
 ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
     const int ns = g->n_seg;
-    // (layer, node) groups of incident segments, via sorting endpoint records
+    auto is_via = [&](int s) { return g->seg_via && g->seg_via[s]; };
+    // (layer, node) groups of incident wire segments, via sorting endpoint
+    // records (via resistors join layers and belong to no stress tree)
     struct Rec { int32_t layer, node, seg; };
-    std::vector<Rec> rec(2 * (size_t)ns);
+    std::vector<Rec> rec;
+    rec.reserve(2 * (size_t)ns);
     for (int s = 0; s < ns; ++s) {
-        rec[2 * s] = {g->seg_layer[s], g->seg_a[s], s};
-        rec[2 * s + 1] = {g->seg_layer[s], g->seg_b[s], s};
+        if (is_via(s)) continue;
+        rec.push_back({g->seg_layer[s], g->seg_a[s], s});
+        rec.push_back({g->seg_layer[s], g->seg_b[s], s});
     }
     std::sort(rec.begin(), rec.end(), [](const Rec &x, const Rec &y) {
         if (x.layer != y.layer) return x.layer < y.layer;
@@ -185,6 +192,7 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
     tr.tree_of_seg.assign(ns, -1);
     std::vector<std::vector<int32_t>> tsegs;
     for (int s = 0; s < ns; ++s) {
+        if (is_via(s)) continue;
         int r = find(uf, s);
         if (tid_of_root[r] < 0) { tid_of_root[r] = (int32_t)tsegs.size(); tsegs.emplace_back(); }
         tr.tree_of_seg[s] = tid_of_root[r];
@@ -530,6 +538,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.ir_id = cv.take<int32_t>(N); d.ir_par = cv.take<int32_t>(N);
     d.node_x = cv.take<double>(nn); d.node_y = cv.take<double>(nn); d.seg_L = cv.take<double>(ns);
     d.ir_fixed = cv.take<int8_t>(nn); d.T_ir = cv.take<double>(nn);
+    d.up_via = cv.take<int32_t>(nn);
     const int rmax = (c && c->prm.method != EMS_BE) ? 2 * c->prm.krylov_q + 2 : 0;
     if (rmax > 0) {
         d.kr_V = cv.take<unsigned char>((size_t)S * rmax * P * eb);
@@ -744,6 +753,20 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
             }
         for (int q = 0; q < g->n_pads; ++q) fixed[g->pad_node[q]] = 1;
         EMS_CUDA(c, up(D.ir_fixed, fixed.data(), fixed.size(), st));
+        // the via from each IR node up to a strictly higher layer (-1: none);
+        // a node's layer is the layer of its wire segments
+        std::vector<int32_t> nl((size_t)g->n_nodes, -1), upv((size_t)g->n_nodes, -1);
+        if (g->seg_via) {
+            for (int q = 0; q < ns; ++q)
+                if (!g->seg_via[q]) { nl[g->seg_a[q]] = g->seg_layer[q]; nl[g->seg_b[q]] = g->seg_layer[q]; }
+            for (int q = 0; q < ns; ++q) {
+                if (!g->seg_via[q]) continue;
+                const int32_t ea = g->seg_a[q], eb = g->seg_b[q];
+                if (nl[ea] >= 0 && nl[eb] > nl[ea] && upv[ea] < 0) upv[ea] = q;
+                if (nl[eb] >= 0 && nl[ea] > nl[eb] && upv[eb] < 0) upv[eb] = q;
+            }
+        }
+        EMS_CUDA(c, up(D.up_via, upv.data(), upv.size(), st));
         EMS_CUDA(c, cudaStreamSynchronize(st));
     }
     {   // inc_ptr is per node: global CSR over all nodes

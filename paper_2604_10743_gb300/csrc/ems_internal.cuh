@@ -20,6 +20,8 @@
 #define EMS_MAX_VOIDS 256     // compile-time cap on void slots per (tree, sample)
 #define EMS_MAX_RASTER (1024 * 1024)  // thermal raster values held in the workspace
 #define EMS_MAX_PERT 4096             // values of one sample's temperature perturbation raster
+// resistance of a via a void has severed (early failure), Ohm
+constexpr double kOpenCircuit = 1.0e9;
 // polls a grid-barrier wait makes before it gives up (about a second)
 constexpr long long kDefaultWaitLimit = 1LL << 24;
 
@@ -196,6 +198,7 @@ struct Dev {
     double *node_x, *node_y, *seg_L;   // IR node coordinates [n_nodes], segment lengths [n_seg]
     int8_t *ir_fixed;                  // [n_nodes] 1: temperature given (via between layers, or a pad)
     double *T_ir;                      // [n_nodes] IR node temperatures of the last profile
+    int32_t *up_via;                   // [n_nodes] via resistor up to a strictly higher layer, -1 none
 };
 
 }  // namespace ems

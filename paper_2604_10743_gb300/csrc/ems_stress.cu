@@ -1597,18 +1597,24 @@ __global__ void k_reset_R(int n_seg, int S, const double *R0, double *R) {
 }
 
 // one thread per (sample, tree): a tree's voids degrade only its own segments
+// (late failure); a void past the critical volume at an IR node with a via up
+// to a higher layer also opens that via (early failure, explicit vias only)
 __global__ void k_void_R(int n_trees, int S, int maxv, int n_seg, const int32_t *v_count, const int32_t *v_seg,
-                         const double *v_vol, const double *W, const double *H, double rho_Ta, double h_Ta,
-                         double rho_Cu, double *R) {
+                         const int32_t *v_node, const double *v_vol, const double *W, const double *H,
+                         double rho_Ta, double h_Ta, double rho_Cu, const int64_t *toff, const int32_t *ir_id,
+                         const int32_t *up_via, double *R) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= (int64_t)n_trees * S) return;
-    const int s = (int)(k / n_trees);
+    const int s = (int)(k / n_trees), t = (int)(k % n_trees);
     for (int q = 0; q < v_count[k]; ++q) {
         const int sg = v_seg[k * maxv + q];
         const double w = W[sg], h = H[sg];
         const double coef = rho_Ta / (h_Ta * (2.0 * h + w)) - rho_Cu / (h * w);
-        const double dR = (v_vol[k * maxv + q] - w * w * h) / (w * h) * coef;
+        const double vol = v_vol[k * maxv + q];
+        const double dR = (vol - w * w * h) / (w * h) * coef;
         if (dR > 0.0) R[(int64_t)s * n_seg + sg] += dR;
+        const int irn = ir_id[toff[t] + v_node[k * maxv + q]];
+        if (irn >= 0 && up_via[irn] >= 0 && vol > w * w * h) R[(int64_t)s * n_seg + up_via[irn]] = kOpenCircuit;
     }
 }
 
@@ -1862,8 +1868,8 @@ ems_status void_update(ems_ctx *c, int *n_changed) {
     EMS_CUDA(c, cudaGetLastError());
     const int64_t ts = (int64_t)c->n_trees * c->S;
     k_void_R<<<(unsigned)((ts + 255) / 256), 256, 0, st>>>(c->n_trees, c->S, c->maxv, c->n_seg, d.v_count,
-                                                           d.v_seg, d.v_vol, d.seg_W, d.seg_H, p.rho_Ta, p.h_Ta,
-                                                           p.rho_Cu, d.R);
+                                                           d.v_seg, d.v_node, d.v_vol, d.seg_W, d.seg_H, p.rho_Ta,
+                                                           p.h_Ta, p.rho_Cu, d.toff, d.ir_id, d.up_via, d.R);
     ++c->launches;
     EMS_CUDA(c, cudaGetLastError());
     EMS_CUDA(c, cudaMemsetAsync(d.counters + 1, 0, sizeof(int32_t), st));

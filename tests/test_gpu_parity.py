@@ -601,3 +601,32 @@ def test_cluster_chain_kernel_against_oracle(cells, cl):
         assert all(abs(p_ - q_) <= 2 for p_, q_ in zip(gv, ov)), t
     _metric_close(r, ref)
     eng.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_via_mesh_early_failure(prec):
+    """Two-layer mesh with explicit via resistors: vias carry current but no
+    stress; voids under a via that pass the critical volume open it (early
+    failure).  Stress, voids, opened vias, drops and TTF against the oracle."""
+    from paper_2604_10743_gb300 import EMS_F32, EMS_F64
+    g = es.via_mesh()
+    p = es.default_params()
+    eng = _engine(p, g, precision=EMS_F32 if prec == "f32" else EMS_F64)
+    assert eng.n_trees == 16
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True)
+    R = eng.resistance()[0]
+    opened = np.nonzero(ref["R"] >= F.R_OPEN)[0]
+    assert opened.size >= 3 and np.all(g["seg_via"][opened] == 1)
+    assert np.array_equal(np.nonzero(R >= F.R_OPEN)[0], opened)
+    if prec == "f64":
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+        gpu, ora, _ = _void_sets(eng, ref)
+        assert gpu == ora
+        assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    else:
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+        nt, _ = _f32_voids(eng, ref)
+        assert nt >= 12
+    _metric_close(r, ref)
+    eng.close()

@@ -122,7 +122,7 @@ class _Script:
     def current_density(self, grid, u, R):
         return np.full(len(grid["seg_a"]), float(self.solves))
 
-    def void_resistance(self, grid, p, st):
+    def void_resistance(self, grid, p, st, tr=None):
         R = np.array(grid["seg_R0"], float) + self.bumps[self.step]
         self.step += 1
         return R
