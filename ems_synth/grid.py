@@ -302,3 +302,102 @@ def config(name, **kw):
     if name == "large":
         return large_grid(**kw)
     raise ValueError(name)
+
+
+def spice_netlist(seed=7, n_trees=4, n_seg=24, pitch_nm=10000, W=(0.5e-6, 0.8e-6), H=(0.2e-6, 0.3e-6),
+                  R_via=1.0, n_vias=4, I_lo=0.5e-3, I_hi=2e-3, dx=0.5e-6):
+    """A synthetic power-grid netlist in SPICE form with junction-heavy trees.
+
+    Layer 1 holds n_trees random Manhattan trees (n_seg segments of 1-3
+    lattice steps each, grown from random existing nodes, so many nodes are
+    junctions); n_vias of each tree's nodes have a via (resistor R_via) up to
+    layer 2, where one strap per tree links the via landings in order and
+    carries a supply pad at each end.  Every layer-1 node other than the via
+    ones draws a U(I_lo, I_hi) sink.  Node names n<layer>_<x>_<y> in nm.
+
+    Returns (text, grid): the netlist text and the same grid as a dict, nodes
+    numbered by first appearance in the text, segments and sources in text
+    order (what a SPICE reader produces).
+    """
+    rng = _rng(seed)
+    rho = default_params()["rho_Cu"]
+    names, xs, ys, layers = [], [], [], []
+    index = {}
+
+    def node(layer, x, y):
+        nm = "n%d_%d_%d" % (layer, x, y)
+        if nm not in index:
+            index[nm] = len(names)
+            names.append(nm); xs.append(x * 1e-9); ys.append(y * 1e-9); layers.append(layer)
+        return nm
+
+    lines = ["* synthetic junction-heavy power grid (seed %d)" % seed]
+    seg = dict(a=[], b=[], layer=[], cells=[], R=[], W=[], H=[], L=[], via=[])
+    pads, sinks = [], []
+
+    def wire(layer, n1, n2):
+        # length = distance of the node coordinates in metres (as a reader computes it)
+        i1, i2 = index[n1], index[n2]
+        L = float(np.hypot(xs[i2] - xs[i1], ys[i2] - ys[i1]))
+        R = rho * L / (W[layer - 1] * H[layer - 1])
+        lines.append("R%d %s %s %.17g" % (len(seg["a"]) + 1, n1, n2, R))
+        seg["a"].append(index[n1]); seg["b"].append(index[n2]); seg["layer"].append(layer)
+        seg["cells"].append(max(1, int(math.floor(L / dx + 0.5)))); seg["R"].append(R)
+        seg["W"].append(W[layer - 1]); seg["H"].append(H[layer - 1]); seg["L"].append(L); seg["via"].append(0)
+
+    occupied = set()
+    for t in range(n_trees):
+        ox = t * 40 * pitch_nm
+        pts = [(ox, 0)]
+        occupied.add((ox, 0))
+        tree_nodes = [node(1, ox, 0)]
+        while len(tree_nodes) - 1 < n_seg:
+            k = int(rng.integers(len(pts)))
+            x0, y0 = pts[k]
+            dxs, dys = [(1, 0), (-1, 0), (0, 1), (0, -1)][int(rng.integers(4))]
+            steps = int(rng.integers(1, 4))
+            path = [(x0 + dxs * pitch_nm * q, y0 + dys * pitch_nm * q) for q in range(1, steps + 1)]
+            if any(pp in occupied for pp in path) or not (ox - 15 * pitch_nm <= path[-1][0] <= ox + 15 * pitch_nm):
+                continue
+            occupied.update(path)
+            x1, y1 = path[-1]
+            n1 = tree_nodes[k]
+            n2 = node(1, x1, y1)
+            wire(1, n1, n2)
+            pts.append((x1, y1))
+            tree_nodes.append(n2)
+        vias = sorted(rng.choice(np.arange(1, len(tree_nodes)), size=n_vias, replace=False).tolist())
+        landing = []
+        for v in vias:
+            x, y = pts[v]
+            up = node(2, x, y)
+            lines.append("R%d %s %s %.17g" % (len(seg["a"]) + 1, tree_nodes[v], up, R_via))
+            seg["a"].append(index[tree_nodes[v]]); seg["b"].append(index[up]); seg["layer"].append(1)
+            seg["cells"].append(1); seg["R"].append(R_via); seg["W"].append(0.2e-6); seg["H"].append(0.2e-6)
+            seg["L"].append(0.2e-6); seg["via"].append(1)
+            landing.append((x, y, up))
+        landing.sort()
+        for (xa, ya, na), (xb, yb, nb) in zip(landing[:-1], landing[1:]):
+            wire(2, na, nb)
+        for end in (landing[0][2], landing[-1][2]):
+            lines.append("V%d %s 0 1.0" % (len(pads) + 1, end))
+            pads.append(index[end])
+        via_nodes = {tree_nodes[v] for v in vias}
+        for nm in tree_nodes:
+            if nm not in via_nodes:
+                I = float(rng.uniform(I_lo, I_hi))
+                lines.append("I%d %s 0 %.17g" % (len(sinks) + 1, nm, I))
+                sinks.append((index[nm], I))
+    lines.append(".end")
+    g = dict(
+        N=0, pitch=pitch_nm * 1e-9,
+        node_x=np.array(xs), node_y=np.array(ys),
+        seg_a=np.array(seg["a"], np.int32), seg_b=np.array(seg["b"], np.int32),
+        seg_layer=np.array(seg["layer"], np.int32), seg_cells=np.array(seg["cells"], np.int32),
+        seg_R0=np.array(seg["R"]), seg_W=np.array(seg["W"]), seg_H=np.array(seg["H"]), seg_L=np.array(seg["L"]),
+        seg_via=np.array(seg["via"], np.int8),
+        pad_node=np.array(pads, np.int32), pad_V=np.ones(len(pads)),
+        sink_node=np.array([q[0] for q in sinks], np.int32), sink_I=np.array([q[1] for q in sinks]),
+        thermal=None, kappa_factor=None, sigc_factor=None,
+    )
+    return "\n".join(lines) + "\n", g

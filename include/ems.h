@@ -124,6 +124,42 @@ typedef struct {
 
 typedef struct ems_ctx ems_ctx;
 
+/*
+ * SPICE power-grid netlist reader (the paper's PNA-to-SPICE input with every
+ * via resistor kept, Sec. IV-A and IV-C).  Elements, one per line:
+ *   R<name> <node> <node> <ohm>   a wire when both nodes are on one metal
+ *                                 layer, else a via resistor
+ *   V<name> <node> 0 <volt>       a supply pad
+ *   I<name> <node> 0 <amp>        a sink drawing <amp> from <node>
+ * Node names n<layer>_<x>_<y> give the metal layer (1..n_layers) and the
+ * position in integer units of coord_unit; "0" / "gnd" is ground.  Lines
+ * starting with '*' or '.' are skipped.  A wire's length is the distance of
+ * its nodes, its width / thickness those of its layer, its finite-difference
+ * cells max(1, floor(L / dx + 1/2)); a via gets via_W x via_W, length via_H, one
+ * cell.  Nodes are numbered in order of first appearance, segments and
+ * sources in file order.
+ */
+typedef struct {
+    int n_layers;              /* metal layers named in the netlist, 1..n_layers (<= 64) */
+    const double *W, *H;       /* [n_layers] wire width and thickness per layer (m) */
+    double via_W, via_H;       /* via side and height (m) */
+    double coord_unit;         /* metres per unit of the node-name coordinates */
+    double dx;                 /* target finite-difference cell length (m) */
+} ems_spice_opts;
+
+typedef struct ems_netlist ems_netlist;
+
+/* Parse len bytes of text.  *out receives the netlist (also on EMS_E_INVAL,
+ * so that ems_netlist_error() can say which line failed); free it with
+ * ems_netlist_free.  EMS_E_INVAL: bad options, a malformed or unsupported
+ * line, a resistor to ground, no resistors or no voltage source. */
+ems_status ems_spice_parse(const char *text, size_t len, const ems_spice_opts *opts, ems_netlist **out);
+/* A grid descriptor whose arrays point into the netlist (valid until freed;
+ * n_samples 0, no Monte Carlo factors). */
+ems_status ems_netlist_desc(const ems_netlist *nl, ems_grid_desc *desc);
+const char *ems_netlist_error(const ems_netlist *nl);
+void ems_netlist_free(ems_netlist *nl);
+
 /* Bytes of device workspace a context needs for this grid (with the Monte
  * Carlo layout params->window_samples selects).  Returns 0 if the
  * descriptor is invalid. */

@@ -48,6 +48,11 @@ class EmsGridDesc(ctypes.Structure):
                 ("seg_via", ctypes.POINTER(ctypes.c_int8))]
 
 
+class EmsSpiceOpts(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("W", c_double_p), ("H", c_double_p), ("via_W", ctypes.c_double),
+                ("via_H", ctypes.c_double), ("coord_unit", ctypes.c_double), ("dx", ctypes.c_double)]
+
+
 class EmsTtfOpts(ctypes.Structure):
     _fields_ = [("screen", ctypes.c_int), ("n_outer", ctypes.c_int), ("no_graph", ctypes.c_int)]
 
@@ -68,7 +73,8 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_krylov_reduce", "ems_void_update", "ems_ttf", "ems_get_sigma", "ems_get_currents",
            "ems_get_resistance", "ems_get_voids", "ems_state_export", "ems_state_import",
            "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc", "ems_joule_profile", "ems_set_wait_limit",
-           "ems_get_node_temperature", "ems_set_thermal_perturbation",
+           "ems_get_node_temperature", "ems_set_thermal_perturbation", "ems_spice_parse", "ems_netlist_desc",
+           "ems_netlist_error", "ems_netlist_free",
            # include/ems_surrogate.h
            "ems_mlp_create", "ems_mlp_destroy", "ems_mlp_last_error", "ems_mlp_param_count",
            "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_fit_norm", "ems_mlp_gradients",
@@ -125,6 +131,14 @@ def lib(path=None):
     L.ems_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.ems_state_import.restype = S
     L.ems_state_import.argtypes = [vp, vp, ctypes.c_size_t]
+    L.ems_spice_parse.restype = S
+    L.ems_spice_parse.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(EmsSpiceOpts), ctypes.POINTER(vp)]
+    L.ems_netlist_desc.restype = S
+    L.ems_netlist_desc.argtypes = [vp, ctypes.POINTER(EmsGridDesc)]
+    L.ems_netlist_error.restype = ctypes.c_char_p
+    L.ems_netlist_error.argtypes = [vp]
+    L.ems_netlist_free.restype = None
+    L.ems_netlist_free.argtypes = [vp]
     L.ems_set_thermal_perturbation.restype = S
     L.ems_set_thermal_perturbation.argtypes = [vp, c_double_p, S, S]
     L.ems_set_wait_limit.restype = S

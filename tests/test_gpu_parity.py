@@ -630,3 +630,30 @@ def test_via_mesh_early_failure(prec):
         assert nt >= 12
     _metric_close(r, ref)
     eng.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_spice_netlist_junction_heavy_trees(prec):
+    """A synthetic junction-heavy SPICE netlist read by the library's parser
+    (branched layer-1 trees, via resistors, layer-2 straps with pads), run on
+    the GPU, against the oracle run of the generator's own grid."""
+    from paper_2604_10743_gb300 import EMS_F32, EMS_F64
+    from paper_2604_10743_gb300.spice import parse_spice
+    text, g = es.spice_netlist()
+    gp = parse_spice(text, W=[0.5e-6, 0.8e-6], H=[0.2e-6, 0.3e-6])
+    p = es.default_params(n_outer=16, sigma_crit=300e6)
+    eng = _engine(p, gp, precision=EMS_F32 if prec == "f32" else EMS_F64)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True)
+    assert ref["n_voids"] >= 3
+    if prec == "f64":
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+        gpu, ora, _ = _void_sets(eng, ref)
+        assert gpu == ora
+        assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    else:
+        assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL32
+        nt, _ = _f32_voids(eng, ref)
+        assert nt >= 6
+    _metric_close(r, ref)
+    eng.close()
