@@ -305,7 +305,7 @@ def config(name, **kw):
 
 
 def spice_netlist(seed=7, n_trees=4, n_seg=24, pitch_nm=10000, W=(0.5e-6, 0.8e-6), H=(0.2e-6, 0.3e-6),
-                  R_via=1.0, n_vias=4, I_lo=0.5e-3, I_hi=2e-3, dx=0.5e-6):
+                  R_via=1.0, n_vias=4, I_lo=0.2e-3, I_hi=0.7e-3, dx=0.5e-6):
     """A synthetic power-grid netlist in SPICE form with junction-heavy trees.
 
     Layer 1 holds n_trees random Manhattan trees (n_seg segments of 1-3
