@@ -312,13 +312,17 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
 void chain_shape(int64_t n, int prec, int method, int *T, int *M, int *CL) {
     const int64_t target = prec == EMS_F32 ? 448 : 192;
     *CL = 1;
-    // FP32 backward-Euler chains longer than one register-resident CTA holds:
-    // a cluster of 2, 4 or 8 CTAs of <= 320 threads, 16 nodes per thread
-    if (prec == EMS_F32 && method == EMS_BE && n > 320 * 16 && !getenv("EMS_NO_CLUSTER")) {
-        const int64_t th = (n + 15) / 16;
+    // backward-Euler chains longer than one register-resident CTA holds
+    // (FP32: 5,120 nodes; FP64: past the streaming kernel's 16,384): a
+    // cluster of 2, 4 or 8 CTAs of <= 320 threads, 16 (FP32) or 8 (FP64)
+    // nodes per thread
+    const int64_t one_cta = prec == EMS_F32 ? 320 * 16 : 256 * 64;
+    if (method == EMS_BE && n > one_cta && !getenv("EMS_NO_CLUSTER")) {
+        const int mc = prec == EMS_F32 ? 16 : 8;
+        const int64_t th = (n + mc - 1) / mc;
         for (int cl : {2, 4, 8}) {
             const int64_t t = ((th + cl - 1) / cl + 31) / 32 * 32;
-            if (t <= 320) { *T = (int)(t * cl); *M = 16; *CL = cl; return; }
+            if (t <= 320) { *T = (int)(t * cl); *M = mc; *CL = cl; return; }
         }
     }
     // FP32 chains the register-resident kernel holds: 16 nodes per thread

@@ -983,9 +983,10 @@ __global__ void __launch_bounds__(RegMaxThreads<M>::value, 1) k_chain_reg(ChainA
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
+template <typename R>
 struct ClSlots {                      // written by the other CTAs of the cluster (push), read locally
-    float fA[8], fB[8], bA[8], bB[8]; // each rank's forward / backward aggregate of its chunks
-    float last_left, first_right;     // stress at the left neighbour CTA's last / right one's first node
+    R fA[8], fB[8], bA[8], bB[8];     // each rank's forward / backward aggregate of its chunks
+    R last_left, first_right;         // stress at the left neighbour CTA's last / right one's first node
     int flags[8];                     // each rank: bit 0 a node reached its threshold, bit 1 near the guard
     double best[8];                   // each rank's argmax of sigma - sigma_crit (nucleation)
     int arg[8];
@@ -995,20 +996,20 @@ struct ClSlots {                      // written by the other CTAs of the cluste
 
 // composition of the ranks' affine maps x -> A + B x applied to 0, from the
 // local copies: forward over ranks < r left to right, backward over ranks > r
-template <int CL>
-__device__ __forceinline__ float cl_carry_fwd(const ClSlots &sl, int rank) {
-    float z = 0.0f;
+template <typename R, int CL>
+__device__ __forceinline__ R cl_carry_fwd(const ClSlots<R> &sl, int rank) {
+    R z = R(0);
 #pragma unroll
     for (int q = 0; q < CL; ++q)
-        if (q < rank) z = fmaf(sl.fB[q], z, sl.fA[q]);
+        if (q < rank) z = fmx(sl.fB[q], z, sl.fA[q]);
     return z;
 }
-template <int CL>
-__device__ __forceinline__ float cl_carry_bwd(const ClSlots &sl, int rank) {
-    float x = 0.0f;
+template <typename R, int CL>
+__device__ __forceinline__ R cl_carry_bwd(const ClSlots<R> &sl, int rank) {
+    R x = R(0);
 #pragma unroll
     for (int q = CL - 1; q >= 0; --q)
-        if (q > rank) x = fmaf(sl.bB[q], x, sl.bA[q]);
+        if (q > rank) x = fmx(sl.bB[q], x, sl.bA[q]);
     return x;
 }
 
@@ -1016,17 +1017,16 @@ __device__ __forceinline__ float cl_carry_bwd(const ClSlots &sl, int rank) {
 // CTA's carry-in composed in: returns the carry entering this thread's chunk
 // and (thread 0 of the CTA, once all threads passed the barrier) the CTA's
 // aggregate map in *aggA, *aggB.  dir 0: left to right, 1: right to left.
-template <int DIR>
-__device__ __forceinline__ void cta_scan(float A, float B, float *sA, float *sB, float &exA, float &exB,
-                                         float &aggA, float &aggB) {
+template <int DIR, typename R>
+__device__ __forceinline__ void cta_scan(R A, R B, R *sA, R *sB, R &exA, R &exB, R &aggA, R &aggB) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // inclusive warp scan
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const float Ao = DIR == 0 ? __shfl_up_sync(full, A, d) : __shfl_down_sync(full, A, d);
-        const float Bo = DIR == 0 ? __shfl_up_sync(full, B, d) : __shfl_down_sync(full, B, d);
-        if (DIR == 0 ? lane >= d : lane + d < 32) { A = fmaf(B, Ao, A); B = B * Bo; }
+        const R Ao = DIR == 0 ? __shfl_up_sync(full, A, d) : __shfl_down_sync(full, A, d);
+        const R Bo = DIR == 0 ? __shfl_up_sync(full, B, d) : __shfl_down_sync(full, B, d);
+        if (DIR == 0 ? lane >= d : lane + d < 32) { A = fmx(B, Ao, A); B = B * Bo; }
     }
     const int edge = DIR == 0 ? 31 : 0;
     if (lane == edge) { sA[DIR * 32 + w] = A; sB[DIR * 32 + w] = B; }
@@ -1034,36 +1034,35 @@ __device__ __forceinline__ void cta_scan(float A, float B, float *sA, float *sB,
     // composite of the earlier warps (fwd: warps < w; bwd: warps > w), as a map
     const int k = DIR == 0 ? lane : nw - 1 - lane;
     const bool take = DIR == 0 ? k < w : k > w;
-    float a = take && k >= 0 && k < nw ? sA[DIR * 32 + k] : 0.0f, b = take && k >= 0 && k < nw ? sB[DIR * 32 + k] : 1.0f;
+    R a = take && k >= 0 && k < nw ? sA[DIR * 32 + k] : R(0), b = take && k >= 0 && k < nw ? sB[DIR * 32 + k] : R(1);
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const float ao = __shfl_up_sync(full, a, d), bo = __shfl_up_sync(full, b, d);
-        if (lane >= d) { a = fmaf(b, ao, a); b = b * bo; }
+        const R ao = __shfl_up_sync(full, a, d), bo = __shfl_up_sync(full, b, d);
+        if (lane >= d) { a = fmx(b, ao, a); b = b * bo; }
     }
-    const float cwA = __shfl_sync(full, a, 31), cwB = __shfl_sync(full, b, 31);
+    const R cwA = __shfl_sync(full, a, 31), cwB = __shfl_sync(full, b, 31);
     // this thread's exclusive map within the CTA: (earlier lanes) o (earlier warps)
-    const float iA = fmaf(B, cwA, A), iB = B * cwB;            // inclusive
-    const float pA = DIR == 0 ? __shfl_up_sync(full, iA, 1) : __shfl_down_sync(full, iA, 1);
-    const float pB = DIR == 0 ? __shfl_up_sync(full, iB, 1) : __shfl_down_sync(full, iB, 1);
+    const R iA = fmx(B, cwA, A), iB = B * cwB;                 // inclusive
+    const R pA = DIR == 0 ? __shfl_up_sync(full, iA, 1) : __shfl_down_sync(full, iA, 1);
+    const R pB = DIR == 0 ? __shfl_up_sync(full, iB, 1) : __shfl_down_sync(full, iB, 1);
     const int first = DIR == 0 ? 0 : 31;
     exA = lane == first ? cwA : pA;
     exB = lane == first ? cwB : pB;
     // the CTA aggregate (every warp's map composed), thread 0
-    aggA = 0.0f; aggB = 1.0f;
+    aggA = R(0); aggB = R(1);
     if (threadIdx.x == 0) {
         if (DIR == 0)
-            for (int q = 0; q < nw; ++q) { aggA = fmaf(sB[q], aggA, sA[q]); aggB = sB[q] * aggB; }
+            for (int q = 0; q < nw; ++q) { aggA = fmx(sB[q], aggA, sA[q]); aggB = sB[q] * aggB; }
         else
-            for (int q = nw - 1; q >= 0; --q) { aggA = fmaf(sB[32 + q], aggA, sA[32 + q]); aggB = sB[32 + q] * aggB; }
+            for (int q = nw - 1; q >= 0; --q) { aggA = fmx(sB[32 + q], aggA, sA[32 + q]); aggB = sB[32 + q] * aggB; }
     }
 }
 
-// Cluster version of chain_factor (increment form, R = float): every CTA
-// calls it; g = team thread, TT = team size.  Two cluster barriers.
-template <int M>
-__device__ __noinline__ void chain_factor_cl(const ChainArgs<float> &a, double dt, int n, int TT, int g, int64_t cb,
-                                             int64_t cs, int64_t ps, ClSlots *sl, int rank) {
-    using R = float;
+// Cluster version of chain_factor (increment form): every CTA calls it;
+// g = team thread, TT = team size.  Two cluster barriers.
+template <typename R, int M>
+__device__ __noinline__ void chain_factor_cl(const ChainArgs<R> &a, double dt, int n, int TT, int g, int64_t cb,
+                                             int64_t cs, int64_t ps, ClSlots<R> *sl, int rank) {
     cg::cluster_group cl = cg::this_cluster();
     __shared__ double sfm[4][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1143,10 +1142,8 @@ __device__ __noinline__ void chain_factor_cl(const ChainArgs<float> &a, double d
     }
 }
 
-template <int CL>
-__global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
-    constexpr int M = 16;
-    using R = float;
+template <typename R, int M, int CL>
+__global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
     __shared__ R sA[64], sB[64], sL[32], sR[32];
     __shared__ double sv[32];
     __shared__ int si[32];
@@ -1155,7 +1152,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
     __shared__ double s_vol[EMS_MAX_VOIDS], s_coef[EMS_MAX_VOIDS];
     __shared__ double s_dt, s_tbase, s_gthr;
     __shared__ int s_rs, s_sbase, s_refac;
-    __shared__ ClSlots sl;
+    __shared__ ClSlots<R> sl;
     cg::cluster_group cl = cg::this_cluster();
 
     const int rank = (int)cl.block_rank();
@@ -1183,7 +1180,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
         return r;
     };
     double thrmin = thr_min();
-    R sg[M], cc[M];
+    R sg[M], cc[M];                   // state and (FP32) its Kahan compensation
 #pragma unroll
     for (int k = 0; k < M; ++k) { sg[k] = a.sig[ps + (int64_t)k * TT + g]; cc[k] = R(0); }
 
@@ -1222,7 +1219,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
     cl.sync();                                   // every CTA has read dirty / fdt
     if (g == 0) { a.dirty[st] = 0; a.fdt[st] = s_dt; }
     if (s_refac) {
-        chain_factor_cl<M>(a, s_dt, n, TT, g, cb, cs, ps, &sl, rank);
+        chain_factor_cl<R, M>(a, s_dt, n, TT, g, cb, cs, ps, &sl, rank);
     } else {
         const double dt = s_dt;
 #pragma unroll
@@ -1248,7 +1245,10 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
             cbt[k] = a.beta[pk];
             cpf[k] = a.Pf[pk];
             cpb[k] = a.Pb[pk];
-            cth[k] = ((vmask >> k) & 1u) ? a.dtl[pk] : (i < n ? __double2float_rd(a.thr[cs + i]) : INFINITY);
+            cth[k] = ((vmask >> k) & 1u) ? a.dtl[pk]
+                                          : (i < n ? (sizeof(R) == 4 ? (R)__double2float_rd(a.thr[cs + i])
+                                                                     : (R)a.thr[cs + i])
+                                                   : (R)INFINITY);
         }
         g_next = g + 1 < TT ? a.dtg[ps + g + 1] : R(0);
     };
@@ -1288,13 +1288,13 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
             gk = gk1;
         }
         // forward carries: within the CTA, then across the cluster
-        float exA, exB, agA, agB;
-        cta_scan<0>(z, cpf[M - 1], sA, sB, exA, exB, agA, agB);
+        R exA, exB, agA, agB;
+        cta_scan<0, R>(z, cpf[M - 1], sA, sB, exA, exB, agA, agB);
         agA = __shfl_sync(0xffffffffu, agA, 0);
         agB = __shfl_sync(0xffffffffu, agB, 0);
-        if (c < CL) { ClSlots *o = cl.map_shared_rank(&sl, c); o->fA[rank] = agA; o->fB[rank] = agB; }
+        if (c < CL) { ClSlots<R> *o = cl.map_shared_rank(&sl, c); o->fA[rank] = agA; o->fB[rank] = agB; }
         cl.sync();
-        const float cf = fmaf(exB, cl_carry_fwd<CL>(sl, rank), exA);
+        const R cf = fmx(exB, cl_carry_fwd<R, CL>(sl, rank), exA);
         R x = R(0);
 #pragma unroll
         for (int k = M - 1; k >= 0; --k) {
@@ -1302,19 +1302,23 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
             x = fmx(cp[k] * gk1, x, fmx(cpf[k], cf, zr[k]));
             zr[k] = x;
         }
-        float bxA, bxB, bgA, bgB;
-        cta_scan<1>(x, cpb[0], sA, sB, bxA, bxB, bgA, bgB);
+        R bxA, bxB, bgA, bgB;
+        cta_scan<1, R>(x, cpb[0], sA, sB, bxA, bxB, bgA, bgB);
         bgA = __shfl_sync(0xffffffffu, bgA, 0);
         bgB = __shfl_sync(0xffffffffu, bgB, 0);
-        if (c < CL) { ClSlots *o = cl.map_shared_rank(&sl, c); o->bA[rank] = bgA; o->bB[rank] = bgB; }
+        if (c < CL) { ClSlots<R> *o = cl.map_shared_rank(&sl, c); o->bA[rank] = bgA; o->bB[rank] = bgB; }
         cl.sync();
-        const float cr = fmaf(bxB, cl_carry_bwd<CL>(sl, rank), bxA);
+        const R cr = fmx(bxB, cl_carry_bwd<R, CL>(sl, rank), bxA);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            const R y = fmx(cpb[k], cr, zr[k]) - cc[k];
-            const R tt = sg[k] + y;
-            cc[k] = (tt - sg[k]) - y;
-            sg[k] = tt;
+            if constexpr (sizeof(R) == 4) {               // compensated (Kahan) FP32 update
+                const R y = fmx(cpb[k], cr, zr[k]) - cc[k];
+                const R tt = sg[k] + y;
+                cc[k] = (tt - sg[k]) - y;
+                sg[k] = tt;
+            } else {
+                sg[k] += fmx(cpb[k], cr, zr[k]);
+            }
         }
         // void growth by the Robin leak (owner thread only)
         if (vmask) {
@@ -1352,7 +1356,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
                 }
             }
             block_argmax(best, arg, sv, si);
-            if (c < CL) { ClSlots *o = cl.map_shared_rank(&sl, c); o->best[rank] = best; o->arg[rank] = arg; }
+            if (c < CL) { ClSlots<R> *o = cl.map_shared_rank(&sl, c); o->best[rank] = best; o->arg[rank] = arg; }
 #pragma unroll
             for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * TT + g] = sg[k];
             cl.sync();
@@ -1412,7 +1416,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<float> a) {
         if (refac_from >= 0) {
             cl.sync();                           // the new threshold is written; every CTA is here
             const double dtf = promoted ? a.dt : s_dt;
-            chain_factor_cl<M>(a, dtf, n, TT, g, cb, cs, ps, &sl, rank);
+            chain_factor_cl<R, M>(a, dtf, n, TT, g, cb, cs, ps, &sl, rank);
             thrmin = thr_min();
             if (c == 0) s_gthr = a.guard * thrmin;
             load();
@@ -1709,7 +1713,9 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
         a.n_bucket = (int)b.trees.size();
         if (b.chain && b.CL > 1) {
             // one thread-block cluster of CL CTAs per (tree, sample)
-            if constexpr (kDelta) {
+            {
+                constexpr int MC = sizeof(R) == 4 ? 16 : 8;
+                if (b.M != MC) return fail(c, EMS_E_STATE, "cluster chain layout with an unexpected chunk length");
                 cudaLaunchConfig_t cfg = {};
                 cudaLaunchAttribute at[1];
                 at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1719,14 +1725,12 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
                 cfg.stream = c->stream;
                 cfg.attrs = at;
                 cfg.numAttrs = 1;
-                cudaError_t e = b.CL == 2 ? cudaLaunchKernelEx(&cfg, k_chain_cl<2>, a)
-                              : b.CL == 4 ? cudaLaunchKernelEx(&cfg, k_chain_cl<4>, a)
-                                          : cudaLaunchKernelEx(&cfg, k_chain_cl<8>, a);
+                cudaError_t e = b.CL == 2 ? cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 2>, a)
+                              : b.CL == 4 ? cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 4>, a)
+                                          : cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 8>, a);
                 EMS_CUDA(c, e);
                 ++c->launches;
                 continue;
-            } else {
-                return fail(c, EMS_E_STATE, "cluster chain layout needs the FP32 path");
             }
         }
         if (b.chain) {

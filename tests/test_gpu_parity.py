@@ -657,3 +657,24 @@ def test_spice_netlist_junction_heavy_trees(prec):
         assert nt >= 6
     _metric_close(r, ref)
     eng.close()
+
+
+def test_cluster_chain_kernel_fp64_full_chip_length():
+    """FP64 stripes of the full chip's length (20,469 nodes) are past the
+    FP64 streaming kernel's reach: one 8-CTA cluster per stripe, 8 nodes per
+    thread, increment form in FP64, against the oracle at the FP64 bar."""
+    g = es.stripe_mesh(8, 20e-6)
+    g["seg_cells"][:] = 2924
+    t = es.tiny_grid()
+    g["pad_node"], g["pad_V"], g["sink_node"], g["sink_I"] = t["pad_node"], t["pad_V"], t["sink_node"], t["sink_I"]
+    g["thermal"] = es.hotspot_raster(np.random.default_rng(11), 140e-6, 2, 360.0, 20.0, 40.0, 0.2, nx=33, ny=33)
+    p = es.default_params(n_outer=3, n_inner=64, sigma_crit=250e6)
+    eng = _engine(p, g, max_voids=64)
+    r = eng.ttf()
+    ref = F.run_ttf(g, p, keep_state=True, n_threads=8)
+    assert ref["n_voids"] >= 16
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+    gpu, ora, _ = _void_sets(eng, ref)
+    assert gpu == ora
+    assert np.abs(r["drops"][0] - ref["drops"]).max() < 1e-9
+    eng.close()
