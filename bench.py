@@ -145,6 +145,28 @@ def full_chip(n_samples, seed=5):
     return es.grid.large_grid(seed=seed, n_samples=n_samples)
 
 
+def tuned_rules(p, prec, args):
+    """Chain shapes of the full chip picked by the autotuner (ems_autotune),
+    measured on a 2-sample copy of the workload: the chains and their launch
+    groups are the same, the samples only multiply the launch size."""
+    from paper_2604_10743_gb300.engine import Engine
+    t0 = time.perf_counter()
+    e = Engine(p, full_chip(2), precision=prec, max_voids=args.max_voids)
+    e.ir_solve()
+    table = e.autotune(n_steps=32, max_samples=2)
+    e.close()
+    return table, time.perf_counter() - t0
+
+
+def kernel_name(rule, prec_name):
+    r = "float" if prec_name == "f32" else "double"
+    if rule["kernel"] == "cluster":
+        return "k_chain_cl<%s,%d,%d>" % (r, rule["M"], rule["CL"])
+    if rule["kernel"] == "register":
+        return "k_chain_reg<%d>" % rule["M"]
+    return "k_chain<%s,%d,%s>" % (r, rule["M"], "shared" if rule["kernel"] == "shared" else "global")
+
+
 def run_mine(args):
     import numpy as np
     import torch
@@ -161,9 +183,10 @@ def run_mine(args):
     S, W = args.samples, args.window
     p = es.default_params()
     prec = EMS_F32 if args.precision == "f32" else EMS_F64
+    rules, tune_s = ([], 0.0) if args.no_tune else tuned_rules(p, prec, args)
     g = full_chip(S)
     t0 = time.perf_counter()
-    eng = Engine(p, g, precision=prec, max_voids=args.max_voids, window=W)
+    eng = Engine(p, g, precision=prec, max_voids=args.max_voids, window=W, chain_rules=rules)
     torch.cuda.synchronize()
     t_load = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
@@ -208,6 +231,9 @@ def run_mine(args):
     # state in + out (2w), plus the per-launch coefficient arrays.
     w = 4 if prec == EMS_F32 else 8
     n_inner = p["n_inner"]
+    from paper_2604_10743_gb300 import _abi as A
+    shape = rules[0] if rules else A.chain_candidates(int(eng.n_stress // eng.n_trees), prec)[0]
+    kname = kernel_name(shape, args.precision)
     n_coef = 7 if prec == EMS_F32 else 6
     nodes_launch = eng.n_stress * (S / n_win)
     alg_bytes_launch = nodes_launch * (2 * w * n_inner + n_coef * w)
@@ -219,15 +245,15 @@ def run_mine(args):
     if os.path.exists(tf):
         try:
             t = json.load(open(tf))
-            if t.get("precision") == args.precision and t.get("kernel") == "k_chain_cl<4>":
+            if t.get("precision") == args.precision and t.get("kernel") == kname:
                 traffic = t.get("bytes_per_launch")
         except (OSError, ValueError):
             pass
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src if src == "measured" else "fallback 6.8 TB/s",
-            "kernel": "k_chain_cl<4> (stress advance: one 4-CTA cluster per (stripe, sample), one launch = "
-                      "256 BE steps of every stripe of %d samples)" % (S // n_win),
+            "kernel": "%s (stress advance, the autotuner's shape for the 20,471-node stripes; one launch = "
+                      "256 BE steps of every stripe of %d samples)" % (kname, S // n_win),
             "alg_bytes_per_launch": int(alg_bytes_launch), "launch_ms": round(per_launch_ms, 3)}
 
     # end to end through the public API with host buffers: the netlist, the
@@ -244,7 +270,7 @@ def run_mine(args):
         ke = 3
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e = Engine(p, g, precision=prec, max_voids=args.max_voids, window=W)
+        e = Engine(p, g, precision=prec, max_voids=args.max_voids, window=W, chain_rules=rules)
         for _ in range(ke):
             r = e.ttf(n_outer=1)                      # results come back to the host
         torch.cuda.synchronize()
@@ -264,7 +290,7 @@ def run_mine(args):
     # chosen = the FP32 path timed above (cluster kernel, compensated sums)
     pvc = None
     if not args.no_plain:
-        pvc = plain_vs_chosen(p, args, stream)
+        pvc = plain_vs_chosen(p, args, stream, rules)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -296,6 +322,11 @@ def run_mine(args):
         "voids_after_timed_steps": voids, "max_drop_after_timed_steps": float(np.max(res["final_drop"])),
         "plain_vs_chosen": pvc, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "surrogate": surrogate, "monte_carlo": mc,
+        "autotune": None if args.no_tune else {
+            "table": rules, "tune_s": round(tune_s, 2),
+            "how": "ems_autotune on a 2-sample copy of the full chip (after one IR solve): every valid shape of "
+                   "each launch group timed over 32 BE steps after a factorising launch, on scratch copies; the "
+                   "fastest applied by loading with ems_set_chain_rules (the load and tuning are not timed)"},
     }
     if rank == 0:
         print(json.dumps(_finite(line)))
@@ -303,9 +334,10 @@ def run_mine(args):
         dist.destroy_process_group()
 
 
-def plain_vs_chosen(p, args, stream, n_samples=1):
-    """Full-chip TTF of the same sample(s), plain FP64 method against the
-    chosen FP32 path: wall time (CUDA events), TTF, final IR drop, errors."""
+def plain_vs_chosen(p, args, stream, rules, n_samples=1):
+    """Full-chip TTF of the same sample(s), plain FP64 method (built-in
+    shapes) against the chosen FP32 path (the autotuner's shapes): wall time
+    (CUDA events), TTF, final IR drop, errors."""
     import numpy as np
     import torch
     from paper_2604_10743_gb300 import EMS_F32, EMS_F64
@@ -313,7 +345,7 @@ def plain_vs_chosen(p, args, stream, n_samples=1):
     g = full_chip(n_samples)
     out = {}
     for name, prec in (("chosen", EMS_F32), ("plain", EMS_F64)):
-        eng = Engine(p, g, precision=prec, max_voids=args.max_voids)
+        eng = Engine(p, g, precision=prec, max_voids=args.max_voids, chain_rules=rules if prec == EMS_F32 else None)
         a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a0.record(stream)
@@ -652,6 +684,7 @@ def main():
     ap.add_argument("--samples", type=int, default=32, help="Monte Carlo samples of the full chip held at once")
     ap.add_argument("--window", type=int, default=8, help="samples whose coefficients are held at once")
     ap.add_argument("--max-voids", type=int, default=128)
+    ap.add_argument("--no-tune", action="store_true", help="built-in chain shapes instead of the autotuner's")
     ap.add_argument("--mid-only", action="store_true",
                     help="time only full TTF runs of the 256 x 256 mesh; prints its own JSON line")
     args = ap.parse_args()

@@ -91,6 +91,10 @@ typedef struct {
                               rebuilds the window's coefficients from the per-segment factors
                               first.  Results are the same as with the full layout; the
                               reduced models (EMS_KRYLOV / EMS_AUTO) need the full layout. */
+    double krylov_eps;     /* deflation threshold of the block Arnoldi (Alg. 1): a new column
+                              whose norm after orthogonalisation falls below krylov_eps times
+                              its block's norm makes the block rank deficient and the tree is
+                              sent to backward Euler (Sec. IV-E.5).  0: 1e-10.  Range [0, 1). */
 } ems_params;
 
 enum { EMS_PC_AUTO = 0, EMS_PC_JACOBI = 1 };       /* IR preconditioner */
@@ -187,6 +191,64 @@ const char *ems_last_error(const ems_ctx *ctx);
  * same-layer cycle, or a node not connected to any pad; EMS_E_NOMEM.
  */
 ems_status ems_load_grid(ems_ctx *ctx, const ems_grid_desc *grid);
+
+/*
+ * Chain solver shapes and the autotuner (batching of Sec. IV-B's per-tree
+ * eliminations over every tree and Monte Carlo sample).  A chain of n stress
+ * nodes is cut into T team threads of M consecutive nodes (packed node i at
+ * (i mod M) T + i / M of its tree's packed block) and advanced by one of:
+ *   EMS_CHAIN_GLOBAL    one CTA per (chain, sample), chunks streamed from HBM
+ *   EMS_CHAIN_SHARED    (FP32) one CTA, the chunk coefficients staged in shared memory
+ *   EMS_CHAIN_REGISTER  (FP32, M <= 16) one CTA, coefficients and state in registers
+ *   EMS_CHAIN_CLUSTER   a cluster of CL CTAs (2, 4 or 8) per (chain, sample), registers,
+ *                       M = 16 (FP32) or 8 (FP64); CTAs trade their carries through
+ *                       distributed shared memory
+ * Every shape solves the same system; results differ by rounding only.
+ */
+enum { EMS_CHAIN_DEFAULT = 0, EMS_CHAIN_GLOBAL = 1, EMS_CHAIN_SHARED = 2, EMS_CHAIN_REGISTER = 3,
+       EMS_CHAIN_CLUSTER = 4 };
+typedef struct {
+    int64_t n_lo, n_hi;    /* chains of n_lo..n_hi stress nodes (inclusive) */
+    int kind;              /* EMS_CHAIN_*; EMS_CHAIN_DEFAULT leaves the built-in choice */
+    int M;                 /* nodes per thread: 4, 8, 16, 32 or 64 */
+    int CL;                /* CTAs per chain: 1, or 2 / 4 / 8 with EMS_CHAIN_CLUSTER */
+    int T;                 /* out (ems_autotune, ems_chain_candidates): team threads for n_hi */
+} ems_chain_rule;
+
+/*
+ * Shapes valid for a chain of n nodes at a precision (backward Euler),
+ * the built-in choice first.  count: out, number written (at most cap).
+ */
+ems_status ems_chain_candidates(int64_t n, int precision, ems_chain_rule *out, int cap, int *count);
+
+/*
+ * Shape rules for the next ems_load_grid of this context (backward Euler;
+ * the reduced models keep the built-in shapes).  The first rule whose range
+ * holds a chain's length and whose shape is valid for it applies; chains no
+ * rule covers take the built-in choice.  The rules are copied; n_rules = 0
+ * clears them.  A caller-provided workspace must be sized for the shapes the
+ * rules pick.  Errors: EMS_E_INVAL for an unknown kind, M or CL.
+ */
+ems_status ems_set_chain_rules(ems_ctx *ctx, const ems_chain_rule *rules, int n_rules);
+
+/* ems_workspace_bytes for a context whose chain shapes follow these rules. */
+size_t ems_workspace_bytes_rules(const ems_params *params, const ems_grid_desc *grid,
+                                 const ems_chain_rule *rules, int n_rules);
+
+/*
+ * Autotuner: for every group of chains the loaded context advances with one
+ * launch (one shape), time each valid shape on scratch copies of those
+ * chains (their current stress and voids, the first min(max_samples, W)
+ * samples): one launch that factorises and runs n_steps backward-Euler steps,
+ * then n_steps more timed with CUDA events.  The context's state is left as
+ * it was.  rules[k] gets the fastest shape of group k (n_lo / n_hi: the
+ * group's chain lengths), ms[k] its time per launch and ms_default[k] the
+ * current shape's (optional, may be NULL); n_rules: out, number of groups
+ * (at most cap).  Loading the grid again after ems_set_chain_rules(rules)
+ * applies the choice.  Needs backward Euler and a solved IR state.
+ */
+ems_status ems_autotune(ems_ctx *ctx, int n_steps, int max_samples, ems_chain_rule *rules, double *ms,
+                        double *ms_default, int cap, int *n_rules);
 
 /* Number of trees / stress nodes / samples of the loaded grid. */
 ems_status ems_dims(const ems_ctx *ctx, int *n_trees, int64_t *n_stress_nodes,

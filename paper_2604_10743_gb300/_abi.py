@@ -34,7 +34,7 @@ class EmsParams(ctypes.Structure):
         ("precision", ctypes.c_int), ("method", ctypes.c_int), ("krylov_q", ctypes.c_int),
         ("krylov_eta", ctypes.c_double), ("ir_rtol", ctypes.c_double), ("ir_max_iter", ctypes.c_int),
         ("max_voids_per_tree", ctypes.c_int), ("ir_precond", ctypes.c_int),
-        ("window_samples", ctypes.c_int)]
+        ("window_samples", ctypes.c_int), ("krylov_eps", ctypes.c_double)]
 
 
 class EmsGridDesc(ctypes.Structure):
@@ -46,6 +46,14 @@ class EmsGridDesc(ctypes.Structure):
                 ("n_sinks", ctypes.c_int), ("sink_node", c_int32_p), ("sink_I", c_double_p),
                 ("n_samples", ctypes.c_int), ("kappa_factor", c_double_p), ("sigc_factor", c_double_p),
                 ("seg_via", ctypes.POINTER(ctypes.c_int8))]
+
+
+class EmsChainRule(ctypes.Structure):
+    _fields_ = [("n_lo", ctypes.c_int64), ("n_hi", ctypes.c_int64), ("kind", ctypes.c_int), ("M", ctypes.c_int),
+                ("CL", ctypes.c_int), ("T", ctypes.c_int)]
+
+
+CHAIN_KINDS = {0: "default", 1: "global", 2: "shared", 3: "register", 4: "cluster"}
 
 
 class EmsSpiceOpts(ctypes.Structure):
@@ -74,7 +82,8 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_get_resistance", "ems_get_voids", "ems_state_export", "ems_state_import",
            "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc", "ems_joule_profile", "ems_set_wait_limit",
            "ems_get_node_temperature", "ems_set_thermal_perturbation", "ems_spice_parse", "ems_netlist_desc",
-           "ems_netlist_error", "ems_netlist_free",
+           "ems_netlist_error", "ems_netlist_free", "ems_chain_candidates", "ems_set_chain_rules",
+           "ems_workspace_bytes_rules", "ems_autotune",
            # include/ems_surrogate.h
            "ems_mlp_create", "ems_mlp_destroy", "ems_mlp_last_error", "ems_mlp_param_count",
            "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_fit_norm", "ems_mlp_gradients",
@@ -143,6 +152,15 @@ def lib(path=None):
     L.ems_set_thermal_perturbation.argtypes = [vp, c_double_p, S, S]
     L.ems_set_wait_limit.restype = S
     L.ems_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    rp = ctypes.POINTER(EmsChainRule)
+    L.ems_chain_candidates.restype = S
+    L.ems_chain_candidates.argtypes = [ctypes.c_int64, S, rp, S, ctypes.POINTER(ctypes.c_int)]
+    L.ems_set_chain_rules.restype = S
+    L.ems_set_chain_rules.argtypes = [vp, rp, S]
+    L.ems_workspace_bytes_rules.restype = ctypes.c_size_t
+    L.ems_workspace_bytes_rules.argtypes = [ctypes.POINTER(EmsParams), ctypes.POINTER(EmsGridDesc), rp, S]
+    L.ems_autotune.restype = S
+    L.ems_autotune.argtypes = [vp, S, S, rp, c_double_p, c_double_p, S, ctypes.POINTER(ctypes.c_int)]
     L.ems_joule_profile.restype = S
     L.ems_joule_profile.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.ems_get_node_temperature.restype = S
@@ -202,6 +220,7 @@ def make_params(p, precision=EMS_F64, method=EMS_BE, ir_rtol=1e-13, ir_max_iter=
     e.max_voids_per_tree = max_voids
     e.ir_precond = ir_precond
     e.window_samples = int(window)
+    e.krylov_eps = float(p.get("krylov_eps", 0.0))
     return e
 
 
@@ -243,3 +262,29 @@ class GridDesc:
         d.seg_via = _ptr(self.keep["via"], ctypes.c_int8)
         self.desc = d
         self.n_samples = max(S, 1)
+
+
+def rules_array(rules):
+    """ems_chain_rule[] from a list of dicts (n_lo, n_hi, kind, M, CL)."""
+    arr = (EmsChainRule * max(1, len(rules)))()
+    for k, r in enumerate(rules):
+        arr[k].n_lo, arr[k].n_hi = int(r["n_lo"]), int(r["n_hi"])
+        arr[k].kind, arr[k].M, arr[k].CL = int(r["kind"]), int(r["M"]), int(r.get("CL", 1))
+        arr[k].T = int(r.get("T", 0))
+    return arr
+
+
+def rule_dict(r):
+    return {"n_lo": int(r.n_lo), "n_hi": int(r.n_hi), "kind": int(r.kind), "kernel": CHAIN_KINDS.get(r.kind, "?"),
+            "M": int(r.M), "CL": int(r.CL), "T": int(r.T)}
+
+
+def chain_candidates(n, precision):
+    """Valid chain shapes for n nodes (ems_chain_candidates), built-in first."""
+    L = lib()
+    arr = (EmsChainRule * 32)()
+    cnt = ctypes.c_int()
+    st = L.ems_chain_candidates(int(n), int(precision), arr, 32, ctypes.byref(cnt))
+    if st != 0:
+        raise EmsError(st, "ems_chain_candidates")
+    return [rule_dict(arr[k]) for k in range(cnt.value)]

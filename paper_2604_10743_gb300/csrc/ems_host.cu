@@ -113,6 +113,7 @@ ems_status validate(ems_ctx *c, const ems_params *p, const ems_grid_desc *g) {
     if (p->method != EMS_BE && (p->krylov_q < 1 || p->krylov_q > 40 || !(p->krylov_eta > 0.0)))
         return fail(c, EMS_E_INVAL, "krylov_q must be 1..40 and krylov_eta > 0");
     if (p->window_samples < 0) return fail(c, EMS_E_INVAL, "window_samples must be >= 0");
+    if (!(p->krylov_eps >= 0.0 && p->krylov_eps < 1.0)) return fail(c, EMS_E_INVAL, "krylov_eps must be in [0, 1)");
     if (p->window_samples > 0 && p->window_samples < S && p->method != EMS_BE)
         return fail(c, EMS_E_INVAL, "the reduced models need every sample's coefficients: window_samples 0");
     return EMS_OK;
@@ -302,53 +303,6 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
     return EMS_OK;
 }
 
-// Chunk length for a chain of n nodes: the smallest power of two in [4, 64]
-// that keeps the team at or below a target size (FP32: 448 threads, the
-// state chunk is the only per-node register array; FP64: 192, the state form
-// keeps more per thread), then T = ceil(n / M) rounded up to whole warps.  A
-// team larger than the chunk length allows moves to a longer chunk; chains
-// too long for any chunk fall back to the single-thread tree path.
-// EMS_CHAIN_M (environment) pins M for tuning.
-void chain_shape(int64_t n, int prec, int method, int *T, int *M, int *CL) {
-    const int64_t target = prec == EMS_F32 ? 448 : 192;
-    *CL = 1;
-    // backward-Euler chains longer than one register-resident CTA holds
-    // (FP32: 5,120 nodes; FP64: past the streaming kernel's 16,384): a
-    // cluster of 2, 4 or 8 CTAs of <= 320 threads, 16 (FP32) or 8 (FP64)
-    // nodes per thread
-    const int64_t one_cta = prec == EMS_F32 ? 320 * 16 : 256 * 64;
-    if (method == EMS_BE && n > one_cta && !getenv("EMS_NO_CLUSTER")) {
-        const int mc = prec == EMS_F32 ? 16 : 8;
-        const int64_t th = (n + mc - 1) / mc;
-        for (int cl : {2, 4, 8}) {
-            const int64_t t = ((th + cl - 1) / cl + 31) / 32 * 32;
-            if (t <= 320) { *T = (int)(t * cl); *M = mc; *CL = cl; return; }
-        }
-    }
-    // FP32 chains the register-resident kernel holds: 16 nodes per thread
-    // (<= 320 threads) for long chains, 8 (<= 576 threads) for short ones
-    if (prec == EMS_F32) {
-        int want = n > 2048 ? 16 : 8;
-        if (const char *e = getenv("EMS_CHAIN_M")) want = atoi(e);
-        for (int m : {want, 16, 8}) {
-            const int64_t lim = m == 16 ? 320 : m == 8 ? 576 : m == 4 ? 896 : 0;
-            const int64_t t = ((n + m - 1) / m + 31) / 32 * 32;
-            if (t <= lim) { *T = (int)t; *M = m; return; }
-        }
-    }
-    int m = 4;
-    while (m < 64 && (n + m - 1) / m > target) m *= 2;
-    if (const char *e = getenv("EMS_CHAIN_M")) {
-        int v = atoi(e);
-        if (v == 4 || v == 8 || v == 16 || v == 32 || v == 64) m = v;
-    }
-    for (; m <= 64; m *= 2) {
-        int64_t t = ((n + m - 1) / m + 31) / 32 * 32;
-        if (t <= chain_max_threads(prec, m)) { *T = (int)t; *M = m; return; }
-    }
-    *T = 0; *M = 0;
-}
-
 // IR structure on the free (non-pad) nodes
 struct HostIR {
     std::vector<int32_t> free_of_node, node_of_free, ptr, col, ent_ptr, ent_seg, rhs_ptr, rhs_seg;
@@ -452,9 +406,10 @@ ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Pl
     for (int t = 0; t < pl.tr.n_trees; ++t) {
         int64_t n = pl.tr.off[t + 1] - pl.tr.off[t];
         int T = 0, M = 0, CL = 1;
-        if (pl.tr.is_chain[t]) chain_shape(n, p->precision, p->method, &T, &M, &CL);
+        int kind = 0;
+        if (pl.tr.is_chain[t]) chain_shape(n, p->precision, p->method, c ? &c->rules : nullptr, &T, &M, &CL, &kind);
         TreePack tp;
-        if (T > 0) { tp.T = T; tp.M = M; tp.CL = CL; tp.pbase = P; P += (int64_t)T * M; }
+        if (T > 0) { tp.T = T; tp.M = M; tp.CL = CL; tp.kind = kind; tp.pbase = P; P += (int64_t)T * M; }
         else { tp.T = 1; tp.M = (int)n; tp.pbase = P; P += (n + 31) / 32 * 32; }
         pl.pack[t] = tp;
     }
@@ -572,18 +527,152 @@ cudaError_t up(T *dst, const T *src, size_t n, cudaStream_t s) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Chain shapes
+// ---------------------------------------------------------------------------
+namespace {
+int64_t round_warp(int64_t t) { return (t + 31) / 32 * 32; }
+bool pow2_chunk(int M) { return M == 4 || M == 8 || M == 16 || M == 32 || M == 64; }
+}  // namespace
+
+bool shape_valid(int64_t n, int prec, int kind, int M, int CL, int *T) {
+    if (n < 1 || !pow2_chunk(M)) return false;
+    const int64_t th = (n + M - 1) / M;             // threads that hold nodes
+    int64_t t = round_warp(th);
+    switch (kind) {
+        case EMS_CHAIN_REGISTER:
+            if (prec != EMS_F32 || CL != 1 || t > reg_max_threads(M)) return false;
+            break;
+        case EMS_CHAIN_SHARED:
+            if (prec != EMS_F32 || CL != 1 || t > chain_max_threads(prec, M) ||
+                (size_t)5 * sizeof(float) * t * M > kSharedCoefBytes)
+                return false;
+            break;
+        case EMS_CHAIN_GLOBAL:
+            if (CL != 1 || t > chain_max_threads(prec, M)) return false;
+            break;
+        case EMS_CHAIN_CLUSTER: {
+            if (M != cluster_chunk(prec) || (CL != 2 && CL != 4 && CL != 8)) return false;
+            const int64_t tc = round_warp((th + CL - 1) / CL);
+            // every CTA must hold nodes of the chain
+            if (tc > kClusterCtaThreads || th <= (int64_t)(CL - 1) * tc) return false;
+            t = tc * CL;
+            break;
+        }
+        default: return false;
+    }
+    if (T) *T = (int)t;
+    return true;
+}
+
+// Built-in choice.  Backward-Euler chains longer than one register-resident
+// CTA holds (FP32: 5,120 nodes; FP64: past the streaming kernel's 16,384):
+// the smallest cluster of 2, 4 or 8 CTAs of <= 320 threads.  FP32 chains the
+// register kernel holds: 16 nodes per thread (<= 320 threads) for chains of
+// more than 2,048 nodes, else 8 (<= 576 threads).  Otherwise the streaming
+// kernel with the smallest power-of-two chunk in [4, 64] that keeps the team
+// at or below a target (FP32: 448 threads; FP64: 192, the state form keeps
+// more per thread), coefficients in shared memory (FP32) while they fit.
+// Chains too long for any shape take the branched-tree path.
+static void builtin_shape(int64_t n, int prec, int method, int *T, int *M, int *CL, int *kind) {
+    *CL = 1;
+    const int64_t one_cta = prec == EMS_F32 ? 320 * 16 : 256 * 64;
+    if (method == EMS_BE && n > one_cta)
+        for (int cl : {2, 4, 8})
+            if (shape_valid(n, prec, EMS_CHAIN_CLUSTER, cluster_chunk(prec), cl, T)) {
+                *M = cluster_chunk(prec); *CL = cl; *kind = EMS_CHAIN_CLUSTER;
+                return;
+            }
+    if (prec == EMS_F32) {
+        const int want = n > 2048 ? 16 : 8;
+        for (int m : {want, 16, 8})
+            if (shape_valid(n, prec, EMS_CHAIN_REGISTER, m, 1, T)) { *M = m; *kind = EMS_CHAIN_REGISTER; return; }
+    }
+    const int64_t target = prec == EMS_F32 ? 448 : 192;
+    int m = 4;
+    while (m < 64 && (n + m - 1) / m > target) m *= 2;
+    for (; m <= 64; m *= 2) {
+        if (prec == EMS_F32 && shape_valid(n, prec, EMS_CHAIN_SHARED, m, 1, T)) {
+            *M = m; *kind = EMS_CHAIN_SHARED;
+            return;
+        }
+        if (shape_valid(n, prec, EMS_CHAIN_GLOBAL, m, 1, T)) { *M = m; *kind = EMS_CHAIN_GLOBAL; return; }
+    }
+    *T = 0; *M = 0; *kind = 0;
+}
+
+void chain_shape(int64_t n, int prec, int method, const std::vector<ems_chain_rule> *rules, int *T, int *M, int *CL,
+                 int *kind) {
+    if (rules && method == EMS_BE)
+        for (const ems_chain_rule &r : *rules)
+            if (n >= r.n_lo && n <= r.n_hi && r.kind != EMS_CHAIN_DEFAULT &&
+                shape_valid(n, prec, r.kind, r.M, r.CL, T)) {
+                *M = r.M; *CL = r.CL; *kind = r.kind;
+                return;
+            }
+    builtin_shape(n, prec, method, T, M, CL, kind);
+}
+
+std::vector<ems_chain_rule> shape_candidates(int64_t n, int prec) {
+    std::vector<ems_chain_rule> out;
+    ems_chain_rule d{n, n, 0, 0, 1, 0};
+    builtin_shape(n, prec, EMS_BE, &d.T, &d.M, &d.CL, &d.kind);
+    if (d.kind) out.push_back(d);
+    auto add = [&](int kind, int M, int CL) {
+        ems_chain_rule r{n, n, kind, M, CL, 0};
+        if (!shape_valid(n, prec, kind, M, CL, &r.T)) return;
+        if (d.kind == kind && d.M == M && d.CL == CL) return;
+        out.push_back(r);
+    };
+    for (int kind : {EMS_CHAIN_REGISTER, EMS_CHAIN_SHARED, EMS_CHAIN_GLOBAL})
+        for (int M : {4, 8, 16, 32, 64}) add(kind, M, 1);
+    for (int CL : {2, 4, 8}) add(EMS_CHAIN_CLUSTER, cluster_chunk(prec), CL);
+    return out;
+}
+
 }  // namespace ems
 
 using namespace ems;
 
-extern "C" size_t ems_workspace_bytes(const ems_params *params, const ems_grid_desc *grid) {
+extern "C" ems_status ems_chain_candidates(int64_t n, int precision, ems_chain_rule *out, int cap, int *count) {
+    if (n < 1 || (precision != EMS_F32 && precision != EMS_F64) || cap < 0 || (cap > 0 && !out) || !count)
+        return EMS_E_INVAL;
+    const std::vector<ems_chain_rule> v = shape_candidates(n, precision);
+    const int k = (int)std::min<size_t>(v.size(), (size_t)cap);
+    for (int i = 0; i < k; ++i) out[i] = v[i];
+    *count = k;
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_set_chain_rules(ems_ctx *c, const ems_chain_rule *rules, int n_rules) {
+    if (!c || n_rules < 0 || (n_rules > 0 && !rules)) return EMS_E_INVAL;
+    for (int i = 0; i < n_rules; ++i) {
+        const ems_chain_rule &r = rules[i];
+        if (r.n_lo < 1 || r.n_hi < r.n_lo) return fail(c, EMS_E_INVAL, "rule range must have 1 <= n_lo <= n_hi");
+        if (r.kind < EMS_CHAIN_DEFAULT || r.kind > EMS_CHAIN_CLUSTER) return fail(c, EMS_E_INVAL, "unknown chain kernel");
+        if (r.kind != EMS_CHAIN_DEFAULT &&
+            (!pow2_chunk(r.M) || (r.kind == EMS_CHAIN_CLUSTER ? (r.CL != 2 && r.CL != 4 && r.CL != 8) : r.CL != 1)))
+            return fail(c, EMS_E_INVAL, "M must be 4, 8, 16, 32 or 64; CL 2, 4 or 8 for a cluster, else 1");
+    }
+    c->rules.assign(rules, rules + n_rules);
+    return EMS_OK;
+}
+
+extern "C" size_t ems_workspace_bytes_rules(const ems_params *params, const ems_grid_desc *grid,
+                                            const ems_chain_rule *rules, int n_rules) {
     ems_ctx tmp;
-    if (!params) return 0;
+    if (!params || n_rules < 0 || (n_rules > 0 && !rules)) return 0;
     tmp.prm = *params;
+    if (n_rules > 0 && ems_set_chain_rules(&tmp, rules, n_rules) != EMS_OK) return 0;
     Plan pl;
     if (make_plan(&tmp, params, grid, pl) != EMS_OK) return 0;
     Dev d{};
     return carve(&tmp, pl, grid, nullptr, d);
+}
+
+extern "C" size_t ems_workspace_bytes(const ems_params *params, const ems_grid_desc *grid) {
+    return ems_workspace_bytes_rules(params, grid, nullptr, 0);
 }
 
 extern "C" ems_status ems_create(ems_ctx **out, const ems_params *params, void *stream,
@@ -790,13 +879,15 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
         bool ch = pl.pack[t].T > 1;
         Bucket *bk = nullptr;
         for (auto &b : c->buckets)
-            if (b.chain == ch && (!ch || (b.T == pl.pack[t].T && b.M == pl.pack[t].M && b.CL == pl.pack[t].CL)))
+            if (b.chain == ch && (!ch || (b.T == pl.pack[t].T && b.M == pl.pack[t].M && b.CL == pl.pack[t].CL &&
+                                          b.kind == pl.pack[t].kind)))
                 bk = &b;
         if (!bk) {
             c->buckets.push_back(Bucket{});
             bk = &c->buckets.back();
             bk->chain = ch; bk->T = ch ? pl.pack[t].T : 1; bk->M = ch ? pl.pack[t].M : 0;
             bk->CL = ch ? pl.pack[t].CL : 1;
+            bk->kind = ch ? pl.pack[t].kind : 0;
         }
         bk->trees.push_back(t);
     }

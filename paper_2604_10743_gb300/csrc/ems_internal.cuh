@@ -77,6 +77,12 @@ inline int chain_max_threads(int prec, int M) {
     if (prec == EMS_F32) return M <= 8 ? 1024 : M == 16 ? 640 : M == 32 ? 640 : 320;
     return M <= 4 ? 1024 : M == 8 ? 896 : M == 16 ? 640 : M == 32 ? 384 : 256;
 }
+// FP32 register-resident kernel: threads a CTA may have per chunk length
+// (its state, coefficients and compensation stay in registers)
+inline int reg_max_threads(int M) { return M == 4 ? 896 : M == 8 ? 576 : M == 16 ? 320 : 0; }
+constexpr int kClusterCtaThreads = 320;        // threads per CTA of the cluster kernel
+constexpr size_t kSharedCoefBytes = 200 * 1024; // FP32 streaming kernel: coefficients staged while they fit
+inline int cluster_chunk(int prec) { return prec == EMS_F32 ? 16 : 8; }
 
 // ---------------------------------------------------------------------------
 // Host-side tree extraction result (canonical order)
@@ -103,11 +109,13 @@ struct TreePack {
     int T, M;          // threads per tree and chunk length (T = 1 for branched)
     int64_t pbase;     // packed base (within one sample)
     int CL = 1;        // CTAs per tree (a thread-block cluster when > 1; T counts all of them)
+    int kind = 0;      // EMS_CHAIN_* kernel of a chain
 };
 
-struct Bucket {        // trees launched together: same precision kernel, T and M
+struct Bucket {        // trees launched together: same kernel, T, M and CL
     int T, M;
     int CL = 1;        // CTAs per tree: T / CL threads each
+    int kind = 0;      // EMS_CHAIN_* (chains)
     bool chain;
     std::vector<int32_t> trees;
     int32_t *d_trees = nullptr;
@@ -232,6 +240,7 @@ struct ems_ctx {
     ems::HostTrees trees;
     std::vector<ems::TreePack> pack;
     std::vector<ems::Bucket> buckets;
+    std::vector<ems_chain_rule> rules;   // chain shapes for the next load (autotuner's table)
     ems::Dev d{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int coop_blocks = 0;       // resident CTAs for the cooperative PCG
@@ -295,6 +304,12 @@ void map_window(ems_ctx *c, int s0, int ns);   // map samples [s0, s0 + ns) (ns 
 void map_all(ems_ctx *c);                      // every sample; per-node arrays are window-sized
 ems_status gather_x(ems_ctx *c);               // IR initial guess of the mapped samples from u
 ems_status window_derive(ems_ctx *c);          // per-node coefficients of the mapped window
+// chain shapes: validity of (kind, M, CL) for n nodes (team size in *T), the
+// built-in choice, and the rules' choice (backward Euler) over it
+bool shape_valid(int64_t n, int prec, int kind, int M, int CL, int *T);
+void chain_shape(int64_t n, int prec, int method, const std::vector<ems_chain_rule> *rules, int *T, int *M,
+                 int *CL, int *kind);
+std::vector<ems_chain_rule> shape_candidates(int64_t n, int prec);
 
 // Krylov (ems_krylov.cu)
 ems_status krylov_advance(ems_ctx *c, double dt, int n_steps, int method, int *n_new);

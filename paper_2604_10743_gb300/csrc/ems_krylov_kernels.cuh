@@ -782,7 +782,7 @@ KrArgs<R> kr_args(ems_ctx *c, double dt, int n_steps, int build_only) {
     KrArgs<R> a;
     a.toff = d.toff; a.pbase = d.pbase; a.N = c->N; a.P = c->P;
     a.n_trees = c->n_trees; a.rmax = c->rmax; a.q = c->kr_q; a.kc = c->kr_kc;
-    a.eta = c->kr_eta; a.eps_rel = 1e-10;
+    a.eta = c->kr_eta; a.eps_rel = c->prm.krylov_eps > 0.0 ? c->prm.krylov_eps : 1e-10;
     a.Vn = d.V; a.g = d.g; a.leak = d.leak; a.f = d.f; a.kap_a = d.kap_a; a.dx = d.face_dx; a.area = d.face_area;
     a.thr = d.thr; a.sig = (R *)d.sig;
     a.sp = d.kr_sp; a.sg = d.kr_sg; a.su = d.kr_su; a.sPf = d.kr_sPf; a.sPb = d.kr_sPb;

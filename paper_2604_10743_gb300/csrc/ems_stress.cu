@@ -21,8 +21,12 @@
 // team (warp shuffles + one shared-memory level), and a correction with the
 // precomputed carry products Pf / Pb.  Trees with branches run one thread
 // per (tree, sample) with leaf-to-root elimination.
+#include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cmath>
+#include <cstdio>
+#include <map>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -985,33 +989,21 @@ namespace cg = cooperative_groups;
 
 template <typename R>
 struct ClSlots {                      // written by the other CTAs of the cluster (push), read locally
-    R fA[8], fB[8], bA[8], bB[8];     // each rank's forward / backward aggregate of its chunks
-    R last_left, first_right;         // stress at the left neighbour CTA's last / right one's first node
-    int flags[8];                     // each rank: bit 0 a node reached its threshold, bit 1 near the guard
+    // every step, two buffers by step parity
+    R fA[2][8];                       // each rank's forward aggregate (no carry into it)
+    R bA[2][8];                       // each rank's first-node increment (no carries into it)
+    R first[2][8], last[2][8];        // each rank's stress at its first / last node (halos)
+    int flags[2][8];                  // each rank: bit 0 a node reached its threshold, bit 1 near the guard
+    // every factorisation
+    R fB[8];                          // forward aggregate: response to the carry into the rank
+    R bB[8];                          // first-node increment: response to the carry from the right
+    R bAz[8];                         // first-node increment: response to the forward carry into the rank
+    R hh[8];                          // p dt g across the boundary to the next rank
     double best[8];                   // each rank's argmax of sigma - sigma_crit (nucleation)
     int arg[8];
     double tmin[8];                   // each rank's lowest threshold
     double fm[8][4];                  // each rank's product of 2 x 2 chunk matrices (factorisation)
 };
-
-// composition of the ranks' affine maps x -> A + B x applied to 0, from the
-// local copies: forward over ranks < r left to right, backward over ranks > r
-template <typename R, int CL>
-__device__ __forceinline__ R cl_carry_fwd(const ClSlots<R> &sl, int rank) {
-    R z = R(0);
-#pragma unroll
-    for (int q = 0; q < CL; ++q)
-        if (q < rank) z = fmx(sl.fB[q], z, sl.fA[q]);
-    return z;
-}
-template <typename R, int CL>
-__device__ __forceinline__ R cl_carry_bwd(const ClSlots<R> &sl, int rank) {
-    R x = R(0);
-#pragma unroll
-    for (int q = CL - 1; q >= 0; --q)
-        if (q > rank) x = fmx(sl.bB[q], x, sl.bA[q]);
-    return x;
-}
 
 // exclusive scan of the chunk maps within the CTA (one barrier), with the
 // CTA's carry-in composed in: returns the carry entering this thread's chunk
@@ -1158,7 +1150,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
     const int rank = (int)cl.block_rank();
     const int t = a.trees[blockIdx.x / CL], s = blockIdx.y;
     const int T = blockDim.x, c = threadIdx.x, TT = T * CL, g = rank * T + c;
-    const int lane = c & 31, w = c >> 5, nw = T >> 5;
+    const int lane = c & 31, w_ = c >> 5, nw = T >> 5;
     const int64_t cb = a.toff[t];
     const int n = (int)(a.toff[t + 1] - cb);
     const int64_t cs = (int64_t)s * a.N + cb, ps = (int64_t)s * a.P + a.pbase[t];
@@ -1188,10 +1180,10 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
     if ((a.n_steps - kd) % rs) rs = 1;
     if (rs > 1) {
         const int nr = __syncthreads_or(near_guard<R, M>(sg, a.guard * thrmin));
-        if (c < CL) cl.map_shared_rank(&sl, c)->flags[rank] = nr ? 2 : 0;
+        if (c < CL) cl.map_shared_rank(&sl, c)->flags[0][rank] = nr ? 2 : 0;
         cl.sync();
         int any = 0;
-        for (int q = 0; q < CL; ++q) any |= sl.flags[q];
+        for (int q = 0; q < CL; ++q) any |= sl.flags[0][q];
         cl.sync();
         if (any & 2) {
             rs = 1;
@@ -1229,8 +1221,27 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
         }
     }
 
-    R cp[M], cg_[M], cbt[M], cpf[M], cpb[M], cth[M], g_next;
+    // One cluster barrier per step.  Each CTA solves its part with no carry
+    // from the other CTAs: forward values z, backward increments xr.  The
+    // true increment is linear in the two carries that cross its ends,
+    //   x_k = xr_k + w_k cf + cpb_k cr,
+    // cf the forward carry into the thread's chunk, cr the backward one, and
+    // cf, cr are affine in the CTA's forward carry-in zin and its right
+    // carry-in; the responses (w, exB, bxB, bxAz and each rank's fB, bB, bAz)
+    // are constants of the factorisation.  So one exchange per step of each
+    // rank's forward aggregate and first-node increment (both without
+    // carries) gives every CTA all carries.  The CTA-boundary halos ride
+    // along: each CTA sweeps with the halos of the previous step's exchange
+    // and corrects with their change d, an increment (exact as the difference
+    // of two nearby values): the left neighbour's d adds to zin, the right
+    // neighbour's adds to the right carry-in (p dt g d at the last node).
+    // Flags raised by step k reach the other CTAs with step k + 1's exchange:
+    // that step's work is dropped, the event handled, the step redone.
+    R cp[M], cg_[M], cbt[M], w[M], cpb[M], cth[M], g_next;
+    R exB = R(1), bxB = R(1), bxAz = R(0);
     unsigned vmask = 0u;
+    __shared__ R s_last, s_hh;
+    const unsigned full = 0xffffffffu;
     auto load = [&]() {
         cl.sync();                               // coefficients of every CTA written
         vmask = 0u;
@@ -1243,7 +1254,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
             cp[k] = a.alpha[pk];
             cg_[k] = a.dtg[pk];
             cbt[k] = a.beta[pk];
-            cpf[k] = a.Pf[pk];
+            w[k] = a.Pf[pk];
             cpb[k] = a.Pb[pk];
             cth[k] = ((vmask >> k) & 1u) ? a.dtl[pk]
                                           : (i < n ? (sizeof(R) == 4 ? (R)__double2float_rd(a.thr[cs + i])
@@ -1251,98 +1262,30 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
                                                    : (R)INFINITY);
         }
         g_next = g + 1 < TT ? a.dtg[ps + g + 1] : R(0);
+        // response of the chunk's backward sweep to a unit forward carry
+#pragma unroll
+        for (int k = M - 2; k >= 0; --k) w[k] = fmx(cp[k] * cg_[k + 1], w[k + 1], w[k]);
+        if (c == T - 1) s_hh = cp[M - 1] * g_next;
+        R u0, u1, fB, v0, bAz, bB;
+        cta_scan<0, R>(R(0), w[M - 1], sA, sB, u0, exB, u1, fB);
+        cta_scan<1, R>(exB * w[0], cpb[0], sA, sB, bxAz, bxB, bAz, bB);
+        fB = __shfl_sync(full, fB, 0);
+        bAz = __shfl_sync(full, bAz, 0);
+        bB = __shfl_sync(full, bB, 0);
+        (void)u0; (void)u1; (void)v0;
+        if (c < CL) {
+            ClSlots<R> *o = cl.map_shared_rank(&sl, c);
+            o->fB[rank] = fB; o->bB[rank] = bB; o->bAz[rank] = bAz; o->hh[rank] = s_hh;
+        }
+        cl.sync();
     };
     load();
 
-    const unsigned full = 0xffffffffu;
-    // boundary stresses: warps in shared memory, the CTA's ends in its slots
-    auto publish = [&]() {
-        if (lane == 31) sL[w] = sg[M - 1];
-        if (lane == 0) sR[w] = sg[0];
-        if (c == 0 && rank > 0) cl.map_shared_rank(&sl, rank - 1)->first_right = sg[0];
-        if (c == T - 1 && rank + 1 < CL) cl.map_shared_rank(&sl, rank + 1)->last_left = sg[M - 1];
-    };
-    publish();
-    cl.sync();
-    for (int step = 0; step < n_steps; ++step) {
-        R left = __shfl_up_sync(full, sg[M - 1], 1);
-        R right = __shfl_down_sync(full, sg[0], 1);
-        if (lane == 0 && w > 0) left = sL[w - 1];
-        if (lane == 31 && w + 1 < nw) right = sR[w + 1];
-        if (c == 0) left = rank > 0 ? sl.last_left : R(0);
-        if (c == T - 1) right = rank + 1 < CL ? sl.first_right : R(0);
-        R gk = cg_[0];
-        R qprev = gk * (left - sg[0]);
-        R z = R(0);
-        R zr[M];
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-            const R nxt = k + 1 < M ? sg[k + 1] : right;
-            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
-            const R qn = gk1 * (sg[k] - nxt);
-            R r = qprev - qn + cbt[k];
-            if ((vmask >> k) & 1u) r -= cth[k] * sg[k];
-            z = cp[k] * fmx(gk, z, r);
-            zr[k] = z;
-            qprev = qn;
-            gk = gk1;
-        }
-        // forward carries: within the CTA, then across the cluster
-        R exA, exB, agA, agB;
-        cta_scan<0, R>(z, cpf[M - 1], sA, sB, exA, exB, agA, agB);
-        agA = __shfl_sync(0xffffffffu, agA, 0);
-        agB = __shfl_sync(0xffffffffu, agB, 0);
-        if (c < CL) { ClSlots<R> *o = cl.map_shared_rank(&sl, c); o->fA[rank] = agA; o->fB[rank] = agB; }
-        cl.sync();
-        const R cf = fmx(exB, cl_carry_fwd<R, CL>(sl, rank), exA);
-        R x = R(0);
-#pragma unroll
-        for (int k = M - 1; k >= 0; --k) {
-            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
-            x = fmx(cp[k] * gk1, x, fmx(cpf[k], cf, zr[k]));
-            zr[k] = x;
-        }
-        R bxA, bxB, bgA, bgB;
-        cta_scan<1, R>(x, cpb[0], sA, sB, bxA, bxB, bgA, bgB);
-        bgA = __shfl_sync(0xffffffffu, bgA, 0);
-        bgB = __shfl_sync(0xffffffffu, bgB, 0);
-        if (c < CL) { ClSlots<R> *o = cl.map_shared_rank(&sl, c); o->bA[rank] = bgA; o->bB[rank] = bgB; }
-        cl.sync();
-        const R cr = fmx(bxB, cl_carry_bwd<R, CL>(sl, rank), bxA);
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-            if constexpr (sizeof(R) == 4) {               // compensated (Kahan) FP32 update
-                const R y = fmx(cpb[k], cr, zr[k]) - cc[k];
-                const R tt = sg[k] + y;
-                cc[k] = (tt - sg[k]) - y;
-                sg[k] = tt;
-            } else {
-                sg[k] += fmx(cpb[k], cr, zr[k]);
-            }
-        }
-        // void growth by the Robin leak (owner thread only)
-        if (vmask) {
-            for (int q = 0; q < s_nv; ++q) {
-                const int v = s_node[q];
-                if (v / M == g) {
-                    R val = R(0);
-#pragma unroll
-                    for (int k = 0; k < M; ++k)
-                        if (v % M == k) val = sg[k];
-                    s_vol[q] += s_coef[q] * (double)val;
-                }
-            }
-        }
-        bool hit = false;
-#pragma unroll
-        for (int k = 0; k < M; ++k) hit |= !((vmask >> k) & 1u) && sg[k] >= cth[k];
-        const bool nr = s_rs > 1 && near_guard<R, M>(sg, s_gthr);
-        publish();
-        const int f = __syncthreads_or(hit) | (__syncthreads_or(nr) << 1);
-        if (c < CL) cl.map_shared_rank(&sl, c)->flags[rank] = f;
-        cl.sync();
-        int any = 0;
-        for (int q = 0; q < CL; ++q) any |= sl.flags[q];
+    int pending = 0;                             // this CTA's flags from the previous step
+    // events of step `ev` (state = after step ev): nucleation, promotion to
+    // fine steps; with `refactor` the factors are rebuilt at once, else left
+    // to the next launch
+    auto handle = [&](int any, int ev, bool refactor) {
         int refac_from = -1;
         if (any & 1) {
             double best = -INFINITY;
@@ -1381,7 +1324,7 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
                             const int64_t e = st * a.maxv + nv;
                             a.v_node[e] = v;
                             a.v_seg[e] = void_segment<R>(a, s, cb + v);
-                            a.v_tnuc[e] = s_tbase + ((double)(step - s_sbase) + frac) * dt;
+                            a.v_tnuc[e] = s_tbase + ((double)(ev - s_sbase) + frac) * dt;
                             a.v_vol[e] = 0.0;
                             a.v_count[st] = nv + 1;
                             atomicAdd(&a.counters[0], 1);
@@ -1400,12 +1343,13 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
         }
         bool promoted = false;
         if (any & 2) {
-            n_steps = step + 1 + (n_steps - step - 1) * s_rs;
+            // coarse steps from ev + 1 on become fine ones
+            n_steps = ev + 1 + (n_steps - ev - 1) * s_rs;
             promoted = true;
             __syncthreads();
             if (c == 0) {
-                s_tbase += (double)(step + 1 - s_sbase) * s_dt;
-                s_sbase = step + 1;
+                s_tbase += (double)(ev + 1 - s_sbase) * s_dt;
+                s_sbase = ev + 1;
                 s_dt = a.dt;
                 s_rs = 1;
                 for (int q = 0; q < s_nv; ++q) s_coef[q] = a.dt * a.Binv * a.leak[cs + s_node[q]];
@@ -1413,15 +1357,155 @@ __global__ void __launch_bounds__(320, 1) k_chain_cl(ChainArgs<R> a) {
             }
             refac_from = 0;
         }
-        if (refac_from >= 0) {
-            cl.sync();                           // the new threshold is written; every CTA is here
-            const double dtf = promoted ? a.dt : s_dt;
-            chain_factor_cl<R, M>(a, dtf, n, TT, g, cb, cs, ps, &sl, rank);
-            thrmin = thr_min();
-            if (c == 0) s_gthr = a.guard * thrmin;
-            load();
+        if (refac_from < 0 || !refactor) return;
+        cl.sync();                               // the new threshold is written; every CTA is here
+        const double dtf = promoted ? a.dt : s_dt;
+        chain_factor_cl<R, M>(a, dtf, n, TT, g, cb, cs, ps, &sl, rank);
+        thrmin = thr_min();
+        if (c == 0) s_gthr = a.guard * thrmin;
+        load();
+    };
+
+    // halos: inside the CTA through shared memory, across CTAs through the
+    // slots (buffer 1 holds the exchange before step 0)
+    if (lane == 31) sL[w_] = sg[M - 1];
+    if (lane == 0) sR[w_] = sg[0];
+    if (c == T - 1) s_last = sg[M - 1];
+    __syncthreads();
+    {
+        const R fst = __shfl_sync(full, sg[0], 0);
+        if (c < CL) { ClSlots<R> *o = cl.map_shared_rank(&sl, c); o->first[1][rank] = fst; o->last[1][rank] = s_last; }
+        cl.sync();
+    }
+
+    for (int step = 0; step < n_steps;) {
+        const int b = step & 1, ob = b ^ 1;
+        R left = __shfl_up_sync(full, sg[M - 1], 1);
+        R right = __shfl_down_sync(full, sg[0], 1);
+        if (lane == 0 && w_ > 0) left = sL[w_ - 1];
+        if (lane == 31 && w_ + 1 < nw) right = sR[w_ + 1];
+        if (c == 0) left = rank > 0 ? sl.last[ob][rank - 1] : R(0);
+        if (c == T - 1) {
+            right = rank + 1 < CL ? sl.first[ob][rank + 1] : R(0);
+            s_last = sg[M - 1];
         }
-        cl.sync();                               // slots read by every CTA before they change
+        // forward sweep, then the carries within the CTA
+        R gk = cg_[0];
+        R qprev = gk * (left - sg[0]);
+        R z = R(0);
+        R zr[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const R nxt = k + 1 < M ? sg[k + 1] : right;
+            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
+            const R qn = gk1 * (sg[k] - nxt);
+            R r = qprev - qn + cbt[k];
+            if ((vmask >> k) & 1u) r -= cth[k] * sg[k];
+            z = cp[k] * fmx(gk, z, r);
+            zr[k] = z;
+            qprev = qn;
+            gk = gk1;
+        }
+        R exA, u0, agA, u1;
+        cta_scan<0, R>(z, w[M - 1], sA, sB, exA, u0, agA, u1);
+        // backward sweep without carries; the first node with this CTA's forward carry
+        R x = R(0);
+#pragma unroll
+        for (int k = M - 1; k >= 0; --k) {
+            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
+            x = fmx(cp[k] * gk1, x, zr[k]);
+            zr[k] = x;
+        }
+        R bxA, u2, bgA, u3;
+        cta_scan<1, R>(fmx(w[0], exA, zr[0]), cpb[0], sA, sB, bxA, u2, bgA, u3);
+        (void)u0; (void)u1; (void)u2; (void)u3;
+        agA = __shfl_sync(full, agA, 0);
+        bgA = __shfl_sync(full, bgA, 0);
+        const R fst = __shfl_sync(full, sg[0], 0);
+        if (c < CL) {
+            ClSlots<R> *o = cl.map_shared_rank(&sl, c);
+            o->fA[b][rank] = agA; o->bA[b][rank] = bgA;
+            o->first[b][rank] = fst; o->last[b][rank] = s_last; o->flags[b][rank] = pending;
+        }
+        cl.sync();
+        int any = 0;
+#pragma unroll
+        for (int q = 0; q < CL; ++q) any |= sl.flags[b][q];
+        if (any) {                               // an event of the previous step: handle, redo this step
+            pending = 0;
+            handle(any, step - 1, true);
+            cl.sync();                           // the slots are written again by the redone step
+            continue;
+        }
+        // carries across the ranks, halo changes included:
+        //   Y_(q+1) = fB_q Y_q + fA_q + hh_q dfirst_(q+1) + dlast_q   (forward carry into rank q + 1)
+        //   C_(q-1) = bA_q + bAz_q Y_q + bB_q (C_q + dfirst_(q+1))    (increment of rank q's first node)
+        R Y[CL];
+        Y[0] = R(0);
+#pragma unroll
+        for (int q = 0; q + 1 < CL; ++q)
+            Y[q + 1] = fmx(sl.fB[q], Y[q], fmx(sl.hh[q], sl.first[b][q + 1] - sl.first[ob][q + 1], sl.fA[b][q])) +
+                       (sl.last[b][q] - sl.last[ob][q]);
+        R C = R(0), zin = R(0);
+#pragma unroll
+        for (int q = CL - 1; q >= 0; --q) {
+            if (q == rank) zin = Y[q];
+            if (q > rank) {
+                const R dn = q + 1 < CL ? sl.first[b][q + 1] - sl.first[ob][q + 1] : R(0);
+                C = fmx(sl.bB[q], C + dn, fmx(sl.bAz[q], Y[q], sl.bA[b][q]));
+            }
+        }
+        if (rank + 1 < CL) C += sl.first[b][rank + 1] - sl.first[ob][rank + 1];
+        const R cf = fmx(exB, zin, exA);
+        const R cr = fmx(bxB, C, fmx(bxAz, zin, bxA));
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const R dk = fmx(cpb[k], cr, fmx(w[k], cf, zr[k]));
+            if constexpr (sizeof(R) == 4) {               // compensated (Kahan) FP32 update
+                const R y = dk - cc[k];
+                const R tt = sg[k] + y;
+                cc[k] = (tt - sg[k]) - y;
+                sg[k] = tt;
+            } else {
+                sg[k] += dk;
+            }
+        }
+        // void growth by the Robin leak (owner thread only)
+        if (vmask) {
+            for (int q = 0; q < s_nv; ++q) {
+                const int v = s_node[q];
+                if (v / M == g) {
+                    R val = R(0);
+#pragma unroll
+                    for (int k = 0; k < M; ++k)
+                        if (v % M == k) val = sg[k];
+                    s_vol[q] += s_coef[q] * (double)val;
+                }
+            }
+        }
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < M; ++k) hit |= !((vmask >> k) & 1u) && sg[k] >= cth[k];
+        const bool nr = s_rs > 1 && near_guard<R, M>(sg, s_gthr);
+        if (lane == 31) sL[w_] = sg[M - 1];
+        if (lane == 0) sR[w_] = sg[0];
+        // the flags, and the warp halos for the next step
+        pending = __syncthreads_or(hit) ? 1 : 0;
+        if (s_rs > 1) pending |= __syncthreads_or(nr) ? 2 : 0;
+        ++step;
+    }
+    // flags of the last step: handled here, the factors rebuilt by the next launch
+    {
+        const int b = n_steps & 1;
+        if (c < CL) cl.map_shared_rank(&sl, c)->flags[b][rank] = pending;
+        cl.sync();
+        int any = 0;
+        for (int q = 0; q < CL; ++q) any |= sl.flags[b][q];
+        if (any) {
+            handle(any, n_steps - 1, false);
+            __syncthreads();
+            if (g == 0) a.dirty[st] = 1;
+        }
     }
 #pragma unroll
     for (int k = 0; k < M; ++k) a.sig[ps + (int64_t)k * TT + g] = sg[k];
@@ -1702,55 +1786,63 @@ cudaError_t launch_chain(dim3 grid, int T, size_t smem, cudaStream_t st, const C
     }
 }
 
-// FP64 solves the state directly; FP32 solves for the increment so that the
-// rounding of its coefficients cannot drift the conserved slow modes
+// One bucket's launch over S samples: the kernel its shape names.  FP64
+// solves the state directly; FP32 solves for the increment so that the
+// rounding of its coefficients cannot drift the conserved slow modes.
 template <typename R>
-ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
+cudaError_t launch_bucket_raw(ems_ctx *c, const Bucket &b, ChainArgs<R> a, int S) {
     constexpr bool kDelta = sizeof(R) == 4;
-    for (auto &b : c->buckets) {
-        ChainArgs<R> a = chain_args<R>(c, dt, n_steps);
-        a.trees = b.d_trees;
-        a.n_bucket = (int)b.trees.size();
-        if (b.chain && b.CL > 1) {
-            // one thread-block cluster of CL CTAs per (tree, sample)
-            {
-                constexpr int MC = sizeof(R) == 4 ? 16 : 8;
-                if (b.M != MC) return fail(c, EMS_E_STATE, "cluster chain layout with an unexpected chunk length");
-                cudaLaunchConfig_t cfg = {};
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeClusterDimension;
-                at[0].val.clusterDim.x = b.CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
-                cfg.gridDim = dim3((unsigned)(b.trees.size() * b.CL), c->S);
-                cfg.blockDim = dim3(b.T / b.CL);
-                cfg.stream = c->stream;
-                cfg.attrs = at;
-                cfg.numAttrs = 1;
-                cudaError_t e = b.CL == 2 ? cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 2>, a)
-                              : b.CL == 4 ? cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 4>, a)
-                                          : cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 8>, a);
-                EMS_CUDA(c, e);
-                ++c->launches;
-                continue;
-            }
+    a.trees = b.d_trees;
+    a.n_bucket = (int)b.trees.size();
+    a.S = S;
+    ++c->launches;
+    if (!b.chain) {
+        const int64_t items = (int64_t)b.trees.size() * S;   // (tree, sample) pairs
+        k_tree<R><<<(unsigned)((items + 63) / 64), 64, 0, c->stream>>>(a);
+        return cudaGetLastError();
+    }
+    const dim3 grid((unsigned)b.trees.size(), S);
+    cudaError_t e = cudaSuccess;
+    switch (b.kind) {
+        case EMS_CHAIN_CLUSTER: {           // one thread-block cluster of CL CTAs per (tree, sample)
+            constexpr int MC = sizeof(R) == 4 ? 16 : 8;
+            if (b.M != MC || b.T % b.CL || b.T / b.CL > kClusterCtaThreads) return cudaErrorInvalidValue;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = b.CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)(b.trees.size() * b.CL), S);
+            cfg.blockDim = dim3(b.T / b.CL);
+            cfg.stream = c->stream;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            e = b.CL == 2 ? cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 2>, a)
+              : b.CL == 4 ? cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 4>, a)
+              : b.CL == 8 ? cudaLaunchKernelEx(&cfg, k_chain_cl<R, MC, 8>, a)
+                          : cudaErrorInvalidValue;
+            break;
         }
-        if (b.chain) {
-            dim3 grid((unsigned)b.trees.size(), c->S);
-            cudaError_t e = cudaSuccess;
+        case EMS_CHAIN_REGISTER:
             if constexpr (kDelta) {
-                if ((b.M == 4 && b.T <= RegMaxThreads<4>::value) || (b.M == 8 && b.T <= RegMaxThreads<8>::value) ||
-                    (b.M == 16 && b.T <= RegMaxThreads<16>::value)) {
-                    if (b.M == 4) k_chain_reg<4><<<grid, b.T, 0, c->stream>>>(a);
-                    else if (b.M == 8) k_chain_reg<8><<<grid, b.T, 0, c->stream>>>(a);
-                    else k_chain_reg<16><<<grid, b.T, 0, c->stream>>>(a);
-                    ++c->launches;
-                    EMS_CUDA(c, cudaGetLastError());
-                    continue;
-                }
+                if (b.T > reg_max_threads(b.M)) return cudaErrorInvalidValue;
+                if (b.M == 4) k_chain_reg<4><<<grid, b.T, 0, c->stream>>>(a);
+                else if (b.M == 8) k_chain_reg<8><<<grid, b.T, 0, c->stream>>>(a);
+                else if (b.M == 16) k_chain_reg<16><<<grid, b.T, 0, c->stream>>>(a);
+                else return cudaErrorInvalidValue;
+                e = cudaGetLastError();
+                break;
+            } else {
+                return cudaErrorInvalidValue;      // the register chain kernel is FP32 only
             }
-            // increment form: coefficients in shared memory while they fit
-            const size_t smem_c = kDelta ? 5 * sizeof(R) * (size_t)b.T * b.M : 0;
-            const bool smc = kDelta && smem_c <= 200 * 1024;
-            const size_t smem = smc ? smem_c : (kDelta ? sizeof(float2) * (size_t)b.T * b.M : 0);
+        case EMS_CHAIN_SHARED:
+        case EMS_CHAIN_GLOBAL: {
+            // increment form: the chunk coefficients in shared memory (SHARED),
+            // else the forward sweep staged there (8 bytes per node)
+            const bool smc = b.kind == EMS_CHAIN_SHARED;
+            if (smc && !kDelta) return cudaErrorInvalidValue;   // the shared-memory kernel is FP32 only
+            const size_t smem = smc ? 5 * sizeof(R) * (size_t)b.T * b.M
+                                    : (kDelta ? sizeof(float2) * (size_t)b.T * b.M : 0);
+            if (smc && smem > kSharedCoefBytes) return cudaErrorInvalidValue;
             switch (b.M) {
                 case 4: e = smc ? launch_chain<R, 4, kDelta, true>(grid, b.T, smem, c->stream, a)
                                 : launch_chain<R, 4, kDelta, false>(grid, b.T, smem, c->stream, a); break;
@@ -1762,17 +1854,29 @@ ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
                                  : launch_chain<R, 32, kDelta, false>(grid, b.T, smem, c->stream, a); break;
                 case 64: e = smc ? launch_chain<R, 64, kDelta, true>(grid, b.T, smem, c->stream, a)
                                  : launch_chain<R, 64, kDelta, false>(grid, b.T, smem, c->stream, a); break;
-                default: return fail(c, EMS_E_STATE, "unsupported chunk length");
+                default: return cudaErrorInvalidValue;
             }
-            EMS_CUDA(c, e);
-            ++c->launches;
-        } else {
-            const int64_t items = (int64_t)b.trees.size() * c->S;   // (tree, sample) pairs
-            k_tree<R><<<(unsigned)((items + 63) / 64), 64, 0, c->stream>>>(a);
-            ++c->launches;
+            break;
         }
-        EMS_CUDA(c, cudaGetLastError());
+        default: return cudaErrorInvalidValue;
     }
+    return e;
+}
+
+template <typename R>
+ems_status launch_bucket(ems_ctx *c, const Bucket &b, ChainArgs<R> a, int S) {
+    const cudaError_t e = launch_bucket_raw<R>(c, b, a, S);
+    if (e != cudaSuccess) {
+        char what[96];
+        snprintf(what, sizeof what, "chain launch (kernel %d, M %d, T %d, CL %d)", b.kind, b.M, b.T, b.CL);
+        return cuda_check(c, e, what);
+    }
+    return EMS_OK;
+}
+
+template <typename R>
+ems_status launch_advance(ems_ctx *c, double dt, int n_steps) {
+    for (auto &b : c->buckets) EMS_TRY(launch_bucket<R>(c, b, chain_args<R>(c, dt, n_steps), c->S));
     return EMS_OK;
 }
 
@@ -1781,6 +1885,178 @@ inline dim3 grid_1d(int64_t n, int S) {
     if (b > 4096) b = 4096;
     if (b < 1) b = 1;
     return dim3((unsigned)b, (unsigned)S);
+}
+
+// ---------------------------------------------------------------------------
+// Shape autotuner.  Each candidate shape of a bucket's chains runs on scratch
+// copies (stress repacked into the candidate's layout; thresholds, voids and
+// schedules copied), so the context's state is never touched.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_repack(const int32_t *trees, const int64_t *toff, const int64_t *pb_src, int T_src, int M_src,
+                         int64_t P_src, const int64_t *pb_dst, const int32_t *T_dst, int M_dst, int64_t P_dst,
+                         const R *src, R *dst) {
+    const int t = trees[blockIdx.x];
+    const int64_t s = blockIdx.y;
+    const int64_t n = toff[t + 1] - toff[t];
+    const int Td = T_dst[t];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        dst[s * P_dst + pb_dst[t] + (i % M_dst) * Td + i / M_dst] =
+            src[s * P_src + pb_src[t] + (i % M_src) * T_src + i / M_src];
+}
+
+struct TuneShape { int kind, M, CL; };
+
+// Time one shape on the bucket's chains over the first S mapped samples: a
+// launch that factorises and runs n_steps steps, then n_steps more timed.
+// *ms < 0: some chain of the bucket cannot take the shape.
+template <typename R>
+ems_status tune_time(ems_ctx *c, const Bucket &b, const TuneShape &sh, int S, double dt, int n_steps, double *ms) {
+    const int nt = c->n_trees, maxv = c->maxv, prec = c->prm.precision;
+    const int64_t N = c->N;
+    std::vector<int64_t> pb(nt, 0);
+    std::vector<int32_t> Tt(nt, 0);
+    std::map<int, std::vector<int32_t>> groups;    // chains of equal team size launch together
+    int64_t P = 0;
+    for (int32_t t : b.trees) {
+        const int64_t n = c->trees.off[t + 1] - c->trees.off[t];
+        int T = 0;
+        if (!shape_valid(n, prec, sh.kind, sh.M, sh.CL, &T)) { *ms = -1.0; return EMS_OK; }
+        pb[t] = P; Tt[t] = T; P += (int64_t)T * sh.M;
+        groups[T].push_back(t);
+    }
+    const size_t ts = (size_t)S * nt, L = (size_t)S * P;
+    size_t bytes = 0;
+    auto take = [&](size_t n) { const size_t o = bytes; bytes += (n + 255) / 256 * 256; return o; };
+    const size_t o_pk = take(10 * L * sizeof(R)), o_pinv = take(L * 8), o_thr = take((size_t)S * N * 8);
+    const size_t o_vc = take(ts * 4), o_vn = take(ts * maxv * 4), o_vs = take(ts * maxv * 4);
+    const size_t o_vv = take(ts * maxv * 8), o_vt = take(ts * maxv * 8);
+    const size_t o_dirty = take(ts * 4), o_sched = take(ts * 4), o_fdt = take(ts * 8), o_kr = take(ts * 4);
+    const size_t o_kd = take(ts * 4), o_misc = take(64 * 4 + 8), o_pb = take((size_t)nt * 8), o_T = take((size_t)nt * 4);
+    const size_t o_tr = take(b.trees.size() * 4);
+    size_t fr = 0, tot = 0;
+    EMS_CUDA(c, cudaMemGetInfo(&fr, &tot));
+    if (bytes > fr / 10 * 9) return fail(c, EMS_E_NOMEM, "autotuner scratch does not fit: lower max_samples");
+    char *base = nullptr;
+    EMS_CUDA(c, cudaMalloc(&base, bytes));
+    cudaStream_t st = c->stream;
+    Dev &d = c->d;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ems_status rc = EMS_OK;
+    auto run = [&]() -> ems_status {
+        EMS_CUDA(c, cudaMemsetAsync(base, 0, bytes, st));
+        const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice, hd = cudaMemcpyHostToDevice;
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_thr, d.thr, (size_t)S * N * 8, dd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_vc, d.v_count, ts * 4, dd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_vn, d.v_node, ts * maxv * 4, dd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_vs, d.v_seg, ts * maxv * 4, dd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_vv, d.v_vol, ts * maxv * 8, dd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_vt, d.v_tnuc, ts * maxv * 8, dd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_sched, d.sched, ts * 4, dd, st));
+        const std::vector<int32_t> ones(ts, 1);
+        const std::vector<double> nofdt(ts, -1.0);
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_dirty, ones.data(), ts * 4, hd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_fdt, nofdt.data(), ts * 8, hd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_pb, pb.data(), (size_t)nt * 8, hd, st));
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_T, Tt.data(), (size_t)nt * 4, hd, st));
+        std::vector<Bucket> gb;
+        std::vector<int32_t> order;
+        for (auto &kv : groups) {
+            Bucket g;
+            g.chain = true; g.T = kv.first; g.M = sh.M; g.CL = sh.CL; g.kind = sh.kind; g.trees = kv.second;
+            g.d_trees = (int32_t *)(base + o_tr) + order.size();
+            order.insert(order.end(), kv.second.begin(), kv.second.end());
+            gb.push_back(std::move(g));
+        }
+        EMS_CUDA(c, cudaMemcpyAsync(base + o_tr, order.data(), order.size() * 4, hd, st));
+        R *pk = (R *)(base + o_pk);
+        k_repack<R><<<dim3((unsigned)b.trees.size(), S), 256, 0, st>>>(
+            b.d_trees, d.toff, d.pbase, b.T, b.M, c->P, (const int64_t *)(base + o_pb), (const int32_t *)(base + o_T),
+            sh.M, P, (const R *)d.sig, pk);
+        ++c->launches;
+        EMS_CUDA(c, cudaGetLastError());
+        ChainArgs<R> a = chain_args<R>(c, dt, n_steps);
+        a.pbase = (const int64_t *)(base + o_pb); a.P = P;
+        a.sig = pk; a.alpha = pk + L; a.beta = pk + 2 * L; a.gam = pk + 3 * L; a.uu = pk + 4 * L;
+        a.Pf = pk + 5 * L; a.Pb = pk + 6 * L; a.dtg = pk + 7 * L; a.dtl = pk + 8 * L; a.kc = pk + 9 * L;
+        a.pinv = (double *)(base + o_pinv);
+        a.thr = (double *)(base + o_thr);
+        a.v_count = (int32_t *)(base + o_vc); a.v_node = (int32_t *)(base + o_vn); a.v_seg = (int32_t *)(base + o_vs);
+        a.v_vol = (double *)(base + o_vv); a.v_tnuc = (double *)(base + o_vt);
+        a.dirty = (int32_t *)(base + o_dirty); a.sched = (int32_t *)(base + o_sched); a.fdt = (double *)(base + o_fdt);
+        a.kr_mode = (const int32_t *)(base + o_kr); a.kdone = (const int32_t *)(base + o_kd);
+        int32_t *misc = (int32_t *)(base + o_misc);
+        a.status = misc; a.counters = misc + 32; a.work = (unsigned long long *)(misc + 64);
+        a.refactor_all = 0;               // the first launch factorises every chain (dirty)
+        a.t0p = nullptr;
+        for (const Bucket &g : gb) {
+            // a shape the device cannot launch (a configuration error; the
+            // context stays usable) is skipped, not an error of the tuner
+            const cudaError_t le = launch_bucket_raw<R>(c, g, a, S);
+            if (le == cudaErrorInvalidValue || le == cudaErrorInvalidConfiguration ||
+                le == cudaErrorLaunchOutOfResources || le == cudaErrorInvalidClusterSize) {
+                (void)cudaGetLastError();
+                *ms = -1.0;
+                return EMS_OK;
+            }
+            EMS_CUDA(c, le);
+        }
+        EMS_CUDA(c, cudaEventCreate(&e0));
+        EMS_CUDA(c, cudaEventCreate(&e1));
+        EMS_CUDA(c, cudaEventRecord(e0, st));
+        for (const Bucket &g : gb) EMS_TRY(launch_bucket<R>(c, g, a, S));
+        EMS_CUDA(c, cudaEventRecord(e1, st));
+        EMS_CUDA(c, cudaEventSynchronize(e1));
+        float t = 0.f;
+        EMS_CUDA(c, cudaEventElapsedTime(&t, e0, e1));
+        *ms = t;
+        return EMS_OK;
+    };
+    rc = run();
+    cudaStreamSynchronize(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(base);
+    return rc;
+}
+
+template <typename R>
+ems_status autotune_run(ems_ctx *c, int n_steps, int max_samples, ems_chain_rule *rules, double *ms,
+                        double *ms_default, int cap, int *n_rules) {
+    const double dt = c->prm.horizon / ((double)c->prm.n_outer * c->prm.n_inner);
+    const int S = std::min(max_samples, c->S), prec = c->prm.precision;
+    int k = 0;
+    for (const Bucket &b : c->buckets) {
+        if (!b.chain) continue;
+        if (k >= cap) break;
+        int64_t lo = LLONG_MAX, hi = 0;
+        for (int32_t t : b.trees) {
+            const int64_t n = c->trees.off[t + 1] - c->trees.off[t];
+            lo = std::min(lo, n);
+            hi = std::max(hi, n);
+        }
+        const TuneShape cur{b.kind, b.M, b.CL};
+        double def_ms = -1.0;
+        EMS_TRY(tune_time<R>(c, b, cur, S, dt, n_steps, &def_ms));
+        TuneShape best = cur;
+        double best_ms = def_ms;
+        for (const ems_chain_rule &r : shape_candidates(hi, prec)) {
+            if (r.kind == cur.kind && r.M == cur.M && r.CL == cur.CL) continue;
+            double t_ms = -1.0;
+            EMS_TRY(tune_time<R>(c, b, TuneShape{r.kind, r.M, r.CL}, S, dt, n_steps, &t_ms));
+            if (t_ms >= 0.0 && t_ms < best_ms) { best = TuneShape{r.kind, r.M, r.CL}; best_ms = t_ms; }
+        }
+        // a change of shape has to beat the current one by 3 %, more than the timing noise
+        if (best_ms > 0.97 * def_ms) { best = cur; best_ms = def_ms; }
+        int T = 0;
+        shape_valid(hi, prec, best.kind, best.M, best.CL, &T);
+        rules[k] = ems_chain_rule{lo, hi, best.kind, best.M, best.CL, T};
+        if (ms) ms[k] = best_ms;
+        if (ms_default) ms_default[k] = def_ms;
+        ++k;
+    }
+    *n_rules = k;
+    return EMS_OK;
 }
 
 }  // namespace
@@ -2042,6 +2318,25 @@ extern "C" ems_status ems_set_thermal_perturbation(ems_ctx *c, const double *dT,
     } else {
         EMS_TRY(sample_physics(c));
     }
+    EMS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EMS_OK;
+}
+
+extern "C" ems_status ems_autotune(ems_ctx *c, int n_steps, int max_samples, ems_chain_rule *rules, double *ms,
+                                   double *ms_default, int cap, int *n_rules) {
+    if (!c || n_steps < 1 || max_samples < 1 || cap < 0 || (cap > 0 && !rules) || !n_rules) return EMS_E_INVAL;
+    if (!c->loaded) return fail(c, EMS_E_STATE, "no grid loaded");
+    if (!c->have_u) return fail(c, EMS_E_STATE, "autotune before the first IR solve (the forcing needs the currents)");
+    if (c->prm.method != EMS_BE) return fail(c, EMS_E_STATE, "the autotuner picks backward-Euler shapes");
+    *n_rules = 0;
+    if (windowed(c)) map_window(c, 0, c->W);
+    ems_status s = window_derive(c);
+    if (s == EMS_OK) s = forcing(c);
+    if (s == EMS_OK)
+        s = c->prm.precision == EMS_F32 ? autotune_run<float>(c, n_steps, max_samples, rules, ms, ms_default, cap, n_rules)
+                                        : autotune_run<double>(c, n_steps, max_samples, rules, ms, ms_default, cap, n_rules);
+    if (windowed(c)) map_all(c);
+    EMS_TRY(s);
     EMS_CUDA(c, cudaStreamSynchronize(c->stream));
     return EMS_OK;
 }

@@ -14,7 +14,7 @@ from . import _abi as A
 class Engine:
     def __init__(self, params, grid, precision=A.EMS_F64, method=A.EMS_BE, ir_rtol=1e-13,
                  ir_max_iter=20000, max_voids=16, workspace="torch", stream=None, thermal=True,
-                 ir_precond=A.EMS_PC_AUTO, window=0):
+                 ir_precond=A.EMS_PC_AUTO, window=0, chain_rules=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Engine needs a CUDA device")
@@ -23,7 +23,10 @@ class Engine:
         self.prm = A.make_params(params, precision, method, ir_rtol, ir_max_iter, max_voids, ir_precond, window)
         self.gd = A.GridDesc(grid)
         self.S = self.gd.n_samples
-        nbytes = self.L.ems_workspace_bytes(ctypes.byref(self.prm), ctypes.byref(self.gd.desc))
+        self.chain_rules = list(chain_rules or [])
+        self._rules = A.rules_array(self.chain_rules)
+        nbytes = self.L.ems_workspace_bytes_rules(ctypes.byref(self.prm), ctypes.byref(self.gd.desc), self._rules,
+                                                  len(self.chain_rules))
         if nbytes == 0:
             raise A.EmsError(A.EMS_E_INVAL, "invalid grid or parameters (ems_workspace_bytes returned 0)")
         self.ws_bytes = int(nbytes)
@@ -41,6 +44,8 @@ class Engine:
                                       ctypes.c_void_p(stream.cuda_stream), ctypes.c_void_p(base),
                                       ctypes.c_size_t(self.ws_bytes)), None)
         self.ctx = ctx
+        if self.chain_rules:
+            self._check(self.L.ems_set_chain_rules(self.ctx, self._rules, len(self.chain_rules)))
         self._check(self.L.ems_load_grid(self.ctx, ctypes.byref(self.gd.desc)))
         nt = ctypes.c_int(); nn = ctypes.c_int64(); ns = ctypes.c_int()
         self._check(self.L.ems_dims(self.ctx, ctypes.byref(nt), ctypes.byref(nn), ctypes.byref(ns)))
@@ -114,6 +119,24 @@ class Engine:
         nv = ctypes.c_int()
         self._check(self.L.ems_stress_advance(self.ctx, float(dt), int(n_steps), int(method), ctypes.byref(nv)))
         return nv.value
+
+    def autotune(self, n_steps=32, max_samples=2):
+        """Time every valid chain shape of each launch group on scratch copies
+        (ems_autotune); the context is unchanged.  Returns one rule per group
+        with its time (ms) and the current shape's (ms_default)."""
+        cap = 256
+        arr = (A.EmsChainRule * cap)()
+        ms = np.zeros(cap); md = np.zeros(cap)
+        k = ctypes.c_int()
+        self._check(self.L.ems_autotune(self.ctx, int(n_steps), int(max_samples), arr,
+                                        ms.ctypes.data_as(A.c_double_p), md.ctypes.data_as(A.c_double_p), cap,
+                                        ctypes.byref(k)))
+        out = []
+        for i in range(k.value):
+            r = A.rule_dict(arr[i])
+            r["ms"], r["ms_default"] = float(ms[i]), float(md[i])
+            out.append(r)
+        return out
 
     def krylov_reduce(self, q, eta=1.0):
         nr = ctypes.c_int(); nf = ctypes.c_int()

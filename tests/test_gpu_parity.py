@@ -489,6 +489,38 @@ def test_krylov_zero_forcing_falls_back_to_be():
     eng.close()
 
 
+def test_krylov_rank_deficient_block_falls_back_to_be():
+    """A uniform initial stress and no void: A 1 = 0 makes R C map the
+    constant starting column onto itself, so the second block is rank
+    deficient (Sec. IV-E.5) and every tree is handed to backward Euler.  The
+    oracle's Alg. 1 reports 'rank' for the same trees; the GPU's stress after
+    a Krylov-method aging step equals a plain BE engine's, and the whole run
+    matches the oracle's Krylov stepper (which falls back the same way)."""
+    from paper_2604_10743_gb300 import EMS_KRYLOV
+    from oracle import krylov as K
+    g = es.tiny_grid()
+    p = es.default_params(krylov_q=10, n_outer=4, sigma_T=50e6)
+    kr = _engine(p, g, method=EMS_KRYLOV)
+    be = _engine(p, g)
+    kr.ir_solve(); be.ir_solve()
+    nr, nf = kr.krylov_reduce(10, 1.0)
+    assert nr == 0 and nf == 16
+    dt = p["horizon"] / (p["n_outer"] * p["n_inner"])
+    kr.stress_advance(dt, p["n_inner"], EMS_KRYLOV)
+    be.stress_advance(dt, p["n_inner"])
+    assert _relerr(kr.sigma()[0], be.sigma()[0]) < 1e-12
+    kr.close(); be.close()
+    # the whole run: reduced models once the stress is no longer uniform
+    eng = _engine(p, g, method=EMS_KRYLOV)
+    r = eng.ttf()
+    ks = K.KrylovStepper(q=10)
+    ref = F.run_ttf(g, p, keep_state=True, stepper=ks)
+    assert ks.n_fallback >= 16 and ks.n_reduced > 0
+    assert _relerr(eng.sigma()[0], ref["state"].sigma) < TOL64
+    assert abs(r["final_drop"][0] - ref["final_drop"]) <= 1e-6 * ref["final_drop"]
+    eng.close()
+
+
 def test_krylov_reduce_counts():
     from paper_2604_10743_gb300 import EMS_KRYLOV
     g = es.tiny_grid()

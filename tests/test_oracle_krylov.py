@@ -147,3 +147,23 @@ def test_augmented_cache_tracks_backward_euler_stale_cache_does_not():
         err[policy] = np.abs(st.sigma - ref.sigma).max() / np.abs(ref.sigma).max()
     assert err["augment"] < 3e-4
     assert err["stale"] > 30 * err["augment"]
+
+
+def test_uniform_initial_stress_makes_the_second_block_rank_deficient():
+    """Before any void the Neumann operator has A 1 = 0, so (s0 C - A)^-1 C 1
+    = 1 / s0: the constant column of the starting block is mapped onto itself.
+    The next block then holds that repeated direction (nothing left after
+    orthogonalisation) beside a new one, which is the rank-deficient case of
+    Sec. IV-E.5 under both orthogonalisation orders; with a zero initial
+    stress the same tree reduces."""
+    g, tr, phys, f = _chain(cells=25)
+    n = tr["n_nodes"]
+    C, A, ft = K.tree_system(tr, phys, f, np.zeros(n, np.int32), 0)
+    s0 = 1.0 / K.shift_time(tr, phys, 0, 1.0)
+    ones = np.ones(n)
+    assert np.abs(A @ ones).max() < 1e-12 * abs(A).max() * n      # rows of A sum to zero
+    lu = spla.splu((s0 * C - A).tocsc())
+    assert np.abs(lu.solve(C @ ones) * s0 - 1.0).max() < 1e-12
+    for ortho in ("mgs", "cgs2"):
+        assert K.krylov_basis(C, A, ft, np.full(n, 50e6), s0, 6, ortho=ortho)[4] == "rank"
+        assert K.krylov_basis(C, A, ft, np.zeros(n), s0, 6, ortho=ortho)[4] == "ok"
