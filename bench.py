@@ -154,7 +154,11 @@ def tuned_rules(p, prec, args):
     e = Engine(p, full_chip(2), precision=prec, max_voids=args.max_voids)
     e.ir_solve()
     table = e.autotune(n_steps=32, max_samples=2)
+    log = e.autotune_log()
     e.close()
+    for k, r in enumerate(table):
+        r["candidates"] = [{"kernel": x["kernel"], "M": x["M"], "CL": x["CL"], "T": x["T"], "ms": round(x["ms"], 3)}
+                           for x in log if x["group"] == k]
     return table, time.perf_counter() - t0
 
 

@@ -250,6 +250,15 @@ size_t ems_workspace_bytes_rules(const ems_params *params, const ems_grid_desc *
 ems_status ems_autotune(ems_ctx *ctx, int n_steps, int max_samples, ems_chain_rule *rules, double *ms,
                         double *ms_default, int cap, int *n_rules);
 
+/*
+ * Every shape the last ems_autotune call timed: shapes[k] (n_lo / n_hi: its
+ * group's chain lengths), ms[k] its time per launch (-1: the device cannot
+ * launch it), group[k] the group's index in the rules.  count: out, number
+ * written (at most cap).  Arrays may be NULL with cap = 0 to get the count.
+ */
+ems_status ems_autotune_log(const ems_ctx *ctx, int cap, ems_chain_rule *shapes, double *ms, int32_t *group,
+                            int *count);
+
 /* Number of trees / stress nodes / samples of the loaded grid. */
 ems_status ems_dims(const ems_ctx *ctx, int *n_trees, int64_t *n_stress_nodes,
                     int *n_samples);

@@ -83,7 +83,7 @@ EXPORTS = ["ems_workspace_bytes", "ems_create", "ems_destroy", "ems_last_error",
            "ems_launch_count", "ems_ir_iterations", "ems_ir_pcg_noalloc", "ems_joule_profile", "ems_set_wait_limit",
            "ems_get_node_temperature", "ems_set_thermal_perturbation", "ems_spice_parse", "ems_netlist_desc",
            "ems_netlist_error", "ems_netlist_free", "ems_chain_candidates", "ems_set_chain_rules",
-           "ems_workspace_bytes_rules", "ems_autotune",
+           "ems_workspace_bytes_rules", "ems_autotune", "ems_autotune_log",
            # include/ems_surrogate.h
            "ems_mlp_create", "ems_mlp_destroy", "ems_mlp_last_error", "ems_mlp_param_count",
            "ems_mlp_set_params", "ems_mlp_get_params", "ems_mlp_set_norm", "ems_mlp_fit_norm", "ems_mlp_gradients",
@@ -161,6 +161,8 @@ def lib(path=None):
     L.ems_workspace_bytes_rules.argtypes = [ctypes.POINTER(EmsParams), ctypes.POINTER(EmsGridDesc), rp, S]
     L.ems_autotune.restype = S
     L.ems_autotune.argtypes = [vp, S, S, rp, c_double_p, c_double_p, S, ctypes.POINTER(ctypes.c_int)]
+    L.ems_autotune_log.restype = S
+    L.ems_autotune_log.argtypes = [vp, S, rp, c_double_p, c_int32_p, ctypes.POINTER(ctypes.c_int)]
     L.ems_joule_profile.restype = S
     L.ems_joule_profile.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.ems_get_node_temperature.restype = S

@@ -553,10 +553,11 @@ bool shape_valid(int64_t n, int prec, int kind, int M, int CL, int *T) {
             if (CL != 1 || t > chain_max_threads(prec, M)) return false;
             break;
         case EMS_CHAIN_CLUSTER: {
-            if (M != cluster_chunk(prec) || (CL != 2 && CL != 4 && CL != 8)) return false;
+            const int tmax = CL >= 2 && CL <= 8 ? cluster_max_threads(prec, M, CL) : 0;
+            if (tmax == 0) return false;
             const int64_t tc = round_warp((th + CL - 1) / CL);
             // every CTA must hold nodes of the chain
-            if (tc > kClusterCtaThreads || th <= (int64_t)(CL - 1) * tc) return false;
+            if (tc > tmax || th <= (int64_t)(CL - 1) * tc) return false;
             t = tc * CL;
             break;
         }
@@ -568,7 +569,8 @@ bool shape_valid(int64_t n, int prec, int kind, int M, int CL, int *T) {
 
 // Built-in choice.  Backward-Euler chains longer than one register-resident
 // CTA holds (FP32: 5,120 nodes; FP64: past the streaming kernel's 16,384):
-// the smallest cluster of 2, 4 or 8 CTAs of <= 320 threads.  FP32 chains the
+// the smallest cluster that holds them (16 nodes per thread in FP32, 8 in
+// FP64).  FP32 chains the
 // register kernel holds: 16 nodes per thread (<= 320 threads) for chains of
 // more than 2,048 nodes, else 8 (<= 576 threads).  Otherwise the streaming
 // kernel with the smallest power-of-two chunk in [4, 64] that keeps the team
@@ -579,7 +581,7 @@ static void builtin_shape(int64_t n, int prec, int method, int *T, int *M, int *
     *CL = 1;
     const int64_t one_cta = prec == EMS_F32 ? 320 * 16 : 256 * 64;
     if (method == EMS_BE && n > one_cta)
-        for (int cl : {2, 4, 8})
+        for (int cl = 2; cl <= 8; ++cl)
             if (shape_valid(n, prec, EMS_CHAIN_CLUSTER, cluster_chunk(prec), cl, T)) {
                 *M = cluster_chunk(prec); *CL = cl; *kind = EMS_CHAIN_CLUSTER;
                 return;
@@ -627,7 +629,8 @@ std::vector<ems_chain_rule> shape_candidates(int64_t n, int prec) {
     };
     for (int kind : {EMS_CHAIN_REGISTER, EMS_CHAIN_SHARED, EMS_CHAIN_GLOBAL})
         for (int M : {4, 8, 16, 32, 64}) add(kind, M, 1);
-    for (int CL : {2, 4, 8}) add(EMS_CHAIN_CLUSTER, cluster_chunk(prec), CL);
+    for (int M : {8, 16})
+        for (int CL = 2; CL <= 8; ++CL) add(EMS_CHAIN_CLUSTER, M, CL);
     return out;
 }
 
@@ -652,8 +655,8 @@ extern "C" ems_status ems_set_chain_rules(ems_ctx *c, const ems_chain_rule *rule
         if (r.n_lo < 1 || r.n_hi < r.n_lo) return fail(c, EMS_E_INVAL, "rule range must have 1 <= n_lo <= n_hi");
         if (r.kind < EMS_CHAIN_DEFAULT || r.kind > EMS_CHAIN_CLUSTER) return fail(c, EMS_E_INVAL, "unknown chain kernel");
         if (r.kind != EMS_CHAIN_DEFAULT &&
-            (!pow2_chunk(r.M) || (r.kind == EMS_CHAIN_CLUSTER ? (r.CL != 2 && r.CL != 4 && r.CL != 8) : r.CL != 1)))
-            return fail(c, EMS_E_INVAL, "M must be 4, 8, 16, 32 or 64; CL 2, 4 or 8 for a cluster, else 1");
+            (!pow2_chunk(r.M) || (r.kind == EMS_CHAIN_CLUSTER ? (r.CL < 2 || r.CL > 8) : r.CL != 1)))
+            return fail(c, EMS_E_INVAL, "M must be 4, 8, 16, 32 or 64; CL 2..8 for a cluster, else 1");
     }
     c->rules.assign(rules, rules + n_rules);
     return EMS_OK;

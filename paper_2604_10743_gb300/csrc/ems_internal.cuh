@@ -80,9 +80,19 @@ inline int chain_max_threads(int prec, int M) {
 // FP32 register-resident kernel: threads a CTA may have per chunk length
 // (its state, coefficients and compensation stay in registers)
 inline int reg_max_threads(int M) { return M == 4 ? 896 : M == 8 ? 576 : M == 16 ? 320 : 0; }
-constexpr int kClusterCtaThreads = 320;        // threads per CTA of the cluster kernel
 constexpr size_t kSharedCoefBytes = 200 * 1024; // FP32 streaming kernel: coefficients staged while they fit
+// cluster chain kernel: nodes per thread of the built-in choice, and the
+// threads a CTA may have for each compiled (precision, M, CL); 0: none.
+// FP32 16 per thread: <= 256 threads (255 registers) on 5- and 6-CTA clusters.
 inline int cluster_chunk(int prec) { return prec == EMS_F32 ? 16 : 8; }
+inline int cluster_max_threads(int prec, int M, int CL) {
+    if (prec == EMS_F32) {
+        if (M == 16) return (CL == 2 || CL == 4 || CL == 8) ? 320 : (CL == 5 || CL == 6) ? 256 : 0;
+        if (M == 8) return (CL == 4 || CL == 8) ? 320 : 0;
+        return 0;
+    }
+    return (M == 8 && (CL == 2 || CL == 4 || CL == 8)) ? 320 : 0;
+}
 
 // ---------------------------------------------------------------------------
 // Host-side tree extraction result (canonical order)
@@ -241,6 +251,8 @@ struct ems_ctx {
     std::vector<ems::TreePack> pack;
     std::vector<ems::Bucket> buckets;
     std::vector<ems_chain_rule> rules;   // chain shapes for the next load (autotuner's table)
+    struct TuneRec { ems_chain_rule shape; double ms; int group; };
+    std::vector<TuneRec> tune_log;       // every shape the last autotune timed
     ems::Dev d{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int coop_blocks = 0;       // resident CTAs for the cooperative PCG

@@ -138,6 +138,23 @@ class Engine:
             out.append(r)
         return out
 
+    def autotune_log(self):
+        """Every shape the last autotune timed: dicts with ms (-1: not
+        launchable) and the group index."""
+        n = ctypes.c_int()
+        self._check(self.L.ems_autotune_log(self.ctx, 0, None, None, None, ctypes.byref(n)))
+        cap = max(1, n.value)
+        arr = (A.EmsChainRule * cap)()
+        ms = np.zeros(cap); grp = np.zeros(cap, np.int32)
+        self._check(self.L.ems_autotune_log(self.ctx, cap, arr, ms.ctypes.data_as(A.c_double_p),
+                                            grp.ctypes.data_as(A.c_int32_p), ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = A.rule_dict(arr[i])
+            r["ms"], r["group"] = float(ms[i]), int(grp[i])
+            out.append(r)
+        return out
+
     def krylov_reduce(self, q, eta=1.0):
         nr = ctypes.c_int(); nf = ctypes.c_int()
         self._check(self.L.ems_krylov_reduce(self.ctx, int(q), float(eta), ctypes.byref(nr), ctypes.byref(nf)))

@@ -101,6 +101,13 @@ def test_autotune_leaves_the_context_unchanged(window):
     for r in table:
         assert 1 <= r["n_lo"] <= r["n_hi"] and r["T"] * r["M"] >= r["n_hi"]
         assert 0.0 < r["ms"] <= r["ms_default"]
+    # the log holds every shape timed; each group's rule is its fastest, or
+    # the built-in shape when nothing beat it by 3 %
+    log = eng.autotune_log()
+    assert len(log) > len(table)
+    for k, r in enumerate(table):
+        times = [e["ms"] for e in log if e["group"] == k and e["ms"] > 0]
+        assert r["ms"] == min(times) or (r["ms"] == r["ms_default"] and min(times) > 0.97 * r["ms_default"])
     ra = eng.ttf()
     rb = twin.ttf()
     assert _relerr(eng.sigma(), twin.sigma()) < 1e-12

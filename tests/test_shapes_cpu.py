@@ -25,8 +25,8 @@ def _check_candidate(r, n, prec):
     assert T % (32 * CL) == 0                       # whole warps in every CTA
     tc = T // CL
     if r["kernel"] == "cluster":
-        assert CL in (2, 4, 8) and tc <= 320
-        assert M == (16 if prec == 1 else 8)
+        assert 2 <= CL <= 8 and tc <= 320
+        assert M in ((8, 16) if prec == 1 else (8,))
         assert (CL - 1) * tc * M < n                # no CTA without nodes
     else:
         assert CL == 1
@@ -52,7 +52,9 @@ def test_builtin_choice_first(A):
     # full-chip stripes: a 4-CTA cluster in FP32, 8 CTAs in FP64
     c32 = A.chain_candidates(20471, 1)
     assert (c32[0]["kernel"], c32[0]["M"], c32[0]["CL"], c32[0]["T"]) == ("cluster", 16, 4, 1280)
-    assert {(r["kernel"], r["M"], r["CL"]) for r in c32} >= {("cluster", 16, 8), ("global", 32, 1), ("global", 64, 1)}
+    assert {(r["kernel"], r["M"], r["CL"]) for r in c32} >= {("cluster", 16, 5), ("cluster", 16, 6), ("cluster", 16, 8),
+                                                          ("cluster", 8, 8), ("global", 32, 1), ("global", 64, 1)}
+    assert all(r["T"] // r["CL"] <= 256 for r in c32 if r["kernel"] == "cluster" and r["CL"] in (5, 6))
     c64 = A.chain_candidates(20471, 0)
     assert (c64[0]["kernel"], c64[0]["CL"]) == ("cluster", 8)
     # mid-grid stripes: 16 nodes per thread in registers, 320 threads
@@ -80,5 +82,5 @@ def test_rules_change_the_layout_only_where_they_fit(A):
     assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=3, M=16, CL=1)], precision=A.EMS_F64) == base
     # malformed rules are rejected
     assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=1, M=12, CL=1)]) == 0
-    assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=4, M=8, CL=3)]) == 0
+    assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=4, M=8, CL=9)]) == 0
     assert _ws(A, g, [dict(n_lo=5, n_hi=4, kind=1, M=8, CL=1)]) == 0
