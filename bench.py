@@ -305,8 +305,12 @@ def run_mine(args):
         mc = mc_leg(p, peaks, src, stream)
 
     surrogate = None
+    sched = None
     if not args.no_surrogate:
         surrogate = surrogate_leg(peaks, src, stream, rows=args.surrogate_rows)
+        # what the learned part buys: the trained surrogate's step schedule on
+        # an unseen Monte Carlo workload, against the plain solver
+        sched = schedule_leg(p, stream)
 
     line = {
         "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps,
@@ -325,7 +329,7 @@ def run_mine(args):
         "stress_ms_per_step": round(stress_ms / args.steps, 1), "ir_ms_per_step": round(ir_ms / args.steps, 1),
         "voids_after_timed_steps": voids, "max_drop_after_timed_steps": float(np.max(res["final_drop"])),
         "plain_vs_chosen": pvc, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "surrogate": surrogate, "monte_carlo": mc,
+        "clocks": clocks, "surrogate": surrogate, "surrogate_schedule": sched, "monte_carlo": mc,
         "autotune": None if args.no_tune else {
             "table": rules, "tune_s": round(tune_s, 2),
             "how": "ems_autotune on a 2-sample copy of the full chip (after one IR solve): every valid shape of "
@@ -593,6 +597,53 @@ def schedule_leg(p, stream, n_train=24, n_valid=3, test_seed=3000, N=64, S=32):
             "max_rel_err_ttf_or_final_drop": _result_error(r_plain, r_sched)}
 
 
+def cluster_stripes_case(n_samples=20, cells=2924):
+    """Small case of the cluster chain kernel for a profiler capture: 16
+    stripes of 7 x cells + 1 stress nodes (full-chip length for cells =
+    2,924), the 8 x 8 grid's pads and sinks, a 33 x 33 hotspot map, n_samples
+    factor sets; two aging steps of 256 BE steps, FP32."""
+    import numpy as np
+    import torch
+    import ems_synth as es
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300.engine import Engine
+    g = es.stripe_mesh(8, 20e-6)
+    g["seg_cells"][:] = cells
+    t = es.tiny_grid()
+    g["pad_node"], g["pad_V"], g["sink_node"], g["sink_I"] = t["pad_node"], t["pad_V"], t["sink_node"], t["sink_I"]
+    g["thermal"] = es.hotspot_raster(np.random.default_rng(4), 140e-6, 2, 360.0, 20.0, 40.0, 0.2, nx=33, ny=33)
+    g["kappa_factor"], g["sigc_factor"] = es.mc_factors(np.random.default_rng(3), n_samples, g["seg_a"].size)
+    p = es.default_params(n_outer=4, n_inner=256)
+    eng = Engine(p, g, precision=EMS_F32, max_voids=64)
+    r = eng.ttf(n_outer=2)
+    torch.cuda.synchronize()
+    out = {"stress_ms": r["stress_ms"], "voids": int(r["n_voids"].sum()),
+           "node_steps_per_s": r["node_steps"] / (r["stress_ms"] / 1e3)}
+    eng.close()
+    return out
+
+
+def ir_mg_case(N=1024, n_samples=4):
+    """Small case of the multigrid IR PCG for a profiler capture: the full
+    chip's pitch, pads, sinks and map on an N x N mesh (N^2 IR nodes; 4
+    samples are 0.5 GB of matrix and vectors, past the L2), one solve from
+    zero."""
+    import torch
+    import ems_synth as es
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300.engine import Engine
+    g = es.grid.large_grid(N=N, n_samples=n_samples)
+    eng = Engine(es.default_params(), g, precision=EMS_F32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eng.ir_solve()
+    torch.cuda.synchronize()
+    out = {"solve_ms": round((time.perf_counter() - t0) * 1e3, 2),
+           "iterations": [int(v) for v in eng.ir_iterations()]}
+    eng.close()
+    return out
+
+
 def corner_grid(n=256):
     """The n x n-crossing corner of the full chip: the same pitch, pads, sinks
     and thermal map, cut out of the 2048 x 2048 netlist (array selection
@@ -689,6 +740,11 @@ def main():
     ap.add_argument("--window", type=int, default=8, help="samples whose coefficients are held at once")
     ap.add_argument("--max-voids", type=int, default=128)
     ap.add_argument("--no-tune", action="store_true", help="built-in chain shapes instead of the autotuner's")
+    ap.add_argument("--profile-case", choices=["cluster-stripes", "ir-mg"],
+                    help="run one small case of a kernel for an ncu capture: cluster-stripes = 16 stripes of "
+                         "20,469 nodes x 20 Monte Carlo samples, two aging steps (k_chain_cl on 4-CTA clusters); "
+                         "ir-mg = two IR solves of a 1024 x 1024 mesh (1.05 M unknowns) for 4 samples "
+                         "(k_pcg_cluster_mg)")
     ap.add_argument("--mid-only", action="store_true",
                     help="time only full TTF runs of the 256 x 256 mesh; prints its own JSON line")
     args = ap.parse_args()
@@ -697,7 +753,11 @@ def main():
     else:
         import __graft_entry__ as ge
         ge.build()
-        if args.schedule_only:
+        if args.profile_case == "cluster-stripes":
+            print(json.dumps({"profile_case": cluster_stripes_case()}))
+        elif args.profile_case == "ir-mg":
+            print(json.dumps({"profile_case": ir_mg_case()}))
+        elif args.schedule_only:
             import torch
             import ems_synth as es
             print(json.dumps({"surrogate_schedule": schedule_leg(es.default_params(), torch.cuda.current_stream())}))

@@ -200,7 +200,7 @@ ems_status ems_load_grid(ems_ctx *ctx, const ems_grid_desc *grid);
  *   EMS_CHAIN_GLOBAL    one CTA per (chain, sample), chunks streamed from HBM
  *   EMS_CHAIN_SHARED    (FP32) one CTA, the chunk coefficients staged in shared memory
  *   EMS_CHAIN_REGISTER  (FP32, M <= 16) one CTA, coefficients and state in registers
- *   EMS_CHAIN_CLUSTER   a cluster of CL CTAs (2, 4 or 8) per (chain, sample), registers,
+ *   EMS_CHAIN_CLUSTER   a cluster of CL CTAs (2..8) per (chain, sample), registers,
  *                       M = 16 (FP32) or 8 (FP64); CTAs trade their carries through
  *                       distributed shared memory
  * Every shape solves the same system; results differ by rounding only.

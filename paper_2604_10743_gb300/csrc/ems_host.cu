@@ -458,6 +458,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.face_dx = cv.take<double>(N); d.face_area = cv.take<double>(N);
     d.nx_ = cv.take<double>(N); d.ny_ = cv.take<double>(N);
     d.Tn = cv.take<double>(N); d.Mface = cv.take<double>((size_t)Sd * N); d.V = cv.take<double>(N);
+    d.fb_ka = cv.take<double>(N); d.fb_g = cv.take<double>(N); d.fb_M = cv.take<double>(N);
     d.kap_a = cv.take<double>((size_t)Sd * N); d.g = cv.take<double>((size_t)Sd * N);
     d.leak = cv.take<double>((size_t)Sd * N); d.thr = cv.take<double>((size_t)Sd * N);
     d.f = cv.take<double>((size_t)Sd * N); d.sig_ss = cv.take<double>((size_t)Sd * N);
@@ -490,6 +491,7 @@ size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev
     d.pred = cv.take<float>((size_t)S * nt * EMS_MLP_OUTPUTS);
     d.mg_i = cv.take<int32_t>(pl.mg.ints.size() + 1);
     d.mg_d = cv.take<double>(pl.mg.dbls.size() + 1);
+    d.mg_f = cv.take<float>(pl.mg.dbls.size() + 1);
     d.mg_sc = cv.take<double>((size_t)Sd * pl.mg.per_sample + 1);
     d.sched = cv.take<int32_t>((size_t)S * nt);
     d.fdt = cv.take<double>((size_t)S * nt);
@@ -789,12 +791,18 @@ extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     if (pl.mg.L >= 2) {
         EMS_CUDA(c, up(D.mg_i, pl.mg.ints.data(), pl.mg.ints.size(), st));
         EMS_CUDA(c, up(D.mg_d, pl.mg.dbls.data(), pl.mg.dbls.size(), st));
+        {
+            const std::vector<float> f(pl.mg.dbls.begin(), pl.mg.dbls.end());
+            EMS_CUDA(c, up(D.mg_f, f.data(), f.size(), st));
+            EMS_CUDA(c, cudaStreamSynchronize(st));    // f is a host temporary
+        }
         c->mg.L = pl.mg.L;
         for (int l = 0; l < EMS_MG_MAXLV; ++l) c->mg.lv[l] = pl.mg.lv[l];
         c->mg.cinv = pl.mg.cinv;
         c->mg.per_sample = pl.mg.per_sample;
         c->mg.I = D.mg_i;
         c->mg.D = D.mg_d;
+        c->mg.F = D.mg_f;
         c->mg.scratch = D.mg_sc;
     }
     // initial guess: every free node at the mean pad voltage

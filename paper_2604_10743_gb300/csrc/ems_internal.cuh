@@ -52,6 +52,7 @@ struct MGDevice {
     int64_t cinv = 0, per_sample = 0;
     const int32_t *I = nullptr;
     const double *D = nullptr;
+    const float *F = nullptr;                   // D rounded to FP32 (the FP32 V-cycle of FP32 contexts)
     double *scratch = nullptr;                  // [S][per_sample]
 };
 
@@ -88,7 +89,6 @@ inline int cluster_chunk(int prec) { return prec == EMS_F32 ? 16 : 8; }
 inline int cluster_max_threads(int prec, int M, int CL) {
     if (prec == EMS_F32) {
         if (M == 16) return (CL == 2 || CL == 4 || CL == 8) ? 320 : (CL == 5 || CL == 6) ? 256 : 0;
-        if (M == 8) return (CL == 4 || CL == 8) ? 320 : 0;
         return 0;
     }
     return (M == 8 && (CL == 2 || CL == 4 || CL == 8)) ? 320 : 0;
@@ -166,6 +166,8 @@ struct Dev {
     double *face_dx, *face_area, *nx_, *ny_;
     double *Tn;                        // [N] node temperature
     double *Mface;                     // [S][N] TM term per face (per sample: temperature perturbations)
+    double *fb_ka, *fb_g, *fb_M;       // [N] per face without the sample's kappa factor: a kappa, a kappa / dx, M
+                                       // (from the node temperatures; rebuilt when they change)
     double *V;                         // [N]
     double *kap_a, *g, *leak, *thr;    // [S][N]
     double *f;                         // [S][N] forcing
@@ -208,6 +210,7 @@ struct Dev {
     float *feat, *pred;                // [S][n_trees][24], [S][n_trees][2]
     int32_t *mg_i;                     // multigrid hierarchy (ints, doubles, scratch)
     double *mg_d, *mg_sc;
+    float *mg_f;
     int32_t *sched;                    // [S][n_trees] step schedule: <= 1 fine, r > 1 r-times coarser, < 0 frozen
     double *fdt;                       // [S][n_trees] step the packed factors were built for
     unsigned long long *work;          // [1] node-steps the stress kernels executed
@@ -310,6 +313,7 @@ ems_status screen(ems_ctx *c);
 ems_status pack_sigma(ems_ctx *c, bool to_packed);
 ems_status init_sigma(ems_ctx *c);
 ems_status sample_physics(ems_ctx *c);     // kappa, conductances, leak, thresholds of the mapped samples
+ems_status face_base(ems_ctx *c);          // sample-independent face terms after the node temperatures changed
 
 // Monte Carlo windows (ems_host.cu)
 void map_window(ems_ctx *c, int s0, int ns);   // map samples [s0, s0 + ns) (ns <= W)

@@ -163,6 +163,7 @@ extern "C" ems_status ems_joule_profile(ems_ctx *c, double k_cu, double k_ild, d
     ++c->launches;
     EMS_CUDA(c, cudaGetLastError());
     c->joule = true;
+    EMS_TRY(face_base(c));
     // kappa and the thermomigration term from the new temperatures (every
     // sample of the full layout; the first window with windows, the others
     // are rebuilt before use)

@@ -294,6 +294,8 @@ struct MGArgs {
     const int32_t *ptr, *col;                   // finest level structure
     const double *val, *b, *dinv;               // [S][nnz], [S][nf], [S][nf]
     double *x, *r, *p, *q, *z;                  // [S][nf]
+    const float *val32, *dinv32;                // the finest level in FP32 (FP32 V-cycle)
+    float *r32;                                 // [S][nf] the residual rounded to FP32 (V-cycle input)
     double rtol;
     int max_iter;
     int32_t *iters, *status;
@@ -377,60 +379,75 @@ __device__ bool gsum(double (&v)[K], double *sh, double *red, unsigned int *bar,
     return true;
 }
 
-__device__ __forceinline__ double csr_dot(const int32_t *ptr, const int32_t *col, const double *val,
-                                          const double *v, int i) {
-    double acc = 0.0;
+// The V-cycle's arithmetic type P: double in FP64 contexts; float in FP32
+// ones, from an FP32 copy of the hierarchy and of the finest matrix, with the
+// CG iteration itself (matrix products, residual, dot products, the
+// convergence test) in FP64 -- the mixed-precision form: FP64 only where the
+// residual is formed.  A preconditioner rounded to FP32 is not exactly
+// linear, so the FP32 variants take the flexible (Polak-Ribiere) beta,
+// (r_new.z_new - r_new.z_old) / (r_old.z_old), which keeps CG convergent
+// with a slightly varying preconditioner.
+template <typename P> __device__ __forceinline__ const P *hier(const MGArgs &a);
+template <> __device__ __forceinline__ const double *hier<double>(const MGArgs &a) { return a.g.D; }
+template <> __device__ __forceinline__ const float *hier<float>(const MGArgs &a) { return a.g.F; }
+
+template <typename P>
+__device__ __forceinline__ P csr_dot(const int32_t *ptr, const int32_t *col, const P *val, const P *v, int i) {
+    P acc = P(0);
     for (int k = ptr[i]; k < ptr[i + 1]; ++k) acc += val[k] * v[col[k]];
     return acc;
 }
 
 // one level's operators: the finest uses the current matrix of the sample
+template <typename P>
 struct Lv {
     int n;
     const int32_t *ap, *ac;
-    const double *av, *dv;
+    const P *av, *dv;
 };
 
-__device__ __forceinline__ Lv level(const MGArgs &a, const double *val0, const double *dinv0, int l) {
+template <typename P>
+__device__ __forceinline__ Lv<P> level(const MGArgs &a, const P *val0, const P *dinv0, int l) {
     const MGLevelDesc &d = a.g.lv[l];
-    if (l == 0) return Lv{a.nf, a.ptr, a.col, val0, dinv0};
-    return Lv{d.n, a.g.I + d.a_ptr, a.g.I + d.a_col, a.g.D + d.a_val, a.g.D + d.dinv};
+    if (l == 0) return Lv<P>{a.nf, a.ptr, a.col, val0, dinv0};
+    return Lv<P>{d.n, a.g.I + d.a_ptr, a.g.I + d.a_col, hier<P>(a) + d.a_val, hier<P>(a) + d.dinv};
 }
 
-// Phase sequence of the V-cycle from level l0 (input r_l0, output out) over
-// the rows [start, n) in steps of `stride`, with `sync` between phases.
-// Level l's result lands in t_l (out for l0); the coarsest level's in e.
-// fused: the caller has already set e_l0 = w D^-1 r_l0, and each restriction
-// also sets the next level's e (the pre-smoothing needs no phase of its own).
-template <class Sync>
-__device__ bool vcycle(const MGArgs &a, const double *val0, const double *dinv0, double *sc, int l0, int l1,
-                       const double *r_l0, double *out, int start, int stride, Sync sync, bool fused = false) {
+// Phase sequence of the V-cycle from level l0 (input r_l0) over the rows
+// [start, n) in steps of `stride`, with `sync` between phases.  Level l's
+// result lands in t_l; the coarsest level's in e.  fused: the caller has
+// already set e_l0 = w D^-1 r_l0, and each restriction also sets the next
+// level's e (the pre-smoothing needs no phase of its own).
+template <typename P, class Sync>
+__device__ bool vcycle(const MGArgs &a, const P *val0, const P *dinv0, P *sc, int l0, int l1, const P *r_l0,
+                       int start, int stride, Sync sync, bool fused = false) {
     const int L = a.g.L;
-    const double *r = r_l0;
+    const P *r = r_l0;
+    const P w = P(kSmooth);
     for (int l = l0; l < l1 && l < L - 1; ++l) {
-        const Lv A = level(a, val0, dinv0, l);
+        const Lv<P> A = level<P>(a, val0, dinv0, l);
         const MGLevelDesc &d = a.g.lv[l];
-        double *e = sc + d.e, *t = sc + d.t;
+        P *e = sc + d.e, *t = sc + d.t;
         if (!fused) {
-            for (int i = start; i < A.n; i += stride) e[i] = kSmooth * A.dv[i] * r[i];
+            for (int i = start; i < A.n; i += stride) e[i] = w * A.dv[i] * r[i];
             if (!sync()) return false;
         }
-        for (int i = start; i < A.n; i += stride) t[i] = r[i] - csr_dot(A.ap, A.ac, A.av, e, i);
+        for (int i = start; i < A.n; i += stride) t[i] = r[i] - csr_dot<P>(A.ap, A.ac, A.av, e, i);
         if (!sync()) return false;
         const MGLevelDesc &dn = a.g.lv[l + 1];
-        double *rn = sc + dn.r;
+        P *rn = sc + dn.r;
         const int32_t *rp = a.g.I + d.r_ptr, *rc = a.g.I + d.r_col;
-        const double *rv = a.g.D + d.r_val;
+        const P *rv = hier<P>(a) + d.r_val;
         if (fused && l + 1 < L - 1) {
-            const double *dvn = a.g.D + dn.dinv;
-            double *en = sc + dn.e;
+            const P *dvn = hier<P>(a) + dn.dinv;
+            P *en = sc + dn.e;
             for (int i = start; i < dn.n; i += stride) {
-                const double v = csr_dot(rp, rc, rv, t, i);
+                const P v = csr_dot<P>(rp, rc, rv, t, i);
                 rn[i] = v;
-                en[i] = kSmooth * dvn[i] * v;
+                en[i] = w * dvn[i] * v;
             }
         } else {
-            for (int i = start; i < dn.n; i += stride) rn[i] = csr_dot(rp, rc, rv, t, i);
+            for (int i = start; i < dn.n; i += stride) rn[i] = csr_dot<P>(rp, rc, rv, t, i);
         }
         if (!sync()) return false;
         r = rn;
@@ -438,50 +455,59 @@ __device__ bool vcycle(const MGArgs &a, const double *val0, const double *dinv0,
     return true;
 }
 
-// acc (optional): the last phase also accumulates r.z and r.r of the rows it
-// writes into acc[0], acc[1] and leaves the closing barrier to the caller
-template <class Sync>
-__device__ bool vcycle_up(const MGArgs &a, const double *val0, const double *dinv0, double *sc, int l_hi, int l_lo,
-                          const double *r_l0, double *out, int l0, int start, int stride, Sync sync,
-                          double *acc = nullptr) {
+// Up sweep from level l_hi down to l_lo; level l0's result goes to out
+// (type O: the FP64 z at the finest level, scratch above it).  acc
+// (optional): the last phase also accumulates r.z and r.r of the rows it
+// writes into acc[0], acc[1] (r from racc, the FP64 residual) and leaves the
+// closing barrier to the caller.
+template <typename P, typename O, class Sync>
+__device__ bool vcycle_up(const MGArgs &a, const P *val0, const P *dinv0, P *sc, int l_hi, int l_lo,
+                          const P *r_l0, O *out, int l0, int start, int stride, Sync sync, double *acc = nullptr,
+                          const double *racc = nullptr) {
     const int L = a.g.L;
+    const P w = P(kSmooth);
     for (int l = l_hi; l >= l_lo; --l) {
-        const Lv A = level(a, val0, dinv0, l);
+        const Lv<P> A = level<P>(a, val0, dinv0, l);
         const MGLevelDesc &d = a.g.lv[l], &dn = a.g.lv[l + 1];
-        const double *en = (l + 1 == L - 1) ? sc + dn.e : sc + dn.t;
-        double *e = sc + d.e;
+        const P *en = (l + 1 == L - 1) ? sc + dn.e : sc + dn.t;
+        P *e = sc + d.e;
         const int32_t *pp = a.g.I + d.p_ptr, *pc = a.g.I + d.p_col;
-        const double *pv = a.g.D + d.p_val;
-        for (int i = start; i < A.n; i += stride) e[i] += csr_dot(pp, pc, pv, en, i);
+        const P *pv = hier<P>(a) + d.p_val;
+        for (int i = start; i < A.n; i += stride) e[i] += csr_dot<P>(pp, pc, pv, en, i);
         if (!sync()) return false;
-        const double *rl = l == l0 ? r_l0 : sc + d.r;
-        double *o = l == l0 ? out : sc + d.t;
-        if (acc && l == l_lo) {
-            for (int i = start; i < A.n; i += stride) {
-                const double oi = e[i] + kSmooth * A.dv[i] * (rl[i] - csr_dot(A.ap, A.ac, A.av, e, i));
-                o[i] = oi;
-                acc[0] += rl[i] * oi;
-                acc[1] += rl[i] * rl[i];
+        const P *rl = l == l0 ? r_l0 : sc + d.r;
+        if (l == l0) {
+            if (acc && l == l_lo) {
+                for (int i = start; i < A.n; i += stride) {
+                    const O oi = (O)(e[i] + w * A.dv[i] * (rl[i] - csr_dot<P>(A.ap, A.ac, A.av, e, i)));
+                    out[i] = oi;
+                    acc[0] += racc[i] * (double)oi;
+                    acc[1] += racc[i] * racc[i];
+                }
+                continue;
             }
-        } else {
             for (int i = start; i < A.n; i += stride)
-                o[i] = e[i] + kSmooth * A.dv[i] * (rl[i] - csr_dot(A.ap, A.ac, A.av, e, i));
-            if (!sync()) return false;
+                out[i] = (O)(e[i] + w * A.dv[i] * (rl[i] - csr_dot<P>(A.ap, A.ac, A.av, e, i)));
+        } else {
+            P *o = sc + d.t;
+            for (int i = start; i < A.n; i += stride)
+                o[i] = e[i] + w * A.dv[i] * (rl[i] - csr_dot<P>(A.ap, A.ac, A.av, e, i));
         }
+        if (!sync()) return false;
     }
     return true;
 }
 
 // coarsest level: e_c = C^-1 r_c
-template <class Sync>
-__device__ bool coarse(const MGArgs &a, double *sc, int start, int stride, Sync sync) {
+template <typename P, class Sync>
+__device__ bool coarse(const MGArgs &a, P *sc, int start, int stride, Sync sync) {
     const int L = a.g.L;
     const MGLevelDesc &d = a.g.lv[L - 1];
     const int n = d.n;
-    const double *ci = a.g.D + a.g.cinv, *r = sc + d.r;
-    double *e = sc + d.e;
+    const P *ci = hier<P>(a) + a.g.cinv, *r = sc + d.r;
+    P *e = sc + d.e;
     for (int i = start; i < n; i += stride) {
-        double acc = 0.0;
+        P acc = P(0);
         for (int j = 0; j < n; ++j) acc += ci[(size_t)i * n + j] * r[j];
         e[i] = acc;
     }
@@ -489,27 +515,48 @@ __device__ bool coarse(const MGArgs &a, double *sc, int start, int stride, Sync 
 }
 
 // whole V-cycle in one CTA: z = M^-1 r
-__device__ void vcycle_block(const MGArgs &a, const double *val0, const double *dinv0, double *sc, const double *r,
-                             double *z) {
+template <typename P>
+__device__ void vcycle_block(const MGArgs &a, const P *val0, const P *dinv0, P *sc, const P *r, double *z) {
     auto bs = []() { __syncthreads(); return true; };
     const int L = a.g.L;
-    vcycle(a, val0, dinv0, sc, 0, L - 1, r, z, threadIdx.x, blockDim.x, bs);
-    coarse(a, sc, threadIdx.x, blockDim.x, bs);
-    vcycle_up(a, val0, dinv0, sc, L - 2, 0, r, z, 0, threadIdx.x, blockDim.x, bs);
+    vcycle<P>(a, val0, dinv0, sc, 0, L - 1, r, threadIdx.x, blockDim.x, bs);
+    coarse<P>(a, sc, threadIdx.x, blockDim.x, bs);
+    vcycle_up<P>(a, val0, dinv0, sc, L - 2, 0, r, z, 0, threadIdx.x, blockDim.x, bs);
 }
 
+// the sample's finest-level operators and V-cycle input in the type P
+template <typename P> struct Fine;
+template <> struct Fine<double> {
+    const double *val, *dinv;
+    double *rin;
+    __device__ Fine(const MGArgs &a, int s)
+        : val(a.val + (size_t)s * a.nnz), dinv(a.dinv + (size_t)s * a.nf), rin(a.r + (size_t)s * a.nf) {}
+    __device__ void set(int, double) const {}            // the input is r itself
+};
+template <> struct Fine<float> {
+    const float *val, *dinv;
+    float *rin;
+    __device__ Fine(const MGArgs &a, int s)
+        : val(a.val32 + (size_t)s * a.nnz), dinv(a.dinv32 + (size_t)s * a.nf), rin(a.r32 + (size_t)s * a.nf) {}
+    __device__ void set(int i, double ri) const { rin[i] = (float)ri; }
+};
+template <typename P> constexpr bool kFlexible = sizeof(P) == 4;
+
 // Mode A with the multigrid preconditioner: one CTA per sample
+template <typename P>
 __global__ void __launch_bounds__(1024) k_pcg_block_mg(MGArgs a) {
     __shared__ double sh[96];
     const int s = blockIdx.x, nf = a.nf;
-    const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf, *dinv = a.dinv + (size_t)s * nf;
+    const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf;
     double *x = a.x + (size_t)s * nf, *r = a.r + (size_t)s * nf, *p = a.p + (size_t)s * nf;
     double *q = a.q + (size_t)s * nf, *z = a.z + (size_t)s * nf;
-    double *sc = a.g.scratch + (size_t)s * a.g.per_sample;
+    P *sc = reinterpret_cast<P *>(a.g.scratch + (size_t)s * a.g.per_sample);
+    const Fine<P> fn(a, s);
     double v2[2] = {0.0, 0.0};
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-        const double ri = b[i] - csr_dot(a.ptr, a.col, val, x, i);
+        const double ri = b[i] - csr_dot<double>(a.ptr, a.col, val, x, i);
         r[i] = ri;
+        fn.set(i, ri);
         v2[0] += ri * ri;
         v2[1] += b[i] * b[i];
     }
@@ -519,7 +566,7 @@ __global__ void __launch_bounds__(1024) k_pcg_block_mg(MGArgs a) {
     int it = 0;
     double rz = 0.0;
     if (rr > tol2) {
-        vcycle_block(a, val, dinv, sc, r, z);
+        vcycle_block<P>(a, fn.val, fn.dinv, sc, fn.rin, z);
         double v1[1] = {0.0};
         for (int i = threadIdx.x; i < nf; i += blockDim.x) { p[i] = z[i]; v1[0] += r[i] * z[i]; }
         bsum<1>(v1, sh);
@@ -529,22 +576,26 @@ __global__ void __launch_bounds__(1024) k_pcg_block_mg(MGArgs a) {
         __syncthreads();
         double v1[1] = {0.0};
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const double qi = csr_dot(a.ptr, a.col, val, p, i);
+            const double qi = csr_dot<double>(a.ptr, a.col, val, p, i);
             q[i] = qi;
             v1[0] += p[i] * qi;
         }
         bsum<1>(v1, sh);
         const double alpha = rz / v1[0];
+        double rzo = 0.0;                              // r_new . z_old (flexible beta)
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
             x[i] += alpha * p[i];
             r[i] -= alpha * q[i];
+            fn.set(i, r[i]);
+            if (kFlexible<P>) rzo += r[i] * z[i];
         }
         __syncthreads();
-        vcycle_block(a, val, dinv, sc, r, z);
-        double w2[2] = {0.0, 0.0};
+        vcycle_block<P>(a, fn.val, fn.dinv, sc, fn.rin, z);
+        double w2[3] = {0.0, 0.0, rzo};
         for (int i = threadIdx.x; i < nf; i += blockDim.x) { w2[0] += r[i] * z[i]; w2[1] += r[i] * r[i]; }
-        bsum<2>(w2, sh);
-        const double beta = w2[0] / rz;
+        if (kFlexible<P>) bsum<3>(w2, sh);
+        else bsum<2>(reinterpret_cast<double (&)[2]>(w2), sh);
+        const double beta = (kFlexible<P> ? w2[0] - w2[2] : w2[0]) / rz;
         rz = w2[0];
         rr = w2[1];
         for (int i = threadIdx.x; i < nf; i += blockDim.x) p[i] = z[i] + beta * p[i];
@@ -559,47 +610,51 @@ __global__ void __launch_bounds__(1024) k_pcg_block_mg(MGArgs a) {
 // grid-wide V-cycle: large levels across the grid, small ones in block 0.
 // The caller has set e_0 = w D^-1 r (fused pre-smoothing); with acc the last
 // phase accumulates (r.z, r.r) and the caller's reduction closes it.
-__device__ bool vcycle_grid(const MGArgs &a, const double *val0, const double *dinv0, double *sc, const double *r,
-                            double *z, double *acc) {
+template <typename P>
+__device__ bool vcycle_grid(const MGArgs &a, const P *val0, const P *dinv0, P *sc, const P *r, double *z,
+                            double *acc, const double *racc) {
     const int L = a.g.L;
     int lb = 0;                       // first level small enough for one CTA
     while (lb < L - 1 && a.g.lv[lb].n > a.g.small) ++lb;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     auto gsy = [&]() { return gsync(a.bar, a.status); };
     auto bs = []() { __syncthreads(); return true; };
-    if (!vcycle(a, val0, dinv0, sc, 0, lb, r, z, gid, gs, gsy, true)) return false;
+    if (!vcycle<P>(a, val0, dinv0, sc, 0, lb, r, gid, gs, gsy, true)) return false;
     if (blockIdx.x == 0) {
         // levels lb..L-1 in this CTA; level lb's input sits in its r slot
         // (lb > 0 always: the finest level is above the small threshold)
-        const double *rl = sc + a.g.lv[lb].r;
-        double *ol = sc + a.g.lv[lb].t;
-        vcycle(a, val0, dinv0, sc, lb, L - 1, rl, ol, threadIdx.x, blockDim.x, bs, true);
-        coarse(a, sc, threadIdx.x, blockDim.x, bs);
-        if (lb <= L - 2) vcycle_up(a, val0, dinv0, sc, L - 2, lb, rl, ol, lb, threadIdx.x, blockDim.x, bs);
+        const P *rl = sc + a.g.lv[lb].r;
+        P *ol = sc + a.g.lv[lb].t;
+        vcycle<P>(a, val0, dinv0, sc, lb, L - 1, rl, threadIdx.x, blockDim.x, bs, true);
+        coarse<P>(a, sc, threadIdx.x, blockDim.x, bs);
+        if (lb <= L - 2) vcycle_up<P>(a, val0, dinv0, sc, L - 2, lb, rl, ol, lb, threadIdx.x, blockDim.x, bs);
         __threadfence();
     }
     if (!gsy()) return false;
-    return vcycle_up(a, val0, dinv0, sc, lb - 1, 0, r, z, 0, gid, gs, gsy, acc);
+    return vcycle_up<P>(a, val0, dinv0, sc, lb - 1, 0, r, z, 0, gid, gs, gsy, acc, racc);
 }
 
 // Mode B with the multigrid preconditioner: cooperative grid, samples in turn
+template <typename P>
 __global__ void __launch_bounds__(512, 2) k_pcg_grid_mg(MGArgs a) {
     __shared__ double sh[96];
     const int nf = a.nf, G = gridDim.x;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x, gs = G * blockDim.x;
     double *redA = a.red, *redB = a.red + 3 * G;
+    const P w = P(kSmooth);
     for (int s = 0; s < a.S; ++s) {
         const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf;
-        const double *dinv = a.dinv + (size_t)s * nf;
         double *x = a.x + (size_t)s * nf, *r = a.r + (size_t)s * nf, *p = a.p + (size_t)s * nf;
         double *q = a.q + (size_t)s * nf, *z = a.z + (size_t)s * nf;
-        double *sc = a.g.scratch + (size_t)s * a.g.per_sample;
-        double *e0 = sc + a.g.lv[0].e;             // pre-smoothing of the V-cycle, fused below
+        P *sc = reinterpret_cast<P *>(a.g.scratch + (size_t)s * a.g.per_sample);
+        const Fine<P> fn(a, s);
+        P *e0 = sc + a.g.lv[0].e;                  // pre-smoothing of the V-cycle, fused below
         double v2[2] = {0.0, 0.0};
         for (int i = gid; i < nf; i += gs) {
-            const double ri = b[i] - csr_dot(a.ptr, a.col, val, x, i);
+            const double ri = b[i] - csr_dot<double>(a.ptr, a.col, val, x, i);
             r[i] = ri;
-            e0[i] = kSmooth * dinv[i] * ri;
+            fn.set(i, ri);
+            e0[i] = w * fn.dinv[i] * (P)ri;
             v2[0] += ri * ri;
             v2[1] += b[i] * b[i];
         }
@@ -609,7 +664,7 @@ __global__ void __launch_bounds__(512, 2) k_pcg_grid_mg(MGArgs a) {
         int it = 0;
         double rz = 0.0;
         if (rr > tol2) {
-            if (!vcycle_grid(a, val, dinv, sc, r, z, nullptr)) return;
+            if (!vcycle_grid<P>(a, fn.val, fn.dinv, sc, fn.rin, z, nullptr, r)) return;
             double v1[1] = {0.0};
             for (int i = gid; i < nf; i += gs) { p[i] = z[i]; v1[0] += r[i] * z[i]; }
             if (!gsum<1>(v1, sh, redB, a.bar, a.status)) return;
@@ -618,23 +673,30 @@ __global__ void __launch_bounds__(512, 2) k_pcg_grid_mg(MGArgs a) {
         while (rr > tol2 && it < a.max_iter) {
             double v1[1] = {0.0};
             for (int i = gid; i < nf; i += gs) {
-                const double qi = csr_dot(a.ptr, a.col, val, p, i);
+                const double qi = csr_dot<double>(a.ptr, a.col, val, p, i);
                 q[i] = qi;
                 v1[0] += p[i] * qi;
             }
             if (!gsum<1>(v1, sh, redA, a.bar, a.status)) return;
             const double alpha = rz / v1[0];
+            double rzo = 0.0;                          // r_new . z_old (flexible beta)
             for (int i = gid; i < nf; i += gs) {
                 x[i] += alpha * p[i];
                 const double ri = r[i] - alpha * q[i];
                 r[i] = ri;
-                e0[i] = kSmooth * dinv[i] * ri;
+                fn.set(i, ri);
+                e0[i] = w * fn.dinv[i] * (P)ri;
+                if (kFlexible<P>) rzo += ri * z[i];
             }
             if (!gsync(a.bar, a.status)) return;          // r, e0 complete
-            double w2[2] = {0.0, 0.0};
-            if (!vcycle_grid(a, val, dinv, sc, r, z, w2)) return;
-            if (!gsum<2>(w2, sh, redB, a.bar, a.status)) return;
-            const double beta = w2[0] / rz;
+            double w2[3] = {0.0, 0.0, rzo};
+            if (!vcycle_grid<P>(a, fn.val, fn.dinv, sc, fn.rin, z, w2, r)) return;
+            if (kFlexible<P>) {
+                if (!gsum<3>(w2, sh, redB, a.bar, a.status)) return;
+            } else {
+                if (!gsum<2>(reinterpret_cast<double (&)[2]>(w2), sh, redB, a.bar, a.status)) return;
+            }
+            const double beta = (kFlexible<P> ? w2[0] - w2[2] : w2[0]) / rz;
             rz = w2[0];
             rr = w2[1];
             for (int i = gid; i < nf; i += gs) p[i] = z[i] + beta * p[i];
@@ -671,6 +733,7 @@ __device__ void csum(double (&v)[K], double *sh, double *slot, cg::cluster_group
     }
 }
 
+template <typename P>
 __global__ void __launch_bounds__(1024) k_pcg_cluster_mg(MGArgs a) {
     __shared__ double sh[96];
     __shared__ double slots[2][4];                 // alternate so a slot is not rewritten while read
@@ -678,22 +741,24 @@ __global__ void __launch_bounds__(1024) k_pcg_cluster_mg(MGArgs a) {
     const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int s = blockIdx.x / CL, nf = a.nf;
     const int gid = rank * blockDim.x + threadIdx.x, gs = CL * blockDim.x;
-    const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf, *dinv = a.dinv + (size_t)s * nf;
+    const double *val = a.val + (size_t)s * a.nnz, *b = a.b + (size_t)s * nf;
     double *x = a.x + (size_t)s * nf, *r = a.r + (size_t)s * nf, *p = a.p + (size_t)s * nf;
     double *q = a.q + (size_t)s * nf, *z = a.z + (size_t)s * nf;
-    double *sc = a.g.scratch + (size_t)s * a.g.per_sample;
+    P *sc = reinterpret_cast<P *>(a.g.scratch + (size_t)s * a.g.per_sample);
+    const Fine<P> fn(a, s);
     auto csy = [&]() { cl.sync(); return true; };
     const int L = a.g.L;
     auto vcyc = [&]() {
-        vcycle(a, val, dinv, sc, 0, L - 1, r, z, gid, gs, csy);
-        coarse(a, sc, gid, gs, csy);
-        vcycle_up(a, val, dinv, sc, L - 2, 0, r, z, 0, gid, gs, csy);
+        vcycle<P>(a, fn.val, fn.dinv, sc, 0, L - 1, fn.rin, gid, gs, csy);
+        coarse<P>(a, sc, gid, gs, csy);
+        vcycle_up<P>(a, fn.val, fn.dinv, sc, L - 2, 0, fn.rin, z, 0, gid, gs, csy);
     };
     int par = 0;
     double v2[2] = {0.0, 0.0};
     for (int i = gid; i < nf; i += gs) {
-        const double ri = b[i] - csr_dot(a.ptr, a.col, val, x, i);
+        const double ri = b[i] - csr_dot<double>(a.ptr, a.col, val, x, i);
         r[i] = ri;
+        fn.set(i, ri);
         v2[0] += ri * ri;
         v2[1] += b[i] * b[i];
     }
@@ -713,22 +778,27 @@ __global__ void __launch_bounds__(1024) k_pcg_cluster_mg(MGArgs a) {
     while (rr > tol2 && it < a.max_iter) {
         double v1[1] = {0.0};
         for (int i = gid; i < nf; i += gs) {
-            const double qi = csr_dot(a.ptr, a.col, val, p, i);
+            const double qi = csr_dot<double>(a.ptr, a.col, val, p, i);
             q[i] = qi;
             v1[0] += p[i] * qi;
         }
         csum<1>(v1, sh, slots[par], cl); par ^= 1;
         const double alpha = rz / v1[0];
+        double rzo = 0.0;                              // r_new . z_old (flexible beta)
         for (int i = gid; i < nf; i += gs) {
             x[i] += alpha * p[i];
             r[i] -= alpha * q[i];
+            fn.set(i, r[i]);
+            if (kFlexible<P>) rzo += r[i] * z[i];
         }
         cl.sync();                                     // r complete
         vcyc();
-        double w2[2] = {0.0, 0.0};
+        double w2[3] = {0.0, 0.0, rzo};
         for (int i = gid; i < nf; i += gs) { w2[0] += r[i] * z[i]; w2[1] += r[i] * r[i]; }
-        csum<2>(w2, sh, slots[par], cl); par ^= 1;
-        const double beta = w2[0] / rz;
+        if (kFlexible<P>) csum<3>(w2, sh, slots[par], cl);
+        else csum<2>(reinterpret_cast<double (&)[2]>(w2), sh, slots[par], cl);
+        par ^= 1;
+        const double beta = (kFlexible<P> ? w2[0] - w2[2] : w2[0]) / rz;
         rz = w2[0];
         rr = w2[1];
         for (int i = gid; i < nf; i += gs) p[i] = z[i] + beta * p[i];
@@ -744,21 +814,23 @@ __global__ void __launch_bounds__(1024) k_pcg_cluster_mg(MGArgs a) {
 
 }  // namespace
 
-// PCG with the multigrid preconditioner (the hierarchy must exist)
-ems_status mg_solve(ems_ctx *c) {
+// PCG with the multigrid preconditioner (the hierarchy must exist); the
+// V-cycle in the context's stress precision
+template <typename P>
+ems_status mg_solve_t(ems_ctx *c) {
     Dev &d = c->d;
     cudaStream_t st = c->stream;
     MGArgs a;
     a.nf = c->nf; a.S = c->S; a.nnz = c->nnz;
     a.ptr = d.csr_ptr; a.col = d.csr_col; a.val = d.csr_val; a.b = d.ir_b; a.dinv = d.ir_dinv;
     a.x = d.ir_x; a.r = d.ir_r; a.p = d.ir_p; a.q = d.ir_Ap; a.z = d.ir_z;
+    a.val32 = d.val32; a.dinv32 = d.dinv32; a.r32 = d.r32;
     a.rtol = c->prm.ir_rtol; a.max_iter = c->prm.ir_max_iter;
     a.iters = d.ir_iters; a.status = d.status; a.red = d.red; a.bar = d.gbar;
     a.g = c->mg;
-    if (const char *e = getenv("EMS_MG_SMALL")) a.g.small = std::max(0, atoi(e));   // tuning override
     if (c->nf <= 4096) {
         const int threads = c->nf >= 1024 ? 1024 : ((c->nf + 31) / 32) * 32;
-        k_pcg_block_mg<<<c->S, threads, 0, st>>>(a);
+        k_pcg_block_mg<P><<<c->S, threads, 0, st>>>(a);
         ++c->launches;
         EMS_CUDA(c, cudaGetLastError());
         return EMS_OK;
@@ -766,7 +838,8 @@ ems_status mg_solve(ems_ctx *c) {
     // one cluster per sample when the device can hold one of 16 (or 8) CTAs
     if (c->mg_cluster == 0) {
         c->mg_cluster = -1;
-        if (cudaFuncSetAttribute(k_pcg_cluster_mg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_pcg_cluster_mg<P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
             cudaGetLastError();
         for (int cs : {16, 8}) {
             cudaLaunchConfig_t cfg = {};
@@ -775,7 +848,7 @@ ems_status mg_solve(ems_ctx *c) {
             at[0].val.clusterDim.x = cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3(cs); cfg.blockDim = dim3(1024); cfg.attrs = at; cfg.numAttrs = 1;
             int nclus = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclus, k_pcg_cluster_mg, &cfg) == cudaSuccess && nclus > 0) {
+            if (cudaOccupancyMaxActiveClusters(&nclus, k_pcg_cluster_mg<P>, &cfg) == cudaSuccess && nclus > 0) {
                 c->mg_cluster = cs;
                 break;
             }
@@ -789,7 +862,7 @@ ems_status mg_solve(ems_ctx *c) {
         at[0].val.clusterDim.x = c->mg_cluster; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(c->mg_cluster * c->S); cfg.blockDim = dim3(1024); cfg.stream = st;
         cfg.attrs = at; cfg.numAttrs = 1;
-        EMS_CUDA(c, cudaLaunchKernelEx(&cfg, k_pcg_cluster_mg, a));
+        EMS_CUDA(c, cudaLaunchKernelEx(&cfg, k_pcg_cluster_mg<P>, a));
         ++c->launches;
         return EMS_OK;
     }
@@ -797,7 +870,7 @@ ems_status mg_solve(ems_ctx *c) {
         int dev = 0, nsm = 0, per = 0;
         EMS_CUDA(c, cudaGetDevice(&dev));
         EMS_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        EMS_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_grid_mg, 512, 0));
+        EMS_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_grid_mg<P>, 512, 0));
         if (per < 1) return fail(c, EMS_E_CUDA, "cooperative multigrid PCG cannot be resident");
         const int need = (c->nf + 511) / 512;
         int G = nsm * (per < 2 ? per : 2);
@@ -807,9 +880,13 @@ ems_status mg_solve(ems_ctx *c) {
     }
     EMS_CUDA(c, cudaMemsetAsync(d.gbar, 0, 2 * sizeof(unsigned int), st));
     void *args[] = {&a};
-    EMS_CUDA(c, cudaLaunchCooperativeKernel((void *)k_pcg_grid_mg, dim3(c->mg_blocks), dim3(512), args, 0, st));
+    EMS_CUDA(c, cudaLaunchCooperativeKernel((void *)k_pcg_grid_mg<P>, dim3(c->mg_blocks), dim3(512), args, 0, st));
     ++c->launches;
     return EMS_OK;
+}
+
+ems_status mg_solve(ems_ctx *c) {
+    return c->prm.precision == EMS_F32 ? mg_solve_t<float>(c) : mg_solve_t<double>(c);
 }
 
 }  // namespace ems

@@ -67,6 +67,7 @@ struct PhysArgs {
     double px0, py0, px1, py1;
     double D0, Ea, kB, B, Omega, Qs, delta, sigma_crit;
     double *kap_a, *g, *Mface, *V, *leak, *thr0, *thr;
+    double *fb_ka, *fb_g, *fb_M;       // face terms without the sample factor (no perturbation)
 };
 
 // a sample's temperature perturbation at (x, y): bilinear over its raster,
@@ -82,8 +83,29 @@ __device__ double pert_at(const PhysArgs &a, const double *r, double x, double y
     return (1 - tx) * (1 - ty) * r0[ix] + tx * (1 - ty) * r0[ix + 1] + (1 - tx) * ty * r1[ix] + tx * ty * r1[ix + 1];
 }
 
+// per face, from the node temperatures alone (Arrhenius kappa without the
+// sample's factor, Eq. kappa; TM term): once per temperature change
+__global__ void k_face_base(PhysArgs a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = a.gpar[i];
+        if (q < 0) {
+            a.fb_ka[i] = 0.0; a.fb_g[i] = 0.0; a.fb_M[i] = 0.0;
+            continue;
+        }
+        const double Ti = a.Tn[i], Tq = a.Tn[q];
+        const double Te = 0.5 * (Ti + Tq);
+        const double ikT = 1.0 / (a.kB * Te);
+        const double ka = a.area[i] * (a.D0 * exp(-a.Ea * ikT) * a.B * a.Omega * ikT);
+        a.fb_ka[i] = ka;
+        a.fb_g[i] = ka / a.dx[i];
+        a.fb_M[i] = a.Qs / (a.Omega * Te) * (Ti - Tq) / a.dx[i];
+    }
+}
+
 // per face (stored at the child node): a kappa, g = a kappa / dx, TM term M
-// (per sample: a sample's perturbation raster adds to the node temperatures)
+// of each mapped sample: the temperature-only terms times the sample's kappa
+// factor, or (a sample's perturbation raster adds to the node temperatures)
+// evaluated per sample
 __global__ void k_faces(PhysArgs a) {
     const int s = blockIdx.y;
     const double *pr = a.pert + (int64_t)s * EMS_MAX_PERT;
@@ -93,6 +115,13 @@ __global__ void k_faces(PhysArgs a) {
         if (q < 0) {
             a.kap_a[si] = 0.0; a.g[si] = 0.0;
             a.Mface[si] = 0.0;
+            continue;
+        }
+        if (a.pnx == 0) {
+            const double kf = a.kfac[(int64_t)s * a.n_seg + a.face_seg[i]];
+            a.kap_a[si] = a.fb_ka[i] * kf;
+            a.g[si] = a.fb_g[i] * kf;
+            a.Mface[si] = a.fb_M[i];
             continue;
         }
         double Ti = a.Tn[i], Tq = a.Tn[q];
@@ -1174,6 +1203,7 @@ cudaError_t launch_bucket_raw(ems_ctx *c, const Bucket &b, ChainArgs<R> a, int S
             if (b.CL < 2 || b.T % b.CL) return cudaErrorInvalidValue;
             e = launch_cluster(b.M, b.CL, b.T / b.CL, (unsigned)b.trees.size(), S, c->stream, a);
             break;
+
         case EMS_CHAIN_REGISTER:
             if constexpr (kDelta) {
                 if (b.T > reg_max_threads(b.M)) return cudaErrorInvalidValue;
@@ -1431,16 +1461,14 @@ ems_status node_physics(ems_ctx *c) {
         ++c->launches;
         EMS_CUDA(c, cudaGetLastError());
     }
+    EMS_TRY(face_base(c));
     return sample_physics(c);
 }
 
-// kappa a, conductances, TM term, volumes, leak and thresholds of the mapped
-// samples from the node temperatures and the per-segment factors; voids
-// raise their node's threshold to +inf and mark the tree for a refactor
-ems_status sample_physics(ems_ctx *c) {
+namespace {
+PhysArgs phys_args(ems_ctx *c) {
     Dev &d = c->d;
     const ems_params &p = c->prm;
-    cudaStream_t st = c->stream;
     PhysArgs a;
     a.N = c->N; a.n_seg = c->n_seg; a.gpar = d.par; a.face_seg = d.face_seg; a.owner_seg = d.owner_seg;
     a.child_ptr = d.child_ptr; a.child_gidx = d.child_idx; a.Tn = d.Tn; a.dx = d.face_dx; a.area = d.face_area;
@@ -1449,6 +1477,25 @@ ems_status sample_physics(ems_ctx *c) {
     a.px0 = c->rx0; a.py0 = c->ry0; a.px1 = c->rx1; a.py1 = c->ry1; a.Ea = p.Ea; a.kB = p.k_B; a.B = p.B_modulus;
     a.Omega = p.Omega; a.Qs = p.Q_star; a.delta = p.delta; a.sigma_crit = p.sigma_crit;
     a.kap_a = d.kap_a; a.g = d.g; a.Mface = d.Mface; a.V = d.V; a.leak = d.leak; a.thr0 = d.thr0; a.thr = d.thr;
+    a.fb_ka = d.fb_ka; a.fb_g = d.fb_g; a.fb_M = d.fb_M;
+    return a;
+}
+}  // namespace
+
+ems_status face_base(ems_ctx *c) {
+    k_face_base<<<grid_1d(c->N, 1), 256, 0, c->stream>>>(phys_args(c));
+    ++c->launches;
+    EMS_CUDA(c, cudaGetLastError());
+    return EMS_OK;
+}
+
+// kappa a, conductances, TM term, volumes, leak and thresholds of the mapped
+// samples from the node temperatures and the per-segment factors; voids
+// raise their node's threshold to +inf and mark the tree for a refactor
+ems_status sample_physics(ems_ctx *c) {
+    Dev &d = c->d;
+    cudaStream_t st = c->stream;
+    const PhysArgs a = phys_args(c);
     k_faces<<<grid_1d(c->N, c->S), 256, 0, st>>>(a);
     ++c->launches;
     EMS_CUDA(c, cudaGetLastError());

@@ -133,3 +133,4 @@ def test_tuned_engine_cache_and_parity(tmp_path):
     metric = "ttf" if math.isfinite(ref["ttf"]) else "final_drop"
     assert abs(r[metric][0] - ref[metric]) <= 1e-6 * ref[metric]
     e1.close(); e2.close()
+

@@ -110,6 +110,29 @@ def test_ir_solve_several_samples_large_grid():
     eng.close()
 
 
+def test_ir_solve_fp32_preconditioner():
+    """FP32 contexts precondition with an FP32 V-cycle inside FP64 CG
+    (flexible beta): the same 1e-11 V bar against the oracle's direct solve,
+    on every multigrid mode (one CTA, the cooperative grid, one cluster per
+    sample), and no more than a few extra iterations over the FP64 V-cycle."""
+    from paper_2604_10743_gb300 import EMS_F32
+    cases = [(es.mid_grid(N=64, with_map=False), 1), (es.mid_grid(with_map=False), 1),
+             (es.grid.surrogate_grid(seed=7, N=96, n_samples=3), 3)]
+    for g, S in cases:
+        p = es.default_params()
+        e32 = _engine(p, g, precision=EMS_F32)
+        e64 = _engine(p, g)
+        u, d = e32.ir_solve()
+        e64.ir_solve()
+        uo = F.ir_solve(g, g["seg_R0"])
+        for s in range(S):
+            assert np.abs(u[s] - uo).max() < 1e-11
+            assert abs(d[s] - F.max_drop(uo, 1.0)) < 1e-11
+        it32, it64 = e32.ir_iterations(), e64.ir_iterations()
+        assert np.all(it32 <= it64 + 3), (it32, it64)
+        e32.close(); e64.close()
+
+
 def test_tiny_full_ttf_fp64():
     g = es.tiny_grid()
     p = es.default_params()
