@@ -245,12 +245,17 @@ def run_mine(args):
     peaks, src = _peaks()
     achieved = alg_bytes_launch / (per_launch_ms / 1e3) / 1e9
     traffic = None
+    issue = None
     tf = os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")
     if os.path.exists(tf):
         try:
             t = json.load(open(tf))
             if t.get("precision") == args.precision and t.get("kernel") == kname:
                 traffic = t.get("bytes_per_launch")
+                if t.get("issue_active_pct") is not None:
+                    issue = {"issue_active_frac": t["issue_active_pct"] / 100.0,
+                             "fma_pipe_active_frac": t["fma_pipe_active_pct"] / 100.0,
+                             "source": "ncu, " + t.get("command", "")}
         except (OSError, ValueError):
             pass
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -258,7 +263,8 @@ def run_mine(args):
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % src if src == "measured" else "fallback 6.8 TB/s",
             "kernel": "%s (stress advance, the autotuner's shape for the 20,471-node stripes; one launch = "
                       "256 BE steps of every stripe of %d samples)" % (kname, S // n_win),
-            "alg_bytes_per_launch": int(alg_bytes_launch), "launch_ms": round(per_launch_ms, 3)}
+            "alg_bytes_per_launch": int(alg_bytes_launch), "launch_ms": round(per_launch_ms, 3),
+            "issue_roof": issue}
 
     # end to end through the public API with host buffers: the netlist, the
     # map and the factor sets copied in, then aging steps with every step's
@@ -342,7 +348,49 @@ def run_mine(args):
         dist.destroy_process_group()
 
 
-def plain_vs_chosen(p, args, stream, rules, n_samples=1):
+def chosen_scheduled(p, args, stream, rules, g, seeds=(6, 7)):
+    """The chosen path plus the learned step schedule on the full chip: the
+    surrogate trained on the plain solver's records of the full chip at
+    another seed (one Monte Carlo sample: 4,096 (tree, sample) records), its
+    skip bound validated end to end on a third seed, then the benchmark
+    grid's TTF run with the schedule (CUDA events), with executed node-steps."""
+    import torch
+    from paper_2604_10743_gb300 import EMS_F32
+    from paper_2604_10743_gb300 import surrogate as sg
+    from paper_2604_10743_gb300.engine import Engine
+    t0 = time.perf_counter()
+    x, t = sg.generate_records(full_chip(1, seed=seeds[0]), p)
+    m = sg.Mlp(n_hidden=4, seed=0)
+    m.fit_norm(x, t)
+    losses = m.train(x, t, batch=1024, epochs=60, lr=1e-3, seed=1)
+    bound, log = sg.validate_bound(m, [full_chip(1, seed=seeds[1])], p, coarsen=16, guard=0.8,
+                                   candidates=(-0.3, 0.0, 0.3, 0.6), max_voids=args.max_voids)
+    t_prep = time.perf_counter() - t0
+    res = {"train_seed": seeds[0], "validation_seed": seeds[1], "records": int(x.shape[0]),
+           "final_loss_ratio": float(losses[-1] / losses[0]), "bound": bound, "validation": log,
+           "prep_s": round(t_prep, 1)}
+    if not math.isfinite(bound):
+        res["note"] = "no candidate bound passed validation: the schedule is not used"
+        return res
+    eng = Engine(p, g, precision=EMS_F32, max_voids=args.max_voids, chain_rules=rules)
+    eng.ir_solve()
+    n_coarse, _ = eng.schedule(m, bound, 16, 0.8)
+    a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    r = eng.ttf()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    tm = a0.elapsed_time(a1)
+    res.update({"ttf_s": [float(v) for v in r["ttf"]], "final_drop": [float(v) for v in r["final_drop"]],
+                "ttf_wall_ms": round(tm, 1), "stress_ms": round(r["stress_ms"], 1), "ir_ms": round(r["ir_ms"], 1),
+                "coarse_trees": [int(v) for v in (n_coarse.cpu() if hasattr(n_coarse, "cpu") else n_coarse)],
+                "node_steps_executed_ratio": r["node_steps_executed"] / r["node_steps"]})
+    eng.close()
+    return res
+
+
+def plain_vs_chosen(p, args, stream, rules, n_samples=1, sched=True):
     """Full-chip TTF of the same sample(s), plain FP64 method (built-in
     shapes) against the chosen FP32 path (the autotuner's shapes): wall time
     (CUDA events), TTF, final IR drop, errors."""
@@ -368,16 +416,24 @@ def plain_vs_chosen(p, args, stream, rules, n_samples=1):
                      "precision": "f32" if prec == EMS_F32 else "f64"}
         eng.close()
     rc, rp = out["chosen"], out["plain"]
-    err = 0.0
-    for a, b in zip(rc["final_drop"], rp["final_drop"]):
-        err = max(err, abs(a - b) / b)
-    for a, b in zip(rc["ttf_s"], rp["ttf_s"]):
-        if math.isfinite(b):
-            err = max(err, abs(a - b) / b if math.isfinite(a) else math.inf)
-        elif math.isfinite(a):
-            err = math.inf
-    out["max_rel_err_ttf_and_final_drop"] = err
+
+    def rel_err(rc, rp):
+        err = 0.0
+        for a, b in zip(rc["final_drop"], rp["final_drop"]):
+            err = max(err, abs(a - b) / b)
+        for a, b in zip(rc["ttf_s"], rp["ttf_s"]):
+            if math.isfinite(b):
+                err = max(err, abs(a - b) / b if math.isfinite(a) else math.inf)
+            elif math.isfinite(a):
+                err = math.inf
+        return err
+    out["max_rel_err_ttf_and_final_drop"] = rel_err(rc, rp)
     out["speedup"] = round(rp["ttf_wall_ms"] / rc["ttf_wall_ms"], 3)
+    if sched:
+        out["chosen_scheduled"] = chosen_scheduled(p, args, stream, rules, g)
+        rs = out["chosen_scheduled"]
+        rs["max_rel_err_ttf_and_final_drop"] = rel_err(rs, rp)
+        rs["speedup_vs_plain"] = round(rp["ttf_wall_ms"] / rs["ttf_wall_ms"], 3)
     out["samples"] = n_samples
     out["workload"] = "2048x2048 full chip, %d Monte Carlo sample(s), whole 10-year horizon (64 x 256 BE steps)" % \
         n_samples
@@ -736,7 +792,7 @@ def main():
     ap.add_argument("--surrogate-only", action="store_true",
                     help="time only the surrogate inference (profiling); prints its own JSON line")
     ap.add_argument("--surrogate-rows", type=int, default=4096 * 1024)
-    ap.add_argument("--samples", type=int, default=32, help="Monte Carlo samples of the full chip held at once")
+    ap.add_argument("--samples", type=int, default=24, help="Monte Carlo samples of the full chip held at once")
     ap.add_argument("--window", type=int, default=8, help="samples whose coefficients are held at once")
     ap.add_argument("--max-voids", type=int, default=128)
     ap.add_argument("--no-tune", action="store_true", help="built-in chain shapes instead of the autotuner's")

@@ -198,12 +198,12 @@ def scale_to_drop(grid, params, target, precision=A.EMS_F32):
 
 
 def validate_bound(mlp, grids, params, coarsen=16, guard=0.8, candidates=(-1.0, -0.6, -0.3, 0.0, 0.3, 0.6, 1.0, 1.5),
-                   tol=5e-4, margin=0.1, precision=A.EMS_F32):
+                   tol=5e-4, margin=0.1, precision=A.EMS_F32, max_voids=32):
     """Schedule bound validated end to end against the plain solver
     (ems_surrogate_validate on one context per held-out grid).  Returns
     (first passing candidate + margin, or inf when none passes;
     per-candidate log of dicts bound / coarse_frac / max_rel_err)."""
-    engs = [Engine(params, g, precision=precision, max_voids=32) for g in grids]
+    engs = [Engine(params, g, precision=precision, max_voids=max_voids) for g in grids]
     try:
         ctxs = (ctypes.c_void_p * len(engs))(*[e.ctx.value for e in engs])
         cand = np.ascontiguousarray(candidates, np.float64)
