@@ -76,6 +76,6 @@ def test_reference_arm_line():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in line, k
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
-    assert line["config"]["workload"] == bench.WORKLOAD % (32, 8)      # the GPU arm's default batch
+    assert line["config"]["workload"] == bench.WORKLOAD % (24, 8)      # the GPU arm's default batch
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
