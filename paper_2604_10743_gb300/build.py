@@ -44,7 +44,7 @@ def build(force=False, verbose=False, extra=()):
     with cf.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(srcs))) as ex:
         objs = list(ex.map(comp, srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -1,10 +1,13 @@
 // ems_host.cu -- context, grid loading (tree extraction, packing, IR
 // structure), workspace layout, state I/O of the GB300 EM/TM engine.
 #include <algorithm>
-#include <cstdlib>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 #include "ems_internal.cuh"
@@ -144,6 +147,27 @@ bool connected_to_pads(const ems_grid_desc *g) {
     return true;
 }
 
+// fn(i) for i in [0, n) on the host's cores (an atomic counter hands out the
+// items; fn must only write what item i owns)
+template <class F>
+void parallel_for(int n, F &&fn) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nthr = std::min(std::min(hw, 32), std::max(1, n / 8));
+    if (nthr <= 1) {
+        for (int i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
+    };
+    std::vector<std::thread> th;
+    th.reserve(nthr - 1);
+    for (int k = 1; k < nthr; ++k) th.emplace_back(work);
+    work();
+    for (auto &x : th) x.join();
+}
+
 int find(std::vector<int> &p, int x) {
     while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
     return x;
@@ -155,39 +179,53 @@ int find(std::vector<int> &p, int x) {
 ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
     const int ns = g->n_seg;
     auto is_via = [&](int s) { return g->seg_via && g->seg_via[s]; };
-    // (layer, node) groups of incident wire segments, via sorting endpoint
-    // records (via resistors join layers and belong to no stress tree)
-    struct Rec { int32_t layer, node, seg; };
-    std::vector<Rec> rec;
-    rec.reserve(2 * (size_t)ns);
+    // (layer, node) groups of incident wire segments, in (layer, node,
+    // segment) order by a counting sort of the endpoint records into per-layer
+    // node buckets (via resistors join layers and belong to no stress tree)
+    const int nn_ = g->n_nodes;
+    int lay_idx[65];
+    std::fill(lay_idx, lay_idx + 65, -1);
+    for (int s = 0; s < ns; ++s)
+        if (!is_via(s)) lay_idx[g->seg_layer[s]] = 0;
+    int nL = 0;
+    for (int l = 0; l < 65; ++l)
+        if (lay_idx[l] == 0) lay_idx[l] = nL++;
+    const int64_t nb = (int64_t)nL * nn_;
+    std::vector<int64_t> bstart(nb + 1, 0);
     for (int s = 0; s < ns; ++s) {
         if (is_via(s)) continue;
-        rec.push_back({g->seg_layer[s], g->seg_a[s], s});
-        rec.push_back({g->seg_layer[s], g->seg_b[s], s});
+        const int64_t li = lay_idx[g->seg_layer[s]];
+        ++bstart[li * nn_ + g->seg_a[s] + 1];
+        ++bstart[li * nn_ + g->seg_b[s] + 1];
     }
-    std::sort(rec.begin(), rec.end(), [](const Rec &x, const Rec &y) {
-        if (x.layer != y.layer) return x.layer < y.layer;
-        if (x.node != y.node) return x.node < y.node;
-        return x.seg < y.seg;
-    });
+    for (int64_t k = 0; k < nb; ++k) bstart[k + 1] += bstart[k];
+    struct Rec { int32_t layer, node, seg; };
+    std::vector<Rec> rec((size_t)bstart[nb]);
+    {
+        std::vector<int64_t> fill(bstart.begin(), bstart.end() - 1);
+        for (int s = 0; s < ns; ++s) {
+            if (is_via(s)) continue;
+            const int64_t li = lay_idx[g->seg_layer[s]];
+            rec[fill[li * nn_ + g->seg_a[s]]++] = {g->seg_layer[s], g->seg_a[s], s};
+            rec[fill[li * nn_ + g->seg_b[s]]++] = {g->seg_layer[s], g->seg_b[s], s};
+        }
+    }
     std::vector<int64_t> gstart;          // group boundaries in rec
-    for (size_t k = 0; k < rec.size(); ++k)
-        if (k == 0 || rec[k].layer != rec[k - 1].layer || rec[k].node != rec[k - 1].node)
-            gstart.push_back((int64_t)k);
+    std::vector<int32_t> grp_of((size_t)nb, -1);   // bucket (layer index, node) -> group
+    for (int64_t k = 0; k < nb; ++k)
+        if (bstart[k + 1] > bstart[k]) {
+            grp_of[k] = (int32_t)gstart.size();
+            gstart.push_back(bstart[k]);
+        }
     gstart.push_back((int64_t)rec.size());
     const size_t ng = gstart.size() - 1;
-    std::unordered_map<int64_t, int32_t> gid;
-    gid.reserve(ng * 2);
-    auto key = [](int32_t layer, int32_t node) { return ((int64_t)layer << 32) ^ (uint32_t)node; };
     std::vector<int> uf(ns);
     std::iota(uf.begin(), uf.end(), 0);
-    for (size_t q = 0; q < ng; ++q) {
-        gid[key(rec[gstart[q]].layer, rec[gstart[q]].node)] = (int32_t)q;
+    for (size_t q = 0; q < ng; ++q)
         for (int64_t k = gstart[q] + 1; k < gstart[q + 1]; ++k) {
             int a = find(uf, rec[gstart[q]].seg), b = find(uf, rec[k].seg);
             if (a != b) uf[std::max(a, b)] = std::min(a, b);
         }
-    }
     // tree ids in order of smallest segment id
     std::vector<int32_t> tid_of_root(ns, -1);
     tr.tree_of_seg.assign(ns, -1);
@@ -200,52 +238,75 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
         tsegs[tid_of_root[r]].push_back(s);
     }
     tr.n_trees = (int)tsegs.size();
-    tr.off.assign(1, 0);
-    int64_t total = 0;
-    for (auto &ts : tsegs)
-        for (int s : ts) total += g->seg_cells[s];
-    total += tr.n_trees;
-    tr.par.reserve(total); tr.face_seg.reserve(total); tr.face_dx.reserve(total);
-    tr.face_area.reserve(total); tr.face_sign.reserve(total); tr.x.reserve(total);
-    tr.y.reserve(total); tr.owner_seg.reserve(total); tr.ir_id.reserve(total); tr.ir_par.reserve(total);
-    tr.inc_ptr.assign(1, 0);
-    tr.is_chain.assign(tr.n_trees, 1);
-
     auto group_of = [&](int32_t layer, int32_t node) -> int32_t {
-        auto it = gid.find(key(layer, node));
-        return it == gid.end() ? -1 : it->second;
+        const int li = layer >= 0 && layer < 65 ? lay_idx[layer] : -1;
+        return li < 0 ? -1 : grp_of[(size_t)li * nn_ + node];
     };
-    for (int t = 0; t < tr.n_trees; ++t) {
+    // pass 1, per tree (in parallel): root (lowest-id leaf), stress nodes
+    // (root + every segment's cells) and incidence entries (an IR node lists
+    // its group's segments, an interior node its own segment)
+    const int nt = tr.n_trees;
+    std::vector<int32_t> root_of(nt, -1);
+    std::vector<int64_t> nn(nt, 0), ni(nt, 0);
+    std::vector<int> bad(nt, 0);            // 1: a cycle, 2: no leaf
+    parallel_for(nt, [&](int t) {
         const auto &ts = tsegs[t];
         const int32_t layer = g->seg_layer[ts[0]];
-        // distinct IR nodes and root
         std::vector<int32_t> nodes;
         nodes.reserve(2 * ts.size());
         for (int s : ts) { nodes.push_back(g->seg_a[s]); nodes.push_back(g->seg_b[s]); }
         std::sort(nodes.begin(), nodes.end());
         nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
-        if (nodes.size() != ts.size() + 1)
-            return fail(c, EMS_E_INVAL, "same-layer component with a cycle: not a tree");
-        int32_t root = -1;
+        if (nodes.size() != ts.size() + 1) { bad[t] = 1; return; }
+        int64_t cnt = 1, inc = 0;
         for (int32_t nd : nodes) {
-            int32_t q = group_of(layer, nd);
-            if (gstart[q + 1] - gstart[q] == 1) { root = nd; break; }   // nodes sorted: lowest id
+            const int32_t q = group_of(layer, nd);
+            const int64_t gs = gstart[q + 1] - gstart[q];
+            inc += gs;
+            if (root_of[t] < 0 && gs == 1) root_of[t] = nd;      // nodes sorted: lowest id
         }
-        if (root < 0) return fail(c, EMS_E_INVAL, "tree without a leaf");
-        const int64_t base = (int64_t)tr.par.size();
+        if (root_of[t] < 0) { bad[t] = 2; return; }
+        for (int s : ts) { cnt += g->seg_cells[s]; inc += g->seg_cells[s] - 1; }
+        nn[t] = cnt;
+        ni[t] = inc;
+    });
+    for (int t = 0; t < nt; ++t) {
+        if (bad[t] == 1) return fail(c, EMS_E_INVAL, "same-layer component with a cycle: not a tree");
+        if (bad[t] == 2) return fail(c, EMS_E_INVAL, "tree without a leaf");
+    }
+    tr.off.assign(nt + 1, 0);
+    std::vector<int64_t> ioff(nt + 1, 0);
+    for (int t = 0; t < nt; ++t) { tr.off[t + 1] = tr.off[t] + nn[t]; ioff[t + 1] = ioff[t] + ni[t]; }
+    const int64_t total = tr.off[nt];
+    tr.par.resize(total); tr.face_seg.resize(total); tr.face_dx.resize(total);
+    tr.face_area.resize(total); tr.face_sign.resize(total); tr.x.resize(total);
+    tr.y.resize(total); tr.owner_seg.resize(total); tr.ir_id.resize(total); tr.ir_par.resize(total);
+    tr.inc_ptr.assign(total + 1, 0);
+    tr.inc_seg.resize(ioff[nt]);
+    tr.is_chain.assign(nt, 1);
+
+    // pass 2, per tree (in parallel): depth-first preorder from the root into
+    // the tree's own range, the canonical order
+    parallel_for(nt, [&](int t) {
+        const auto &ts = tsegs[t];
+        const int32_t layer = g->seg_layer[ts[0]];
+        const int32_t root = root_of[t];
+        const int64_t base = tr.off[t];
+        int64_t ip = ioff[t];
         int32_t cnt = 0;
         auto emit = [&](int32_t parent, int32_t seg, double dx, double area, int8_t sign, double xx,
                         double yy, int32_t own, int32_t grp, int32_t irn, int32_t irp) -> int32_t {
-            tr.ir_id.push_back(irn); tr.ir_par.push_back(irp);
-            tr.par.push_back(parent); tr.face_seg.push_back(seg); tr.face_dx.push_back(dx);
-            tr.face_area.push_back(area); tr.face_sign.push_back(sign);
-            tr.x.push_back(xx); tr.y.push_back(yy); tr.owner_seg.push_back(own);
+            const int64_t i = base + cnt;
+            tr.ir_id[i] = irn; tr.ir_par[i] = irp;
+            tr.par[i] = parent; tr.face_seg[i] = seg; tr.face_dx[i] = dx;
+            tr.face_area[i] = area; tr.face_sign[i] = sign;
+            tr.x[i] = xx; tr.y[i] = yy; tr.owner_seg[i] = own;
             if (grp >= 0) {
-                for (int64_t k = gstart[grp]; k < gstart[grp + 1]; ++k) tr.inc_seg.push_back(rec[k].seg);
+                for (int64_t k = gstart[grp]; k < gstart[grp + 1]; ++k) tr.inc_seg[ip++] = rec[k].seg;
             } else {
-                tr.inc_seg.push_back(seg);
+                tr.inc_seg[ip++] = seg;
             }
-            tr.inc_ptr.push_back((int32_t)tr.inc_seg.size());
+            tr.inc_ptr[i + 1] = (int32_t)ip;
             return cnt++;
         };
         int32_t rg = group_of(layer, root);
@@ -287,8 +348,7 @@ ems_status extract_trees(ems_ctx *c, const ems_grid_desc *g, HostTrees &tr) {
         }
         for (int32_t i = 1; i < cnt; ++i)
             if (tr.par[base + i] != i - 1) { tr.is_chain[t] = 0; break; }
-        tr.off.push_back(base + cnt);
-    }
+    });
     // children CSR (tree-local indices)
     const int64_t N = tr.off.back();
     tr.child_ptr.assign(N + 1, 0);
@@ -415,6 +475,64 @@ ems_status make_plan(ems_ctx *c, const ems_params *p, const ems_grid_desc *g, Pl
     }
     pl.P = P;
     return EMS_OK;
+}
+
+// One-slot cache of the last plan ems_workspace_bytes made, so that the
+// usual sequence (size query, workspace allocation, ems_load_grid) plans once.
+// The key hashes everything planning reads: the parameters it depends on, the shape rules,
+// the grid's sizes and the arrays of its topology, geometry, pads, sinks and
+// initial resistances (not the Monte Carlo factors or the map: validate()
+// checks those on every load).
+struct PlanCache {
+    std::mutex mu;
+    bool valid = false;
+    uint64_t key = 0;
+    Plan plan;
+};
+PlanCache &plan_cache() {
+    static PlanCache pc;
+    return pc;
+}
+
+struct Hasher {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+    void mix(uint64_t v) {
+        h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 31;
+    }
+    void bytes(const void *p, size_t n) {
+        mix(n);
+        if (!p) { mix(0xFFFFFFFFull); return; }
+        const unsigned char *b = (const unsigned char *)p;
+        size_t k = 0;
+        for (; k + 8 <= n; k += 8) {
+            uint64_t v;
+            std::memcpy(&v, b + k, 8);
+            mix(v);
+        }
+        uint64_t t = 0;
+        for (; k < n; ++k) t = (t << 8) | b[k];
+        mix(t);
+    }
+};
+
+uint64_t plan_key(const ems_params *p, const std::vector<ems_chain_rule> &rules, const ems_grid_desc *g) {
+    Hasher h;
+    // the parameters the plan depends on (field by field: the struct has padding)
+    h.mix((uint64_t)(int64_t)p->precision); h.mix((uint64_t)(int64_t)p->method);
+    h.mix((uint64_t)(int64_t)p->ir_precond); h.mix((uint64_t)(int64_t)p->window_samples);
+    h.bytes(rules.data(), rules.size() * sizeof(ems_chain_rule));
+    const size_t nn = g->n_nodes > 0 ? (size_t)g->n_nodes : 0, ns = g->n_seg > 0 ? (size_t)g->n_seg : 0;
+    const size_t np = g->n_pads > 0 ? (size_t)g->n_pads : 0, nk = g->n_sinks > 0 ? (size_t)g->n_sinks : 0;
+    h.mix(nn); h.mix(ns); h.mix(np); h.mix(nk); h.mix((uint64_t)(int64_t)g->n_samples);
+    h.bytes(g->node_x, 8 * nn); h.bytes(g->node_y, 8 * nn);
+    h.bytes(g->seg_a, 4 * ns); h.bytes(g->seg_b, 4 * ns); h.bytes(g->seg_layer, 4 * ns);
+    h.bytes(g->seg_cells, 4 * ns); h.bytes(g->seg_R0, 8 * ns); h.bytes(g->seg_W, 8 * ns);
+    h.bytes(g->seg_H, 8 * ns); h.bytes(g->seg_L, 8 * ns); h.bytes(g->seg_via, ns);
+    h.bytes(g->pad_node, 4 * np); h.bytes(g->pad_V, 8 * np);
+    h.bytes(g->sink_node, 4 * nk); h.bytes(g->sink_I, 8 * nk);
+    return h.h;
 }
 
 size_t carve(ems_ctx *c, const Plan &pl, const ems_grid_desc *g, void *base, Dev &d) {
@@ -670,10 +788,17 @@ extern "C" size_t ems_workspace_bytes_rules(const ems_params *params, const ems_
     if (!params || n_rules < 0 || (n_rules > 0 && !rules)) return 0;
     tmp.prm = *params;
     if (n_rules > 0 && ems_set_chain_rules(&tmp, rules, n_rules) != EMS_OK) return 0;
+    if (!grid) return 0;
     Plan pl;
     if (make_plan(&tmp, params, grid, pl) != EMS_OK) return 0;
     Dev d{};
-    return carve(&tmp, pl, grid, nullptr, d);
+    const size_t need = carve(&tmp, pl, grid, nullptr, d);
+    PlanCache &pc = plan_cache();
+    std::lock_guard<std::mutex> lk(pc.mu);
+    pc.key = plan_key(params, tmp.rules, grid);
+    pc.plan = std::move(pl);
+    pc.valid = true;
+    return need;
 }
 
 extern "C" size_t ems_workspace_bytes(const ems_params *params, const ems_grid_desc *grid) {
@@ -719,8 +844,23 @@ extern "C" const char *ems_last_error(const ems_ctx *c) { return c ? c->err.c_st
 
 extern "C" ems_status ems_load_grid(ems_ctx *c, const ems_grid_desc *g) {
     if (!c) return EMS_E_INVAL;
+    if (!g) return fail(c, EMS_E_INVAL, "null grid");
     Plan pl;
-    EMS_TRY(make_plan(c, &c->prm, g, pl));
+    bool cached = false;
+    {
+        PlanCache &pc = plan_cache();
+        std::lock_guard<std::mutex> lk(pc.mu);
+        if (pc.valid) {
+            if (pc.key == plan_key(&c->prm, c->rules, g)) {
+                pl = std::move(pc.plan);
+                cached = true;
+            }
+            pc.plan = Plan();
+            pc.valid = false;
+        }
+    }
+    if (cached) EMS_TRY(validate(c, &c->prm, g));     // the factors and the map are not in the key
+    else EMS_TRY(make_plan(c, &c->prm, g, pl));
     Dev d{};
     size_t need = carve(c, pl, g, nullptr, d);
     if (c->own_ws) {
