@@ -300,7 +300,7 @@ def run_mine(args):
     # chosen = the FP32 path timed above (cluster kernel, compensated sums)
     pvc = None
     if not args.no_plain:
-        pvc = plain_vs_chosen(p, args, stream, rules)
+        pvc = plain_vs_chosen(p, args, stream, rules, n_samples=args.mc_samples)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -796,6 +796,9 @@ def main():
     ap.add_argument("--window", type=int, default=8, help="samples whose coefficients are held at once")
     ap.add_argument("--max-voids", type=int, default=128)
     ap.add_argument("--no-tune", action="store_true", help="built-in chain shapes instead of the autotuner's")
+    ap.add_argument("--mc-samples", type=int, default=1,
+                    help="Monte Carlo samples of the full-chip plain vs chosen TTF comparison (plain FP64 takes "
+                         "about 100 s per sample)")
     ap.add_argument("--profile-case", choices=["cluster-stripes", "ir-mg"],
                     help="run one small case of a kernel for an ncu capture: cluster-stripes = 16 stripes of "
                          "20,469 nodes x 20 Monte Carlo samples, two aging steps (k_chain_cl on 4-CTA clusters); "

@@ -147,27 +147,6 @@ bool connected_to_pads(const ems_grid_desc *g) {
     return true;
 }
 
-// fn(i) for i in [0, n) on the host's cores (an atomic counter hands out the
-// items; fn must only write what item i owns)
-template <class F>
-void parallel_for(int n, F &&fn) {
-    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-    const int nthr = std::min(std::min(hw, 32), std::max(1, n / 8));
-    if (nthr <= 1) {
-        for (int i = 0; i < n; ++i) fn(i);
-        return;
-    }
-    std::atomic<int> next(0);
-    auto work = [&]() {
-        for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
-    };
-    std::vector<std::thread> th;
-    th.reserve(nthr - 1);
-    for (int k = 1; k < nthr; ++k) th.emplace_back(work);
-    work();
-    for (auto &x : th) x.join();
-}
-
 int find(std::vector<int> &p, int x) {
     while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
     return x;
@@ -382,43 +361,84 @@ void build_ir(const ems_grid_desc *g, HostIR &ir) {
             ir.node_of_free.push_back(i);
         }
     const int nf = (int)ir.node_of_free.size();
-    // per free row: (col, seg, diag) contributions
+    // per free row its (col, seg, diag) contributions and its pad segments,
+    // gathered by a counting sort over the segments (ascending segment id)
     struct E { int32_t col, seg; int8_t diag; };
-    std::vector<std::vector<E>> rows(nf);
-    std::vector<std::vector<std::pair<int32_t, double>>> pads(nf);
+    std::vector<int64_t> eoff((size_t)nf + 1, 0), poff((size_t)nf + 1, 0);
     for (int s = 0; s < g->n_seg; ++s) {
-        int a = g->seg_a[s], b = g->seg_b[s];
-        int fa = ir.free_of_node[a], fb = ir.free_of_node[b];
-        if (fa >= 0) {
-            rows[fa].push_back({fa, s, 1});
-            if (fb >= 0) rows[fa].push_back({fb, s, 0});
-            else pads[fa].push_back({s, ir.padV_of_node[b]});
-        }
-        if (fb >= 0) {
-            rows[fb].push_back({fb, s, 1});
-            if (fa >= 0) rows[fb].push_back({fa, s, 0});
-            else pads[fb].push_back({s, ir.padV_of_node[a]});
-        }
+        const int fa = ir.free_of_node[g->seg_a[s]], fb = ir.free_of_node[g->seg_b[s]];
+        if (fa >= 0) { eoff[fa + 1] += fb >= 0 ? 2 : 1; if (fb < 0) ++poff[fa + 1]; }
+        if (fb >= 0) { eoff[fb + 1] += fa >= 0 ? 2 : 1; if (fa < 0) ++poff[fb + 1]; }
     }
-    ir.ptr.assign(1, 0); ir.ent_ptr.assign(1, 0); ir.rhs_ptr.assign(1, 0);
-    for (int r = 0; r < nf; ++r) {
-        auto &v = rows[r];
-        std::sort(v.begin(), v.end(), [](const E &x, const E &y) {
-            return x.col != y.col ? x.col < y.col : x.seg < y.seg;
-        });
-        for (size_t k = 0; k < v.size(); ++k) {
-            if (k == 0 || v[k].col != v[k - 1].col) {
-                if (k > 0) ir.ent_ptr.push_back((int32_t)ir.ent_seg.size());
-                ir.col.push_back(v[k].col);
-                ir.ent_diag.push_back(v[k].diag);
+    for (int r = 0; r < nf; ++r) { eoff[r + 1] += eoff[r]; poff[r + 1] += poff[r]; }
+    std::vector<E> ent((size_t)eoff[nf]);
+    ir.rhs_seg.resize((size_t)poff[nf]);
+    ir.rhs_padV.resize((size_t)poff[nf]);
+    {
+        std::vector<int64_t> ep(eoff.begin(), eoff.end() - 1), pp(poff.begin(), poff.end() - 1);
+        for (int s = 0; s < g->n_seg; ++s) {
+            const int a = g->seg_a[s], b = g->seg_b[s];
+            const int fa = ir.free_of_node[a], fb = ir.free_of_node[b];
+            if (fa >= 0) {
+                ent[ep[fa]++] = {fa, s, 1};
+                if (fb >= 0) ent[ep[fa]++] = {fb, s, 0};
+                else { ir.rhs_seg[pp[fa]] = s; ir.rhs_padV[pp[fa]++] = ir.padV_of_node[b]; }
             }
-            ir.ent_seg.push_back(v[k].seg);
+            if (fb >= 0) {
+                ent[ep[fb]++] = {fb, s, 1};
+                if (fa >= 0) ent[ep[fb]++] = {fa, s, 0};
+                else { ir.rhs_seg[pp[fb]] = s; ir.rhs_padV[pp[fb]++] = ir.padV_of_node[a]; }
+            }
         }
-        if (!v.empty()) ir.ent_ptr.push_back((int32_t)ir.ent_seg.size());
-        ir.ptr.push_back((int32_t)ir.col.size());
-        for (auto &pv : pads[r]) { ir.rhs_seg.push_back(pv.first); ir.rhs_padV.push_back(pv.second); }
-        ir.rhs_ptr.push_back((int32_t)ir.rhs_seg.size());
     }
+    ir.rhs_ptr.resize((size_t)nf + 1);
+    for (int r = 0; r <= nf; ++r) ir.rhs_ptr[r] = (int32_t)poff[r];
+    // rows in parallel blocks: entries sorted by (col, seg), one matrix entry
+    // per distinct column listing its segments
+    const int nblk = std::max(1, std::min(1024, nf / 4096));
+    std::vector<int32_t> ncol((size_t)nf);
+    auto rows_of = [&](int q, int &r0, int &r1) {
+        r0 = (int)((int64_t)nf * q / nblk); r1 = (int)((int64_t)nf * (q + 1) / nblk);
+    };
+    parallel_for(nblk, [&](int q) {
+        int r0, r1;
+        rows_of(q, r0, r1);
+        for (int r = r0; r < r1; ++r) {
+            E *v = ent.data() + eoff[r], *ve = ent.data() + eoff[r + 1];
+            std::sort(v, ve, [](const E &x, const E &y) { return x.col != y.col ? x.col < y.col : x.seg < y.seg; });
+            int32_t k = 0;
+            for (E *e = v; e < ve; ++e)
+                if (e == v || e->col != (e - 1)->col) ++k;
+            ncol[r] = k;
+        }
+    });
+    ir.ptr.resize((size_t)nf + 1);
+    ir.ptr[0] = 0;
+    for (int r = 0; r < nf; ++r) ir.ptr[r + 1] = ir.ptr[r] + ncol[r];
+    const size_t nnz = (size_t)ir.ptr[nf];
+    ir.col.resize(nnz);
+    ir.ent_diag.resize(nnz);
+    ir.ent_ptr.resize(nnz + 1);
+    ir.ent_seg.resize((size_t)eoff[nf]);
+    ir.ent_ptr[0] = 0;
+    parallel_for(nblk, [&](int q) {
+        int r0, r1;
+        rows_of(q, r0, r1);
+        for (int r = r0; r < r1; ++r) {
+            int64_t j = (int64_t)ir.ptr[r] - 1;        // the current entry (column group)
+            for (int64_t k = eoff[r]; k < eoff[r + 1]; ++k) {
+                const E &e = ent[k];
+                if (k == eoff[r] || e.col != ent[k - 1].col) {
+                    if (k > eoff[r]) ir.ent_ptr[j + 1] = (int32_t)k;      // end of entry j
+                    ++j;
+                    ir.col[j] = e.col;
+                    ir.ent_diag[j] = e.diag;
+                }
+                ir.ent_seg[k] = e.seg;
+            }
+            if (eoff[r + 1] > eoff[r]) ir.ent_ptr[j + 1] = (int32_t)eoff[r + 1];
+        }
+    });
     ir.sink.assign(nf, 0.0);
     for (int i = 0; i < g->n_sinks; ++i) {
         int f = ir.free_of_node[g->sink_node[i]];

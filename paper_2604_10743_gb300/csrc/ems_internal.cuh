@@ -12,7 +12,11 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ems.h"
@@ -94,24 +98,58 @@ inline int cluster_max_threads(int prec, int M, int CL) {
     return (M == 8 && (CL == 2 || CL == 4 || CL == 8)) ? 320 : 0;
 }
 
+// host arrays that a pass fills completely: resize leaves trivial elements
+// unset instead of zeroing them first (the first touch then happens in the
+// filling pass, on its threads)
+template <class T>
+struct NoInit : std::allocator<T> {
+    template <class U> struct rebind { using other = NoInit<U>; };
+    NoInit() noexcept = default;
+    template <class U> NoInit(const NoInit<U> &) noexcept {}
+    template <class U> void construct(U *p) noexcept { ::new (static_cast<void *>(p)) U; }
+    template <class U, class... A> void construct(U *p, A &&...a) { ::new (static_cast<void *>(p)) U(static_cast<A &&>(a)...); }
+};
+template <class T> using hvec = std::vector<T, NoInit<T>>;
+
+// fn(i) for i in [0, n) on the host's cores (an atomic counter hands out the
+// items; fn must only write what item i owns)
+template <class F>
+void parallel_for(int n, F &&fn) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nthr = std::min(std::min(hw, 32), std::max(1, n / 8));
+    if (nthr <= 1) {
+        for (int i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
+    };
+    std::vector<std::thread> th;
+    th.reserve(nthr - 1);
+    for (int k = 1; k < nthr; ++k) th.emplace_back(work);
+    work();
+    for (auto &x : th) x.join();
+}
+
 // ---------------------------------------------------------------------------
 // Host-side tree extraction result (canonical order)
 // ---------------------------------------------------------------------------
 struct HostTrees {
     int n_trees = 0;
     std::vector<int64_t> off;          // [n_trees+1]
-    std::vector<int32_t> par;          // tree-local parent, -1 at the root
-    std::vector<int32_t> face_seg;     // segment of the face to the parent (-1 root)
-    std::vector<double> face_dx, face_area;
-    std::vector<int8_t> face_sign;     // +1 if parent->child is the segment's a->b
-    std::vector<double> x, y;
-    std::vector<int32_t> owner_seg;    // MC factor segment of the node
-    std::vector<int32_t> inc_ptr, inc_seg;  // incident tree segments (IR nodes), CSR
+    hvec<int32_t> par;                 // tree-local parent, -1 at the root
+    hvec<int32_t> face_seg;            // segment of the face to the parent (-1 root)
+    hvec<double> face_dx, face_area;
+    hvec<int8_t> face_sign;            // +1 if parent->child is the segment's a->b
+    hvec<double> x, y;
+    hvec<int32_t> owner_seg;           // MC factor segment of the node
+    hvec<int32_t> inc_ptr, inc_seg;    // incident tree segments (IR nodes), CSR
     std::vector<int32_t> child_ptr, child_idx;  // tree-local children, CSR over nodes
     std::vector<uint8_t> is_chain;     // per tree
     std::vector<int32_t> tree_of_seg;  // per segment
-    std::vector<int32_t> ir_id;        // per stress node: its IR node, -1 inside a segment
-    std::vector<int32_t> ir_par;       // per IR stress node: tree-local index of the parent IR stress node (-1 root)
+    hvec<int32_t> ir_id;               // per stress node: its IR node, -1 inside a segment
+    hvec<int32_t> ir_par;              // per IR stress node: tree-local index of the parent IR stress node (-1 root)
 };
 
 // Packing of one tree

@@ -62,13 +62,45 @@ SpM transpose(const SpM &A) {
     return T;   // rows come out with ascending columns
 }
 
-SpM spmm(const SpM &A, const SpM &B) {
+// rows [0, nr) built in parallel blocks: row(i, acc, mark, cols, col, val)
+// appends row i to (col, val) using the block's own scratch; the blocks are
+// concatenated in order, so every row's sums run in the same order as a
+// serial pass (the result is the same bit for bit)
+template <class Row>
+SpM build_rows(int nr, int nc, Row row) {
+    const int nblk = std::max(1, std::min(256, nr / 4096));
+    std::vector<std::vector<int32_t>> bptr(nblk), bcol(nblk);
+    std::vector<std::vector<double>> bval(nblk);
+    parallel_for(nblk, [&](int q) {
+        const int r0 = (int)((int64_t)nr * q / nblk), r1 = (int)((int64_t)nr * (q + 1) / nblk);
+        std::vector<double> acc(nc, 0.0);
+        std::vector<int32_t> mark(nc, -1), cols;
+        auto &pp = bptr[q];
+        pp.reserve(r1 - r0);
+        for (int i = r0; i < r1; ++i) {
+            row(i, acc, mark, cols, bcol[q], bval[q]);
+            pp.push_back((int32_t)bcol[q].size());
+        }
+    });
     SpM C;
-    C.nr = A.nr; C.nc = B.nc;
+    C.nr = nr; C.nc = nc;
     C.ptr.assign(1, 0);
-    std::vector<double> acc(B.nc, 0.0);
-    std::vector<int32_t> mark(B.nc, -1), cols;
-    for (int i = 0; i < A.nr; ++i) {
+    size_t tot = 0;
+    for (int q = 0; q < nblk; ++q) tot += bcol[q].size();
+    C.ptr.reserve(nr + 1); C.col.reserve(tot); C.val.reserve(tot);
+    for (int q = 0; q < nblk; ++q) {
+        const int32_t o = (int32_t)C.col.size();
+        for (int32_t v : bptr[q]) C.ptr.push_back(o + v);
+        C.col.insert(C.col.end(), bcol[q].begin(), bcol[q].end());
+        C.val.insert(C.val.end(), bval[q].begin(), bval[q].end());
+    }
+    return C;
+}
+
+SpM spmm(const SpM &A, const SpM &B) {
+    return build_rows(A.nr, B.nc, [&](int i, std::vector<double> &acc, std::vector<int32_t> &mark,
+                                       std::vector<int32_t> &cols, std::vector<int32_t> &ocol,
+                                       std::vector<double> &oval) {
         cols.clear();
         for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
             const double a = A.val[k];
@@ -80,10 +112,8 @@ SpM spmm(const SpM &A, const SpM &B) {
             }
         }
         std::sort(cols.begin(), cols.end());
-        for (int c : cols) { C.col.push_back(c); C.val.push_back(acc[c]); }
-        C.ptr.push_back((int32_t)C.col.size());
-    }
-    return C;
+        for (int c : cols) { ocol.push_back(c); oval.push_back(acc[c]); }
+    });
 }
 
 std::vector<double> diagonal(const SpM &A) {
@@ -141,12 +171,9 @@ SpM smoothed_prolongation(const SpM &A, const std::vector<double> &d, const std:
         rho = std::max(rho, s / d[i]);
     }
     const double omega = 4.0 / (3.0 * rho);
-    SpM P;
-    P.nr = A.nr; P.nc = nagg;
-    P.ptr.assign(1, 0);
-    std::vector<double> acc(nagg, 0.0);
-    std::vector<int32_t> mark(nagg, -1), cols;
-    for (int i = 0; i < A.nr; ++i) {
+    return build_rows(A.nr, nagg, [&](int i, std::vector<double> &acc, std::vector<int32_t> &mark,
+                                      std::vector<int32_t> &cols, std::vector<int32_t> &ocol,
+                                      std::vector<double> &oval) {
         cols.clear();
         auto add = [&](int c, double v) {
             if (mark[c] != i) { mark[c] = i; acc[c] = 0.0; cols.push_back(c); }
@@ -156,13 +183,13 @@ SpM smoothed_prolongation(const SpM &A, const std::vector<double> &d, const std:
         for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) add(agg[A.col[k]], -omega * A.val[k] / d[i]);
         std::sort(cols.begin(), cols.end());
         for (int c : cols)
-            if (acc[c] != 0.0) { P.col.push_back(c); P.val.push_back(acc[c]); }
-        P.ptr.push_back((int32_t)P.col.size());
-    }
-    return P;
+            if (acc[c] != 0.0) { ocol.push_back(c); oval.push_back(acc[c]); }
+    });
 }
 
-// inverse of an SPD dense matrix by Cholesky; false if not positive definite
+// inverse of an SPD dense matrix by Cholesky; false if not positive definite.
+// The rows below each pivot and the columns of the inverse run on the host's
+// cores; every entry's sums keep their order (the same result as one core).
 bool spd_inverse(int n, std::vector<double> &a /* n x n, in: A, out: A^-1 */) {
     std::vector<double> L((size_t)n * n, 0.0);
     for (int j = 0; j < n; ++j) {
@@ -171,26 +198,34 @@ bool spd_inverse(int n, std::vector<double> &a /* n x n, in: A, out: A^-1 */) {
         if (!(s > 0.0)) return false;
         const double ljj = std::sqrt(s);
         L[(size_t)j * n + j] = ljj;
-        for (int i = j + 1; i < n; ++i) {
-            double t = a[(size_t)i * n + j];
-            for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-            L[(size_t)i * n + j] = t / ljj;
-        }
+        const int rows = n - j - 1;
+        const int nb = std::max(1, std::min(64, rows / 64));
+        parallel_for(nb, [&](int q) {
+            const int i0 = j + 1 + (int)((int64_t)rows * q / nb), i1 = j + 1 + (int)((int64_t)rows * (q + 1) / nb);
+            for (int i = i0; i < i1; ++i) {
+                double t = a[(size_t)i * n + j];
+                for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+                L[(size_t)i * n + j] = t / ljj;
+            }
+        });
     }
-    std::vector<double> y(n), x(n);
-    for (int c = 0; c < n; ++c) {
-        for (int i = 0; i < n; ++i) {             // L y = e_c
+    std::vector<double> LT((size_t)n * n);              // LT[i][k] = L[k][i]
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) LT[(size_t)i * n + k] = L[(size_t)k * n + i];
+    parallel_for(n, [&](int c) {
+        std::vector<double> y(n, 0.0), x(n);
+        for (int i = c; i < n; ++i) {                    // L y = e_c (y_i = 0 for i < c)
             double t = i == c ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
+            for (int k = c; k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
             y[i] = t / L[(size_t)i * n + i];
         }
-        for (int i = n - 1; i >= 0; --i) {        // L^T x = y
+        for (int i = n - 1; i >= 0; --i) {               // L^T x = y
             double t = y[i];
-            for (int k = i + 1; k < n; ++k) t -= L[(size_t)k * n + i] * x[k];
+            for (int k = i + 1; k < n; ++k) t -= LT[(size_t)i * n + k] * x[k];
             x[i] = t / L[(size_t)i * n + i];
         }
         for (int i = 0; i < n; ++i) a[(size_t)i * n + c] = x[i];
-    }
+    });
     return true;
 }
 

@@ -61,25 +61,27 @@ def test_cached_plan_equals_fresh_plan():
 
 
 def test_changed_input_misses_the_cache():
-    """The resistances change in place after the size query: the load plans
-    with the new ones (the IR solve matches the oracle's with them)."""
+    """The segment lengths change in place after the size query (sizes stay,
+    the faces' spacing changes): the load plans again, and the stress run
+    matches the oracle's with the new lengths, not the old ones."""
     from paper_2604_10743_gb300 import _abi as A
     from paper_2604_10743_gb300.engine import Engine
-    g = dict(es.mid_grid(N=64, with_map=False))
-    g["seg_R0"] = np.array(g["seg_R0"], dtype=np.float64)
+    g = dict(es.mid_grid(N=32, with_map=False))
+    g["seg_L"] = np.array(g["seg_L"], dtype=np.float64)
     L = A.lib()
     orig = L.ems_load_grid
-    R_new = g["seg_R0"] * np.linspace(0.8, 1.2, g["seg_R0"].size)
+    L_new = g["seg_L"] * 1.25
 
     def load(ctx, desc):
-        g["seg_R0"][:] = R_new                         # same array, new values, after the size query
+        g["seg_L"][:] = L_new                          # same array, new values, after the size query
         return orig(ctx, desc)
     L.ems_load_grid = load
+    p = es.default_params(n_outer=4)
     try:
-        e = Engine(es.default_params(), g)
+        e = Engine(p, g)
     finally:
         L.ems_load_grid = orig
-    u, _ = e.ir_solve()
-    uo = F.ir_solve(g, R_new)
-    assert np.abs(u[0] - uo).max() < 1e-11
+    e.ttf()
+    ref = F.run_ttf(g, p, keep_state=True)          # g holds the new lengths
+    assert np.abs(e.sigma()[0] - ref["state"].sigma).max() < 1e-9 * np.abs(ref["state"].sigma).max()
     e.close()
