@@ -166,7 +166,11 @@ void ems_netlist_free(ems_netlist *nl);
 
 /* Bytes of device workspace a context needs for this grid (with the Monte
  * Carlo layout params->window_samples selects).  Returns 0 if the
- * descriptor is invalid. */
+ * descriptor is invalid.  Planning the grid (tree extraction, IR structure,
+ * multigrid hierarchy) is the work here; the plan stays in host memory for
+ * the next ems_load_grid and is used by it when the grid's arrays and the
+ * plan-relevant parameters and shape rules hash the same (the next size query
+ * or load releases it). */
 size_t ems_workspace_bytes(const ems_params *params, const ems_grid_desc *grid);
 
 /*

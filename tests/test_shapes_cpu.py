@@ -84,3 +84,20 @@ def test_rules_change_the_layout_only_where_they_fit(A):
     assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=1, M=12, CL=1)]) == 0
     assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=4, M=8, CL=9)]) == 0
     assert _ws(A, g, [dict(n_lo=5, n_hi=4, kind=1, M=8, CL=1)]) == 0
+
+
+def test_tuning_cache_key():
+    """The tuned-shape cache is keyed by what the chain lengths and launch
+    sizes depend on: the same grid gives the same key, a changed
+    discretisation, sample count, window or precision another."""
+    import numpy as np
+    from paper_2604_10743_gb300 import tune
+    g = es.mc_grid(n_samples=4)
+    k = tune.grid_key(g, 1)
+    assert k == tune.grid_key(dict(g), 1)
+    g2 = dict(g)
+    g2["seg_cells"] = np.array(g["seg_cells"]) + 1
+    assert tune.grid_key(g2, 1) != k
+    assert tune.grid_key(es.mc_grid(n_samples=5), 1) != k
+    assert tune.grid_key(g, 1, window=2) != k
+    assert tune.grid_key(g, 0) != k
