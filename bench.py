@@ -166,6 +166,8 @@ def kernel_name(rule, prec_name):
     r = "float" if prec_name == "f32" else "double"
     if rule["kernel"] == "cluster":
         return "k_chain_cl<%s,%d,%d>" % (r, rule["M"], rule["CL"])
+    if rule["kernel"] == "cluster_shared":
+        return "k_chain_cl<%s,%d,%d,smem>" % (r, rule["M"], rule["CL"])
     if rule["kernel"] == "register":
         return "k_chain_reg<%d>" % rule["M"]
     return "k_chain<%s,%d,%s>" % (r, rule["M"], "shared" if rule["kernel"] == "shared" else "global")
@@ -653,11 +655,12 @@ def schedule_leg(p, stream, n_train=24, n_valid=3, test_seed=3000, N=64, S=32):
             "max_rel_err_ttf_or_final_drop": _result_error(r_plain, r_sched)}
 
 
-def cluster_stripes_case(n_samples=20, cells=2924):
+def cluster_stripes_case(n_samples=20, cells=2924, shape=None):
     """Small case of the cluster chain kernel for a profiler capture: 16
     stripes of 7 x cells + 1 stress nodes (full-chip length for cells =
     2,924), the 8 x 8 grid's pads and sinks, a 33 x 33 hotspot map, n_samples
-    factor sets; two aging steps of 256 BE steps, FP32."""
+    factor sets; two aging steps of 256 BE steps, FP32.  shape "KIND:CL"
+    (e.g. "cluster_shared:4") overrides the built-in chain shape."""
     import numpy as np
     import torch
     import ems_synth as es
@@ -670,7 +673,13 @@ def cluster_stripes_case(n_samples=20, cells=2924):
     g["thermal"] = es.hotspot_raster(np.random.default_rng(4), 140e-6, 2, 360.0, 20.0, 40.0, 0.2, nx=33, ny=33)
     g["kappa_factor"], g["sigc_factor"] = es.mc_factors(np.random.default_rng(3), n_samples, g["seg_a"].size)
     p = es.default_params(n_outer=4, n_inner=256)
-    eng = Engine(p, g, precision=EMS_F32, max_voids=64)
+    rules = None
+    if shape:
+        from paper_2604_10743_gb300 import _abi as A
+        kind, cl = shape.split(":")
+        kinds = {v: k for k, v in A.CHAIN_KINDS.items()}
+        rules = [dict(n_lo=1, n_hi=10 ** 9, kind=kinds[kind], M=16, CL=int(cl))]
+    eng = Engine(p, g, precision=EMS_F32, max_voids=64, chain_rules=rules)
     r = eng.ttf(n_outer=2)
     torch.cuda.synchronize()
     out = {"stress_ms": r["stress_ms"], "voids": int(r["n_voids"].sum()),
@@ -804,6 +813,8 @@ def main():
                          "20,469 nodes x 20 Monte Carlo samples, two aging steps (k_chain_cl on 4-CTA clusters); "
                          "ir-mg = two IR solves of a 1024 x 1024 mesh (1.05 M unknowns) for 4 samples "
                          "(k_pcg_cluster_mg)")
+    ap.add_argument("--profile-shape", default=None,
+                    help="with --profile-case cluster-stripes: chain shape KIND:CL, e.g. cluster_shared:4")
     ap.add_argument("--mid-only", action="store_true",
                     help="time only full TTF runs of the 256 x 256 mesh; prints its own JSON line")
     args = ap.parse_args()
@@ -813,7 +824,7 @@ def main():
         import __graft_entry__ as ge
         ge.build()
         if args.profile_case == "cluster-stripes":
-            print(json.dumps({"profile_case": cluster_stripes_case()}))
+            print(json.dumps({"profile_case": cluster_stripes_case(shape=args.profile_shape)}))
         elif args.profile_case == "ir-mg":
             print(json.dumps({"profile_case": ir_mg_case()}))
         elif args.schedule_only:

@@ -207,15 +207,19 @@ ems_status ems_load_grid(ems_ctx *ctx, const ems_grid_desc *grid);
  *   EMS_CHAIN_CLUSTER   a cluster of CL CTAs (2..8) per (chain, sample), registers,
  *                       M = 16 (FP32) or 8 (FP64); CTAs trade their carries through
  *                       distributed shared memory
+ *   EMS_CHAIN_CLUSTER_SHARED  (FP32, M = 16) the cluster kernel with the chunk
+ *                       coefficients in shared memory (20 bytes per node), so that
+ *                       two CTAs share an SM; CL 2, 4, 8 (<= 320 threads a CTA) or
+ *                       5, 6 (<= 256)
  * Every shape solves the same system; results differ by rounding only.
  */
 enum { EMS_CHAIN_DEFAULT = 0, EMS_CHAIN_GLOBAL = 1, EMS_CHAIN_SHARED = 2, EMS_CHAIN_REGISTER = 3,
-       EMS_CHAIN_CLUSTER = 4 };
+       EMS_CHAIN_CLUSTER = 4, EMS_CHAIN_CLUSTER_SHARED = 5 };
 typedef struct {
     int64_t n_lo, n_hi;    /* chains of n_lo..n_hi stress nodes (inclusive) */
     int kind;              /* EMS_CHAIN_*; EMS_CHAIN_DEFAULT leaves the built-in choice */
     int M;                 /* nodes per thread: 4, 8, 16, 32 or 64 */
-    int CL;                /* CTAs per chain: 1, or 2 / 4 / 8 with EMS_CHAIN_CLUSTER */
+    int CL;                /* CTAs per chain: 1, or 2..8 with the cluster kinds */
     int T;                 /* out (ems_autotune, ems_chain_candidates): team threads for n_hi */
 } ems_chain_rule;
 

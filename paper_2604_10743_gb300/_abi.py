@@ -53,7 +53,7 @@ class EmsChainRule(ctypes.Structure):
                 ("CL", ctypes.c_int), ("T", ctypes.c_int)]
 
 
-CHAIN_KINDS = {0: "default", 1: "global", 2: "shared", 3: "register", 4: "cluster"}
+CHAIN_KINDS = {0: "default", 1: "global", 2: "shared", 3: "register", 4: "cluster", 5: "cluster_shared"}
 
 
 class EmsSpiceOpts(ctypes.Structure):

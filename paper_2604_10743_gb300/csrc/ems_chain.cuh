@@ -104,5 +104,8 @@ cudaError_t launch_cluster(int M, int CL, int T_cta, unsigned n_trees, int S, cu
                            const ChainArgs<float> &a);
 cudaError_t launch_cluster(int M, int CL, int T_cta, unsigned n_trees, int S, cudaStream_t st,
                            const ChainArgs<double> &a);
+// the same with the chunk coefficients in shared memory (FP32; ems_chain_cl_f32s.cu)
+cudaError_t launch_cluster_smem(int M, int CL, int T_cta, unsigned n_trees, int S, cudaStream_t st,
+                                const ChainArgs<float> &a);
 
 }  // namespace ems

@@ -27,6 +27,9 @@ namespace {
 
 namespace cg = cooperative_groups;
 
+// component j (0..3) of a float4; j is a constant after unrolling
+__device__ __forceinline__ float f4at(const float4 &v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+
 template <typename R>
 struct ClSlots {                      // written by the other CTAs of the cluster (push), read locally
     // every step, two buffers by step parity
@@ -174,8 +177,13 @@ __device__ __noinline__ void chain_factor_cl(const ChainArgs<R> &a, double dt, i
     }
 }
 
-template <typename R, int M, int CL, int TMAX>
-__global__ void __launch_bounds__(TMAX, 1) k_chain_cl(ChainArgs<R> a) {
+// SMC (FP32): the chunk coefficients (alpha, dt g, dt f, the response w)
+// and the thresholds live in dynamic shared memory, [array][k / 4][thread] as
+// float4 (20 bytes per node), instead of registers, so that two or more CTAs
+// share an SM; the arithmetic and its order are those of the register form.
+template <typename R, int M, int CL, int TMAX, bool SMC>
+__global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) {
+    static_assert(!SMC || (sizeof(R) == 4 && M % 4 == 0), "shared-memory coefficients: FP32, M a multiple of 4");
     __shared__ R sA[64], sB[64], sL[32], sR[32];
     __shared__ double sv[32];
     __shared__ int si[32];
@@ -283,8 +291,13 @@ __global__ void __launch_bounds__(TMAX, 1) k_chain_cl(ChainArgs<R> a) {
     // running products where they are used (the factorisation's order, so
     // the same values)
     R cp[M], cg_[M], cbt[M], w[M], g_next, cpb0, thc;
+    R w_first, w_last;                           // (SMC) the response w at the chunk's ends
     R exB = R(1), bxB = R(1), bxAz = R(0);
-    __shared__ R s_th[M * TMAX];
+    __shared__ R s_th_st[SMC ? 1 : M * TMAX];
+    extern __shared__ float4 s_c4[];             // (SMC) [4][M / 4][T] coefficients, then [M][T] thresholds
+    R *const s_th = SMC ? (R *)(s_c4 + 4 * (M / 4) * T) : s_th_st;
+    auto c4 = [&](int arr, int q) -> float4 { return s_c4[(arr * (M / 4) + q) * T + c]; };
+    auto put = [&](int arr, int k, R v) { ((float *)s_c4)[((arr * (M / 4) + k / 4) * T + c) * 4 + (k & 3)] = v; };
     unsigned vmask = 0u;
     __shared__ R s_last, s_hh;
     const unsigned full = 0xffffffffu;
@@ -298,10 +311,16 @@ __global__ void __launch_bounds__(TMAX, 1) k_chain_cl(ChainArgs<R> a) {
         for (int k = 0; k < M; ++k) {
             const int64_t pk = ps + (int64_t)k * TT + g;
             const int i = g * M + k;
-            cp[k] = a.alpha[pk];
-            cg_[k] = a.dtg[pk];
-            cbt[k] = a.beta[pk];
-            w[k] = a.Pf[pk];
+            if constexpr (SMC) {
+                put(0, k, a.alpha[pk]);
+                put(1, k, a.dtg[pk]);
+                put(2, k, a.beta[pk]);
+            } else {
+                cp[k] = a.alpha[pk];
+                cg_[k] = a.dtg[pk];
+                cbt[k] = a.beta[pk];
+                w[k] = a.Pf[pk];
+            }
             const R th = ((vmask >> k) & 1u) ? a.dtl[pk]
                                               : (i < n ? (sizeof(R) == 4 ? (R)__double2float_rd(a.thr[cs + i])
                                                                          : (R)a.thr[cs + i])
@@ -312,12 +331,29 @@ __global__ void __launch_bounds__(TMAX, 1) k_chain_cl(ChainArgs<R> a) {
         cpb0 = a.Pb[ps + g];
         g_next = g + 1 < TT ? a.dtg[ps + g + 1] : R(0);
         // response of the chunk's backward sweep to a unit forward carry
+        if constexpr (SMC) {
+            const int64_t pl = ps + (int64_t)(M - 1) * TT + g;
+            R wn = a.Pf[pl];
+            w_last = wn;
+            put(3, M - 1, wn);
 #pragma unroll
-        for (int k = M - 2; k >= 0; --k) w[k] = fmx(cp[k] * cg_[k + 1], w[k + 1], w[k]);
-        if (c == T - 1) s_hh = cp[M - 1] * g_next;
+            for (int k = M - 2; k >= 0; --k) {
+                const int64_t pk = ps + (int64_t)k * TT + g;
+                wn = fmx(a.alpha[pk] * a.dtg[pk + TT], wn, a.Pf[pk]);
+                put(3, k, wn);
+            }
+            w_first = wn;
+            if (c == T - 1) s_hh = a.alpha[pl] * g_next;
+        } else {
+#pragma unroll
+            for (int k = M - 2; k >= 0; --k) w[k] = fmx(cp[k] * cg_[k + 1], w[k + 1], w[k]);
+            w_first = w[0];
+            w_last = w[M - 1];
+            if (c == T - 1) s_hh = cp[M - 1] * g_next;
+        }
         R u0, u1, fB, v0, bAz, bB;
-        cta_scan<0, R>(R(0), w[M - 1], sA, sB, u0, exB, u1, fB);
-        cta_scan<1, R>(exB * w[0], cpb0, sA, sB, bxAz, bxB, bAz, bB);
+        cta_scan<0, R>(R(0), w_last, sA, sB, u0, exB, u1, fB);
+        cta_scan<1, R>(exB * w_first, cpb0, sA, sB, bxAz, bxB, bAz, bB);
         fB = __shfl_sync(full, fB, 0);
         bAz = __shfl_sync(full, bAz, 0);
         bB = __shfl_sync(full, bB, 0);
@@ -439,34 +475,67 @@ __global__ void __launch_bounds__(TMAX, 1) k_chain_cl(ChainArgs<R> a) {
             s_last = sg[M - 1];
         }
         // forward sweep, then the carries within the CTA
-        R gk = cg_[0];
-        R qprev = gk * (left - sg[0]);
         R z = R(0);
         R zr[M];
+        if constexpr (SMC) {                     // coefficients by groups of 4 nodes
+            float4 P = c4(0, 0), G = c4(1, 0), B = c4(2, 0), Gn = G;
+            R gk = G.x;
+            R qprev = gk * (left - sg[0]);
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-            const R nxt = k + 1 < M ? sg[k + 1] : right;
-            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
-            const R qn = gk1 * (sg[k] - nxt);
-            R r = qprev - qn + cbt[k];
-            if ((vmask >> k) & 1u) r -= s_th[k * T + c] * sg[k];
-            z = cp[k] * fmx(gk, z, r);
-            zr[k] = z;
-            qprev = qn;
-            gk = gk1;
+            for (int k = 0; k < M; ++k) {
+                const int j = k & 3;
+                if (j == 0 && k > 0) { P = c4(0, k >> 2); B = c4(2, k >> 2); G = Gn; }
+                if (j == 0 && k + 4 < M) Gn = c4(1, (k >> 2) + 1);
+                const R nxt = k + 1 < M ? sg[k + 1] : right;
+                const R gk1 = j < 3 ? f4at(G, j + 1) : (k + 1 < M ? Gn.x : g_next);
+                const R qn = gk1 * (sg[k] - nxt);
+                R r = qprev - qn + f4at(B, j);
+                if ((vmask >> k) & 1u) r -= s_th[k * T + c] * sg[k];
+                z = f4at(P, j) * fmx(gk, z, r);
+                zr[k] = z;
+                qprev = qn;
+                gk = gk1;
+            }
+        } else {
+            R gk = cg_[0];
+            R qprev = gk * (left - sg[0]);
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const R nxt = k + 1 < M ? sg[k + 1] : right;
+                const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
+                const R qn = gk1 * (sg[k] - nxt);
+                R r = qprev - qn + cbt[k];
+                if ((vmask >> k) & 1u) r -= s_th[k * T + c] * sg[k];
+                z = cp[k] * fmx(gk, z, r);
+                zr[k] = z;
+                qprev = qn;
+                gk = gk1;
+            }
         }
         R exA, u0, agA, u1;
-        cta_scan<0, R>(z, w[M - 1], sA, sB, exA, u0, agA, u1);
+        cta_scan<0, R>(z, w_last, sA, sB, exA, u0, agA, u1);
         // backward sweep without carries; the first node with this CTA's forward carry
         R x = R(0);
+        if constexpr (SMC) {
+            float4 P = c4(0, M / 4 - 1), G = c4(1, M / 4 - 1), Gn = G;
 #pragma unroll
-        for (int k = M - 1; k >= 0; --k) {
-            const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
-            x = fmx(cp[k] * gk1, x, zr[k]);
-            zr[k] = x;
+            for (int k = M - 1; k >= 0; --k) {
+                const int j = k & 3;
+                if (j == 3 && k + 1 < M) { Gn = G; P = c4(0, k >> 2); G = c4(1, k >> 2); }
+                const R gk1 = j < 3 ? f4at(G, j + 1) : (k + 1 < M ? Gn.x : g_next);
+                x = fmx(f4at(P, j) * gk1, x, zr[k]);
+                zr[k] = x;
+            }
+        } else {
+#pragma unroll
+            for (int k = M - 1; k >= 0; --k) {
+                const R gk1 = k + 1 < M ? cg_[k + 1] : g_next;
+                x = fmx(cp[k] * gk1, x, zr[k]);
+                zr[k] = x;
+            }
         }
         R bxA, u2, bgA, u3;
-        cta_scan<1, R>(fmx(w[0], exA, zr[0]), cpb0, sA, sB, bxA, u2, bgA, u3);
+        cta_scan<1, R>(fmx(w_first, exA, zr[0]), cpb0, sA, sB, bxA, u2, bgA, u3);
         (void)u0; (void)u1; (void)u2; (void)u3;
         agA = __shfl_sync(full, agA, 0);
         bgA = __shfl_sync(full, bgA, 0);
@@ -508,10 +577,20 @@ __global__ void __launch_bounds__(TMAX, 1) k_chain_cl(ChainArgs<R> a) {
         const R cf = fmx(exB, zin, exA);
         const R cr = fmx(bxB, C, fmx(bxAz, zin, bxA));
         R pb = R(1);
+        float4 P4, G4, W4, Gn4;
+        if constexpr (SMC) { P4 = c4(0, M / 4 - 1); G4 = c4(1, M / 4 - 1); W4 = c4(3, M / 4 - 1); Gn4 = G4; }
 #pragma unroll
         for (int k = M - 1; k >= 0; --k) {
-            pb *= cp[k] * (k + 1 < M ? cg_[k + 1] : g_next);
-            const R dk = fmx(pb, cr, fmx(w[k], cf, zr[k]));
+            R dk;
+            if constexpr (SMC) {
+                const int j = k & 3;
+                if (j == 3 && k + 1 < M) { Gn4 = G4; P4 = c4(0, k >> 2); G4 = c4(1, k >> 2); W4 = c4(3, k >> 2); }
+                pb *= f4at(P4, j) * (j < 3 ? f4at(G4, j + 1) : (k + 1 < M ? Gn4.x : g_next));
+                dk = fmx(pb, cr, fmx(f4at(W4, j), cf, zr[k]));
+            } else {
+                pb *= cp[k] * (k + 1 < M ? cg_[k + 1] : g_next);
+                dk = fmx(pb, cr, fmx(w[k], cf, zr[k]));
+            }
             if constexpr (sizeof(R) == 4) {               // compensated (Kahan) FP32 update
                 const R y = dk - cc[k];
                 const R tt = sg[k] + y;
@@ -576,20 +655,31 @@ __global__ void __launch_bounds__(TMAX, 1) k_chain_cl(ChainArgs<R> a) {
     cl.sync();                                   // no CTA leaves while another may read its slots
 }
 
-// one launch: n_trees chains x S samples, one cluster of CL CTAs per chain
+// raise the dynamic shared-memory limit of a shared-memory variant to what
+// TMAX threads need (outside any stream capture)
 template <typename R, int M, int CL, int TMAX>
+cudaError_t smem_limit() {
+    return cudaFuncSetAttribute(k_chain_cl<R, M, CL, TMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cluster_smem_bytes(M, TMAX));
+}
+
+// one launch: n_trees chains x S samples, one cluster of CL CTAs per chain
+template <typename R, int M, int CL, int TMAX, bool SMC = false>
 cudaError_t launch_cl(int T_cta, unsigned n_trees, int S, cudaStream_t st, const ChainArgs<R> &a) {
     if (T_cta > TMAX || T_cta < 32 || T_cta % 32) return cudaErrorInvalidValue;
+    // (SMC: the shared-memory limit was raised once by cluster_smem_init)
+    const size_t smem = SMC ? cluster_smem_bytes(M, T_cta) : 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = CL; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(n_trees * CL, S);
     cfg.blockDim = dim3(T_cta);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_chain_cl<R, M, CL, TMAX>, a);
+    return cudaLaunchKernelEx(&cfg, k_chain_cl<R, M, CL, TMAX, SMC>, a);
 }
 
 }  // namespace

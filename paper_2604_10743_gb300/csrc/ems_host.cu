@@ -701,6 +701,14 @@ bool shape_valid(int64_t n, int prec, int kind, int M, int CL, int *T) {
             t = tc * CL;
             break;
         }
+        case EMS_CHAIN_CLUSTER_SHARED: {
+            const int tmax = prec == EMS_F32 && CL >= 2 && CL <= 8 ? cluster_smem_max_threads(M, CL) : 0;
+            if (tmax == 0) return false;
+            const int64_t tc = round_warp((th + CL - 1) / CL);
+            if (tc > tmax || th <= (int64_t)(CL - 1) * tc) return false;
+            t = tc * CL;
+            break;
+        }
         default: return false;
     }
     if (T) *T = (int)t;
@@ -709,8 +717,9 @@ bool shape_valid(int64_t n, int prec, int kind, int M, int CL, int *T) {
 
 // Built-in choice.  Backward-Euler chains longer than one register-resident
 // CTA holds (FP32: 5,120 nodes; FP64: past the streaming kernel's 16,384):
-// the smallest cluster that holds them (16 nodes per thread in FP32, 8 in
-// FP64).  FP32 chains the
+// the smallest cluster that holds them (FP32: 16 nodes per thread, the
+// coefficients in shared memory, two CTAs per SM -- 30 % faster than in
+// registers on 20,469-node stripes; FP64: 8 per thread).  FP32 chains the
 // register kernel holds: 16 nodes per thread (<= 320 threads) for chains of
 // more than 2,048 nodes, else 8 (<= 576 threads).  Otherwise the streaming
 // kernel with the smallest power-of-two chunk in [4, 64] that keeps the team
@@ -720,10 +729,11 @@ bool shape_valid(int64_t n, int prec, int kind, int M, int CL, int *T) {
 static void builtin_shape(int64_t n, int prec, int method, int *T, int *M, int *CL, int *kind) {
     *CL = 1;
     const int64_t one_cta = prec == EMS_F32 ? 320 * 16 : 256 * 64;
+    const int ck = prec == EMS_F32 ? EMS_CHAIN_CLUSTER_SHARED : EMS_CHAIN_CLUSTER;
     if (method == EMS_BE && n > one_cta)
         for (int cl = 2; cl <= 8; ++cl)
-            if (shape_valid(n, prec, EMS_CHAIN_CLUSTER, cluster_chunk(prec), cl, T)) {
-                *M = cluster_chunk(prec); *CL = cl; *kind = EMS_CHAIN_CLUSTER;
+            if (shape_valid(n, prec, ck, cluster_chunk(prec), cl, T)) {
+                *M = cluster_chunk(prec); *CL = cl; *kind = ck;
                 return;
             }
     if (prec == EMS_F32) {
@@ -771,6 +781,7 @@ std::vector<ems_chain_rule> shape_candidates(int64_t n, int prec) {
         for (int M : {4, 8, 16, 32, 64}) add(kind, M, 1);
     for (int M : {8, 16})
         for (int CL = 2; CL <= 8; ++CL) add(EMS_CHAIN_CLUSTER, M, CL);
+    for (int CL = 2; CL <= 8; ++CL) add(EMS_CHAIN_CLUSTER_SHARED, 16, CL);
     return out;
 }
 
@@ -793,9 +804,10 @@ extern "C" ems_status ems_set_chain_rules(ems_ctx *c, const ems_chain_rule *rule
     for (int i = 0; i < n_rules; ++i) {
         const ems_chain_rule &r = rules[i];
         if (r.n_lo < 1 || r.n_hi < r.n_lo) return fail(c, EMS_E_INVAL, "rule range must have 1 <= n_lo <= n_hi");
-        if (r.kind < EMS_CHAIN_DEFAULT || r.kind > EMS_CHAIN_CLUSTER) return fail(c, EMS_E_INVAL, "unknown chain kernel");
-        if (r.kind != EMS_CHAIN_DEFAULT &&
-            (!pow2_chunk(r.M) || (r.kind == EMS_CHAIN_CLUSTER ? (r.CL < 2 || r.CL > 8) : r.CL != 1)))
+        if (r.kind < EMS_CHAIN_DEFAULT || r.kind > EMS_CHAIN_CLUSTER_SHARED)
+            return fail(c, EMS_E_INVAL, "unknown chain kernel");
+        const bool clk = r.kind == EMS_CHAIN_CLUSTER || r.kind == EMS_CHAIN_CLUSTER_SHARED;
+        if (r.kind != EMS_CHAIN_DEFAULT && (!pow2_chunk(r.M) || (clk ? (r.CL < 2 || r.CL > 8) : r.CL != 1)))
             return fail(c, EMS_E_INVAL, "M must be 4, 8, 16, 32 or 64; CL 2..8 for a cluster, else 1");
     }
     c->rules.assign(rules, rules + n_rules);
@@ -838,7 +850,10 @@ extern "C" ems_status ems_create(ems_ctx **out, const ems_params *params, void *
         delete c;
         return EMS_E_INVAL;
     }
-    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        cluster_smem_init() != cudaSuccess) {
+        if (c->ev0) cudaEventDestroy(c->ev0);
+        if (c->ev1) cudaEventDestroy(c->ev1);
         delete c;
         return EMS_E_CUDA;
     }

@@ -97,6 +97,17 @@ inline int cluster_max_threads(int prec, int M, int CL) {
     }
     return (M == 8 && (CL == 2 || CL == 4 || CL == 8)) ? 320 : 0;
 }
+// cluster chain kernel with the coefficients in shared memory (FP32, 16 per
+// thread, two or more CTAs per SM): threads a CTA may have per CL, and the
+// dynamic shared memory of a CTA (alpha, dt g, dt f, w and the threshold:
+// 20 bytes per node)
+inline int cluster_smem_max_threads(int M, int CL) {
+    return M == 16 ? ((CL == 2 || CL == 4 || CL == 8) ? 320 : (CL == 5 || CL == 6) ? 256 : 0) : 0;
+}
+inline size_t cluster_smem_bytes(int M, int T_cta) { return (size_t)5 * sizeof(float) * M * T_cta; }
+// raises those kernels' shared-memory limit; ems_create calls it, outside any
+// stream capture (ems_chain_cl_f32s.cu)
+cudaError_t cluster_smem_init();
 
 // host arrays that a pass fills completely: resize leaves trivial elements
 // unset instead of zeroing them first (the first touch then happens in the

@@ -1203,6 +1203,14 @@ cudaError_t launch_bucket_raw(ems_ctx *c, const Bucket &b, ChainArgs<R> a, int S
             if (b.CL < 2 || b.T % b.CL) return cudaErrorInvalidValue;
             e = launch_cluster(b.M, b.CL, b.T / b.CL, (unsigned)b.trees.size(), S, c->stream, a);
             break;
+        case EMS_CHAIN_CLUSTER_SHARED:      // the same, coefficients in shared memory (FP32)
+            if constexpr (kDelta) {
+                if (b.CL < 2 || b.T % b.CL) return cudaErrorInvalidValue;
+                e = launch_cluster_smem(b.M, b.CL, b.T / b.CL, (unsigned)b.trees.size(), S, c->stream, a);
+                break;
+            } else {
+                return cudaErrorInvalidValue;
+            }
 
         case EMS_CHAIN_REGISTER:
             if constexpr (kDelta) {

@@ -134,3 +134,52 @@ def test_tuned_engine_cache_and_parity(tmp_path):
     assert abs(r[metric][0] - ref[metric]) <= 1e-6 * ref[metric]
     e1.close(); e2.close()
 
+
+
+def test_cluster_shapes_on_full_chip_length_stripes():
+    """FP32 stripes of the full chip's length (20,469 stress nodes) on every
+    cluster shape the autotuner may pick -- coefficients in registers (one
+    CTA per SM) or in shared memory (two per SM), 4 to 8 CTAs a chain --
+    against one oracle run: stress at the FP32 bar, every tree's voids
+    within two nodes of the oracle's, TTF / final drop at 0.05 %.  A
+    shared-memory kernel does the register kernel's arithmetic in the same
+    order; the two compiled forms may contract a product into an addition
+    differently, so on the same cluster they agree at the FP32 bar (measured
+    on 8 CTAs: 7.2e-6)."""
+    from paper_2604_10743_gb300 import _abi as A
+    from paper_2604_10743_gb300.engine import Engine
+    g = es.stripe_mesh(8, 20e-6)
+    g["seg_cells"][:] = 2924
+    t = es.tiny_grid()
+    g["pad_node"], g["pad_V"], g["sink_node"], g["sink_I"] = t["pad_node"], t["pad_V"], t["sink_node"], t["sink_I"]
+    g["thermal"] = es.hotspot_raster(np.random.default_rng(2924), 140e-6, 2, 360.0, 20.0, 40.0, 0.2, nx=33, ny=33)
+    p = es.default_params(n_outer=3, n_inner=64, sigma_crit=250e6)
+    ref = F.run_ttf(g, p, keep_state=True, n_threads=8)
+    assert ref["n_voids"] >= 16
+    off = ref["trees"]["off"]
+    n = int(np.diff(off).max())
+    assert n == 20469
+    cands = [r for r in A.chain_candidates(n, 1) if r["kernel"] in ("cluster", "cluster_shared")]
+    assert {(r["kernel"], r["CL"]) for r in cands} >= {("cluster", 4), ("cluster_shared", 4), ("cluster_shared", 5),
+                                                        ("cluster_shared", 8)}
+    metric = "ttf" if math.isfinite(ref["ttf"]) else "final_drop"
+    sig = {}
+    for r in cands:
+        rule = dict(r, n_lo=1, n_hi=10 ** 9)
+        eng = Engine(p, g, precision=1, max_voids=64, chain_rules=[rule])
+        res = eng.ttf()
+        tag = "%s CL=%d" % (r["kernel"], r["CL"])
+        s = eng.sigma()[0]
+        assert _relerr(s, ref["state"].sigma) < TOL32, tag
+        v = eng.voids()
+        for k in range(len(off) - 1):
+            gv = sorted(x for x in v["node"].tolist() if off[k] <= x < off[k + 1])
+            ov = sorted(x for x in ref["void_nodes"].tolist() if off[k] <= x < off[k + 1])
+            assert len(gv) == len(ov), (tag, k)
+            assert all(abs(a - b) <= 2 for a, b in zip(gv, ov)), (tag, k)
+        assert abs(res[metric][0] - ref[metric]) <= TTF_TOL * ref[metric], tag
+        sig[(r["kernel"], r["CL"])] = s
+        eng.close()
+    for (kind, cl), s in sig.items():
+        if kind == "cluster_shared" and ("cluster", cl) in sig:
+            assert _relerr(s, sig[("cluster", cl)]) < TOL32, cl

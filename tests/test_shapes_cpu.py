@@ -28,6 +28,11 @@ def _check_candidate(r, n, prec):
         assert 2 <= CL <= 8 and tc <= 320
         assert M == (16 if prec == 1 else 8)
         assert (CL - 1) * tc * M < n                # no CTA without nodes
+    elif r["kernel"] == "cluster_shared":
+        assert prec == 1 and M == 16 and CL in (2, 4, 5, 6, 8)
+        assert tc <= (256 if CL in (5, 6) else 320)
+        assert (CL - 1) * tc * M < n
+        assert 2 * (20 * tc * M + 9 * 1024) <= 228 * 1024   # two CTAs' shared memory on one SM
     else:
         assert CL == 1
         assert T - 32 < -(-n // M)                  # the smallest team in whole warps
@@ -49,12 +54,16 @@ def test_candidates_hold_the_chain(A, n, prec):
 
 
 def test_builtin_choice_first(A):
-    # full-chip stripes: a 4-CTA cluster in FP32, 8 CTAs in FP64
+    # full-chip stripes: a 4-CTA cluster in FP32 (coefficients in shared memory), 8 CTAs in FP64
     c32 = A.chain_candidates(20471, 1)
-    assert (c32[0]["kernel"], c32[0]["M"], c32[0]["CL"], c32[0]["T"]) == ("cluster", 16, 4, 1280)
-    assert {(r["kernel"], r["M"], r["CL"]) for r in c32} >= {("cluster", 16, 5), ("cluster", 16, 6), ("cluster", 16, 8),
-                                                          ("global", 32, 1), ("global", 64, 1)}
+    assert (c32[0]["kernel"], c32[0]["M"], c32[0]["CL"], c32[0]["T"]) == ("cluster_shared", 16, 4, 1280)
+    assert {(r["kernel"], r["M"], r["CL"]) for r in c32} >= {("cluster", 16, 4), ("cluster", 16, 5), ("cluster", 16, 6),
+                                                          ("cluster", 16, 8), ("global", 32, 1), ("global", 64, 1)}
     assert all(r["T"] // r["CL"] <= 256 for r in c32 if r["kernel"] == "cluster" and r["CL"] in (5, 6))
+    # the same clusters with the coefficients in shared memory
+    assert {(r["CL"], r["T"]) for r in c32 if r["kernel"] == "cluster_shared"} == {(4, 1280), (5, 1280), (6, 1344),
+                                                                                  (8, 1280)}
+    assert not any(r["kernel"] == "cluster_shared" for r in A.chain_candidates(20471, 0))
     c64 = A.chain_candidates(20471, 0)
     assert (c64[0]["kernel"], c64[0]["CL"]) == ("cluster", 8)
     # mid-grid stripes: 16 nodes per thread in registers, 320 threads
@@ -83,6 +92,8 @@ def test_rules_change_the_layout_only_where_they_fit(A):
     # malformed rules are rejected
     assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=1, M=12, CL=1)]) == 0
     assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=4, M=8, CL=9)]) == 0
+    assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=5, M=16, CL=1)]) == 0
+    assert _ws(A, g, [dict(n_lo=1, n_hi=10**6, kind=6, M=16, CL=2)]) == 0
     assert _ws(A, g, [dict(n_lo=5, n_hi=4, kind=1, M=8, CL=1)]) == 0
 
 
