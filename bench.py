@@ -251,13 +251,13 @@ def run_mine(args):
     tf = os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")
     if os.path.exists(tf):
         try:
-            t = json.load(open(tf))
-            if t.get("precision") == args.precision and t.get("kernel") == kname:
-                traffic = t.get("bytes_per_launch")
-                if t.get("issue_active_pct") is not None:
-                    issue = {"issue_active_frac": t["issue_active_pct"] / 100.0,
-                             "fma_pipe_active_frac": t["fma_pipe_active_pct"] / 100.0,
-                             "source": "ncu, " + t.get("command", "")}
+            for t in json.load(open(tf)).get("captures", []):
+                if t.get("precision") == args.precision and t.get("kernel") == kname:
+                    traffic = t.get("bytes_per_launch")
+                    if t.get("issue_active_pct") is not None:
+                        issue = {"issue_active_frac": t["issue_active_pct"] / 100.0,
+                                 "fma_pipe_active_frac": t["fma_pipe_active_pct"] / 100.0,
+                                 "source": "ncu, " + t.get("command", "")}
         except (OSError, ValueError):
             pass
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
