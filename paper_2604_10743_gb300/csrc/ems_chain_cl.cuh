@@ -478,14 +478,18 @@ __global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) 
         R z = R(0);
         R zr[M];
         if constexpr (SMC) {                     // coefficients by groups of 4 nodes
-            float4 P = c4(0, 0), G = c4(1, 0), B = c4(2, 0), Gn = G;
+            // the next group's coefficients are loaded a group ahead
+            float4 P = c4(0, 0), G = c4(1, 0), B = c4(2, 0), Pn = P, Bn = B, Gn = G;
+            if (M > 4) { Pn = c4(0, 1); Bn = c4(2, 1); Gn = c4(1, 1); }
             R gk = G.x;
             R qprev = gk * (left - sg[0]);
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const int j = k & 3;
-                if (j == 0 && k > 0) { P = c4(0, k >> 2); B = c4(2, k >> 2); G = Gn; }
-                if (j == 0 && k + 4 < M) Gn = c4(1, (k >> 2) + 1);
+                if (j == 0 && k > 0) {
+                    P = Pn; B = Bn; G = Gn;
+                    if (k + 4 < M) { Pn = c4(0, (k >> 2) + 1); Bn = c4(2, (k >> 2) + 1); Gn = c4(1, (k >> 2) + 1); }
+                }
                 const R nxt = k + 1 < M ? sg[k + 1] : right;
                 const R gk1 = j < 3 ? f4at(G, j + 1) : (k + 1 < M ? Gn.x : g_next);
                 const R qn = gk1 * (sg[k] - nxt);
@@ -517,11 +521,16 @@ __global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) 
         // backward sweep without carries; the first node with this CTA's forward carry
         R x = R(0);
         if constexpr (SMC) {
-            float4 P = c4(0, M / 4 - 1), G = c4(1, M / 4 - 1), Gn = G;
+            // the previous group's coefficients are loaded a group ahead
+            float4 P = c4(0, M / 4 - 1), G = c4(1, M / 4 - 1), Gn = G, Pp = P, Gp = G;
+            if (M > 4) { Pp = c4(0, M / 4 - 2); Gp = c4(1, M / 4 - 2); }
 #pragma unroll
             for (int k = M - 1; k >= 0; --k) {
                 const int j = k & 3;
-                if (j == 3 && k + 1 < M) { Gn = G; P = c4(0, k >> 2); G = c4(1, k >> 2); }
+                if (j == 3 && k + 1 < M) {
+                    Gn = G; P = Pp; G = Gp;
+                    if (k >= 4) { Pp = c4(0, (k >> 2) - 1); Gp = c4(1, (k >> 2) - 1); }
+                }
                 const R gk1 = j < 3 ? f4at(G, j + 1) : (k + 1 < M ? Gn.x : g_next);
                 x = fmx(f4at(P, j) * gk1, x, zr[k]);
                 zr[k] = x;
@@ -577,14 +586,21 @@ __global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) 
         const R cf = fmx(exB, zin, exA);
         const R cr = fmx(bxB, C, fmx(bxAz, zin, bxA));
         R pb = R(1);
-        float4 P4, G4, W4, Gn4;
-        if constexpr (SMC) { P4 = c4(0, M / 4 - 1); G4 = c4(1, M / 4 - 1); W4 = c4(3, M / 4 - 1); Gn4 = G4; }
+        float4 P4, G4, W4, Gn4, Pp4, Gp4, Wp4;
+        if constexpr (SMC) {
+            P4 = c4(0, M / 4 - 1); G4 = c4(1, M / 4 - 1); W4 = c4(3, M / 4 - 1); Gn4 = G4;
+            Pp4 = P4; Gp4 = G4; Wp4 = W4;
+            if (M > 4) { Pp4 = c4(0, M / 4 - 2); Gp4 = c4(1, M / 4 - 2); Wp4 = c4(3, M / 4 - 2); }
+        }
 #pragma unroll
         for (int k = M - 1; k >= 0; --k) {
             R dk;
             if constexpr (SMC) {
                 const int j = k & 3;
-                if (j == 3 && k + 1 < M) { Gn4 = G4; P4 = c4(0, k >> 2); G4 = c4(1, k >> 2); W4 = c4(3, k >> 2); }
+                if (j == 3 && k + 1 < M) {
+                    Gn4 = G4; P4 = Pp4; G4 = Gp4; W4 = Wp4;
+                    if (k >= 4) { Pp4 = c4(0, (k >> 2) - 1); Gp4 = c4(1, (k >> 2) - 1); Wp4 = c4(3, (k >> 2) - 1); }
+                }
                 pb *= f4at(P4, j) * (j < 3 ? f4at(G4, j + 1) : (k + 1 < M ? Gn4.x : g_next));
                 dk = fmx(pb, cr, fmx(f4at(W4, j), cf, zr[k]));
             } else {
