@@ -493,8 +493,7 @@ ems_status ems_state_import(ems_ctx *ctx, const void *buf, size_t bytes);
  * allocated or freed.  All calls share that array: calls whose kernels can
  * overlap on one GPU (several streams or threads at once) race and must be
  * serialised by the caller.  The first call on each device looks the
- * array's device address up once, with that device current; make that first
- * call before any stream capture.
+ * array's device address up once, with that device current.
  */
 ems_status ems_ir_pcg_noalloc(int n, const int32_t *row_ptr, const int32_t *col, const double *val,
                               const double *b, double *x, double rtol, int max_iter, int *iterations,
