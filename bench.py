@@ -21,6 +21,7 @@ rank 0 prints the aggregate.  --impl reference times the CPU oracle on a
 bounded sample of the same workload on this host's cores.
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -162,6 +163,20 @@ def tuned_rules(p, prec, args):
     return table, time.perf_counter() - t0
 
 
+def source_sha1(files):
+    """SHA-1 over the bytes of the named repository files, in order (None
+    when one is missing): ties a stored profiler capture to the kernel
+    source it was taken on."""
+    h = hashlib.sha1()
+    for f in files:
+        try:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        except OSError:
+            return None
+    return h.hexdigest() if files else None
+
+
 def kernel_name(rule, prec_name):
     r = "float" if prec_name == "f32" else "double"
     if rule["kernel"] == "cluster":
@@ -247,12 +262,17 @@ def run_mine(args):
     peaks, src = _peaks()
     achieved = alg_bytes_launch / (per_launch_ms / 1e3) / 1e9
     traffic = None
+    traffic_note = None
     issue = None
     tf = os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")
     if os.path.exists(tf):
         try:
             for t in json.load(open(tf)).get("captures", []):
                 if t.get("precision") == args.precision and t.get("kernel") == kname:
+                    # counters of another build of the kernel do not count
+                    if source_sha1(t.get("source_files", [])) != t.get("source_sha1"):
+                        traffic_note = "kernel source changed since the ncu capture (%s)" % t.get("captured_at", "?")
+                        break
                     traffic = t.get("bytes_per_launch")
                     if t.get("issue_active_pct") is not None:
                         issue = {"issue_active_frac": t["issue_active_pct"] / 100.0,
@@ -267,6 +287,8 @@ def run_mine(args):
                       "256 BE steps of every stripe of %d samples)" % (kname, S // n_win),
             "alg_bytes_per_launch": int(alg_bytes_launch), "launch_ms": round(per_launch_ms, 3),
             "issue_roof": issue}
+    if traffic_note:
+        roof["traffic_note"] = traffic_note
 
     # end to end through the public API with host buffers: the netlist, the
     # map and the factor sets copied in, then aging steps with every step's

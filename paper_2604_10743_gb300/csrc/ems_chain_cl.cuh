@@ -49,11 +49,13 @@ struct ClSlots {                      // written by the other CTAs of the cluste
 };
 
 // exclusive scan of the chunk maps within the CTA (one barrier), with the
-// CTA's carry-in composed in: returns the carry entering this thread's chunk
-// and (thread 0 of the CTA, once all threads passed the barrier) the CTA's
-// aggregate map in *aggA, *aggB.  dir 0: left to right, 1: right to left.
+// CTA's carry-in composed in: returns the carry entering this thread's chunk,
+// and the CTA's aggregate map -- the inclusive map of the scan's last thread:
+// dir 0 (left to right) stored by lane 31 of the last warp in sAg[0..1], to
+// be read after the next barrier; dir 1 (right to left) in aggA, aggB of
+// lane 0 of warp 0.
 template <int DIR, typename R>
-__device__ __forceinline__ void cta_scan(R A, R B, R *sA, R *sB, R &exA, R &exB, R &aggA, R &aggB) {
+__device__ __forceinline__ void cta_scan(R A, R B, R *sA, R *sB, R &exA, R &exB, R &aggA, R &aggB, R *sAg) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // inclusive warp scan
@@ -83,14 +85,8 @@ __device__ __forceinline__ void cta_scan(R A, R B, R *sA, R *sB, R &exA, R &exB,
     const int first = DIR == 0 ? 0 : 31;
     exA = lane == first ? cwA : pA;
     exB = lane == first ? cwB : pB;
-    // the CTA aggregate (every warp's map composed), thread 0
-    aggA = R(0); aggB = R(1);
-    if (threadIdx.x == 0) {
-        if (DIR == 0)
-            for (int q = 0; q < nw; ++q) { aggA = fmx(sB[q], aggA, sA[q]); aggB = sB[q] * aggB; }
-        else
-            for (int q = nw - 1; q >= 0; --q) { aggA = fmx(sB[32 + q], aggA, sA[32 + q]); aggB = sB[32 + q] * aggB; }
-    }
+    aggA = iA; aggB = iB;
+    if (DIR == 0 && w == nw - 1 && lane == 31) { sAg[0] = iA; sAg[1] = iB; }
 }
 
 // Cluster version of chain_factor (increment form): every CTA calls it;
@@ -184,7 +180,7 @@ __device__ __noinline__ void chain_factor_cl(const ChainArgs<R> &a, double dt, i
 template <typename R, int M, int CL, int TMAX, bool SMC>
 __global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) {
     static_assert(!SMC || (sizeof(R) == 4 && M % 4 == 0), "shared-memory coefficients: FP32, M a multiple of 4");
-    __shared__ R sA[64], sB[64], sL[32], sR[32];
+    __shared__ R sA[64], sB[64], sL[32], sR[32], sAg[2];
     __shared__ double sv[32];
     __shared__ int si[32];
     __shared__ int s_nv;
@@ -352,9 +348,9 @@ __global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) 
             if (c == T - 1) s_hh = cp[M - 1] * g_next;
         }
         R u0, u1, fB, v0, bAz, bB;
-        cta_scan<0, R>(R(0), w_last, sA, sB, u0, exB, u1, fB);
-        cta_scan<1, R>(exB * w_first, cpb0, sA, sB, bxAz, bxB, bAz, bB);
-        fB = __shfl_sync(full, fB, 0);
+        cta_scan<0, R>(R(0), w_last, sA, sB, u0, exB, u1, fB, sAg);
+        cta_scan<1, R>(exB * w_first, cpb0, sA, sB, bxAz, bxB, bAz, bB, sAg);
+        fB = sAg[1];                             // written before the second scan's barrier
         bAz = __shfl_sync(full, bAz, 0);
         bB = __shfl_sync(full, bB, 0);
         (void)u0; (void)u1; (void)v0;
@@ -517,7 +513,7 @@ __global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) 
             }
         }
         R exA, u0, agA, u1;
-        cta_scan<0, R>(z, w_last, sA, sB, exA, u0, agA, u1);
+        cta_scan<0, R>(z, w_last, sA, sB, exA, u0, agA, u1, sAg);
         // backward sweep without carries; the first node with this CTA's forward carry
         R x = R(0);
         if constexpr (SMC) {
@@ -544,9 +540,9 @@ __global__ void __launch_bounds__(TMAX, SMC ? 2 : 1) k_chain_cl(ChainArgs<R> a) 
             }
         }
         R bxA, u2, bgA, u3;
-        cta_scan<1, R>(fmx(w_first, exA, zr[0]), cpb0, sA, sB, bxA, u2, bgA, u3);
+        cta_scan<1, R>(fmx(w_first, exA, zr[0]), cpb0, sA, sB, bxA, u2, bgA, u3, sAg);
         (void)u0; (void)u1; (void)u2; (void)u3;
-        agA = __shfl_sync(full, agA, 0);
+        agA = sAg[0];                            // written before the second scan's barrier
         bgA = __shfl_sync(full, bgA, 0);
         const R fst = __shfl_sync(full, sg[0], 0);
         if (c < CL) {

@@ -79,3 +79,23 @@ def test_reference_arm_line():
     assert line["config"]["workload"] == bench.WORKLOAD % (24, 8)      # the GPU arm's default batch
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_entries_are_tied_to_their_kernel_source(tmp_path):
+    """Each stored DRAM-traffic capture names the kernel source files it was
+    taken on and their SHA-1; the bench reports the traffic only while the
+    files still hash to it (a missing file never matches)."""
+    import hashlib
+    import json
+    t = json.load(open(os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")))
+    assert t["captures"]
+    for c in t["captures"]:
+        assert c["source_files"] and all(os.path.exists(os.path.join(ROOT, f)) for f in c["source_files"])
+        assert len(c["source_sha1"]) == 40 and c["bytes_per_launch"] > 0
+    files = t["captures"][0]["source_files"]
+    h = hashlib.sha1()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    assert bench.source_sha1(files) == h.hexdigest()
+    assert bench.source_sha1(files + ["no/such/file.cu"]) is None
+    assert bench.source_sha1([]) is None
