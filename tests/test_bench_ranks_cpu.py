@@ -99,3 +99,14 @@ def test_traffic_entries_are_tied_to_their_kernel_source(tmp_path):
     assert bench.source_sha1(files) == h.hexdigest()
     assert bench.source_sha1(files + ["no/such/file.cu"]) is None
     assert bench.source_sha1([]) is None
+
+
+def test_kernel_names_match_the_traffic_entries():
+    """The bench names the tuned stress kernel the way the stored captures
+    do, so a capture of the kernel it times is found."""
+    import json
+    names = {c["kernel"] for c in json.load(open(os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")))["captures"]}
+    assert bench.kernel_name({"kernel": "cluster_shared", "M": 16, "CL": 5}, "f32") in names
+    assert bench.kernel_name({"kernel": "cluster_shared", "M": 16, "CL": 4}, "f32") in names
+    assert bench.kernel_name({"kernel": "cluster", "M": 16, "CL": 4}, "f32") in names
+    assert bench.kernel_name({"kernel": "register", "M": 16, "CL": 1}, "f32") == "k_chain_reg<16>"
